@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark of the biharmonic field extension on GB300: extension solves/s at relative residual
+1e-8.
+
+Workloads (seeded synthetic inputs shaped like the paper's test problems):
+  single : one 1024x1024 extension (six-lobed star, field known outside, extend in, periodic
+           edges), plain FP32 path; a step is one complete solve (set-up, PCG to 1e-8, output).
+  batch  : 256 uneven grids (sides from {128,192,256,384,512}, wobbly interfaces, extend out,
+           symmetric edges) solved together; a step is the whole batch.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle (assembled sparse matrix and
+SuperLU direct solve, which reaches a residual far below 1e-8) on the same workload instead.
+
+Timing: inputs resident in HBM, CUDA events on the library's stream around each step, a 256 MiB
+L2 flush between steps (outside the events); the whole loop bracketed by barrier + synchronize.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+CSRC = os.path.join(ROOT, "paper_1704_08897_gb300", "csrc")
+
+# FP32 CUDA-core peak of a GB300 derived from unit counts and clock:
+# 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--prec", default=None, help="fp32 | mixed_fp16 | mixed_bf16")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------------------------
+def make_workload(name, rank):
+    from paper_1704_08897_gb300 import synth
+    if name == "single":
+        p = synth.single_star_case(1024)
+        return [p], {"workload": "star1024_periodic_extend_in", "grid": "1024x1024",
+                     "instances": 1, "prec": "fp32"}
+    probs = synth.batch_case(256, seed=synth.BASE_SEED + 1000 * rank)
+    nodes = sum(p.nx * p.ny for p in probs)
+    return probs, {"workload": "batch256_sides128-512_wobbly_extend_out", "instances": 256,
+                   "nodes": nodes, "prec": "fp32"}
+
+
+def algorithmic_cost(probs, kind):
+    """(amount, unit) per launch of one kernel kind over the workload's instances."""
+    if kind.startswith("prec_stage"):
+        # stage k contracts one axis: 2 * nx * ny * (length of that axis) flop
+        s = int(kind[-1])
+        fl = 0
+        for p in probs:
+            fl += 2 * p.nx * p.ny * (p.nx if s in (0, 2) else p.ny)
+        return fl, "flop"
+    if kind == "stencil":   # read z, p_old, mask; write p, q
+        return sum(17 * p.nx * p.ny for p in probs), "byte"
+    if kind == "update":    # read xhat(8), p, q, r; write xhat(8), r
+        return sum(32 * p.nx * p.ny for p in probs), "byte"
+    return None, None
+
+
+# ----------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ----------------------------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.tmp = None
+
+    def start(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------------------------
+# our implementation
+# ----------------------------------------------------------------------------------------------
+def kernel_hash(kind):
+    f = "kernels_gemm_simt.cu" if kind.startswith("prec") else "kernels_grid.cu"
+    with open(os.path.join(CSRC, f), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    from paper_1704_08897_gb300 import ext
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+    ext.load()
+    probs, cfg = make_workload(args.workload, rank)
+    prec = args.prec or cfg["prec"]
+    cfg["prec"] = prec
+    stream = torch.cuda.Stream()
+    ctx = ext.ext_create(ext.options(prec, rtol=1e-8), stream=stream)
+    dprobs = [ext.problem_of(p) for p in probs]
+    phis = [torch.from_numpy(p.phi).cuda() for p in probs]
+    fs = [torch.from_numpy(p.f).cuda() for p in probs]
+    outs = [torch.empty_like(x) for x in phis]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+
+    def step():
+        if len(probs) == 1:
+            r = ext.ext_solve(ctx, dprobs[0], phis[0], fs[0], outs[0])
+            return [r]
+        rc, res = ext.ext_solve_batch(ctx, dprobs, phis, fs, outs)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    launches0 = ext.ext_launch_count(ctx)
+    step_ms, results = [], None
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        results = step()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    launches = ext.ext_launch_count(ctx) - launches0
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+        torch.distributed.barrier()
+    solves = len(probs) * args.steps * world
+    value = solves / (total_ms / 1e3)
+    iters = [r["iters"] for r in results]
+    nodes = sum(p.nx * p.ny for p in probs)
+    pt_its = sum(p.nx * p.ny * r["iters"] for p, r in zip(probs, results))
+
+    # end to end through the public API with host (pinned) buffers
+    e2e = None
+    if not args.no_e2e:
+        hphis = [torch.from_numpy(p.phi).pin_memory() for p in probs]
+        hfs = [torch.from_numpy(p.f).pin_memory() for p in probs]
+        houts = [torch.empty(p.phi.shape, dtype=torch.float32).pin_memory() for p in probs]
+        if len(probs) == 1:
+            ext.ext_solve(ctx, dprobs[0], hphis[0], hfs[0], houts[0])
+        else:
+            ext.ext_solve_batch(ctx, dprobs, hphis, hfs, houts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            if len(probs) == 1:
+                ext.ext_solve(ctx, dprobs[0], hphis[0], hfs[0], houts[0])
+            else:
+                ext.ext_solve_batch(ctx, dprobs, hphis, hfs, houts)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        e2e = {"value": len(probs) * args.steps * world / el, "unit": "solves/s",
+               "h2d_bytes_per_step": sum(8 * p.nx * p.ny for p in probs),
+               "d2h_bytes_per_step": sum(4 * p.nx * p.ny for p in probs)}
+
+    # per-kernel CUDA-event durations of the same workload (a profiled pass: no graphs)
+    roofline, kernels = None, None
+    if not args.no_profile and rank == 0:
+        pctx = ext.ext_create(ext.options(prec, rtol=1e-8, profile=1), stream=stream)
+        if len(probs) == 1:
+            ext.ext_solve(pctx, dprobs[0], phis[0], fs[0], outs[0])
+        else:
+            ext.ext_solve_batch(pctx, dprobs, phis, fs, outs)
+        prof = ext.ext_profile_read(pctx)
+        ext.ext_destroy(pctx)
+        tot = sum(ms for ms, n in prof.values())
+        kernels = {k: {"ms_total": round(ms, 3), "launches": n, "share": round(ms / tot, 4) if tot else 0,
+                       "us_per_launch": round(1e3 * ms / n, 3) if n else None}
+                   for k, (ms, n) in prof.items() if n}
+        dom = max(prof, key=lambda k: prof[k][0])
+        ms, n = prof[dom]
+        amount, unit = algorithmic_cost(probs, dom)
+        if amount is not None and n:
+            per_launch_s = ms / n / 1e3
+            if unit == "flop":
+                achieved = amount / per_launch_s / 1e12
+                peak, bound, u = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s"
+                peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
+            else:
+                achieved = amount / per_launch_s / 1e9
+                with open(PEAKS_FILE) as fh:
+                    peak = json.load(fh)["hbm_gbs"]
+                bound, u, peak_src = "hbm", "GB/s", "measured hbm_gbs"
+            traffic = None
+            if os.path.exists(TRAFFIC_FILE):
+                with open(TRAFFIC_FILE) as fh:
+                    tr = json.load(fh)
+                ent = tr.get(f"{dom}:{cfg['workload']}")
+                if ent and ent.get("source_hash") == kernel_hash(dom):
+                    traffic = ent.get("bytes_per_launch")
+            roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3),
+                        "peak": round(peak, 3), "unit": u, "frac": round(achieved / peak, 4),
+                        "traffic": traffic, "peak_source": peak_src,
+                        "algorithmic_per_launch": amount, "algorithmic_unit": unit}
+
+    ext.ext_destroy(ctx)
+    out = {"metric": "extension solves/s at rel-res 1e-8", "value": round(value, 4),
+           "unit": "solves/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+           "data": "synthetic (seeded; paper-shaped interfaces and fields)",
+           "config": dict(cfg, l2="flushed between steps (256 MiB write)",
+                          parallelism="replicas" if world > 1 else "single"),
+           "iterations": iters if len(iters) <= 4 else
+           {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},
+           "grid_point_iterations_per_s": round(pt_its * args.steps * world / (total_ms / 1e3), 1),
+           "relres_true_max": max(r["relres_true"] for r in results),
+           "e2e": e2e, "roofline": roofline, "kernels": kernels,
+           "gpu_launches": launches, "clocks": clk}
+    return out, probs
+
+
+def oracle_solve(p):
+    import numpy as np
+
+    from oracle import biharmonic as ob
+    return ob.extend(p.phi.astype(np.float64), p.f.astype(np.float64), p.direction, p.bc_x,
+                     p.bc_y, p.hx, p.hy, method="direct")
+
+
+def cpu_baseline(args, probs, budget_s=30.0):
+    """The oracle, as it stands, on a bounded sample of the workload (whole problems only)."""
+    t0 = time.perf_counter()
+    done = 0
+    for p in probs:
+        oracle_solve(p)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    el = time.perf_counter() - t0
+    return {"value": round(done / el, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {len(probs)} problem(s) of the workload solved completely by the "
+                      f"FP64 oracle (sparse assembly + SuperLU), {el:.1f} s",
+            "host_cores_available": os.cpu_count()}
+
+
+def run_reference(args, rank, world):
+    probs, cfg = make_workload(args.workload, rank)
+    sample = probs[:1] if len(probs) == 1 else probs[:4]
+    for _ in range(args.warmup):
+        oracle_solve(sample[0])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for p in sample:
+            oracle_solve(p)
+    el = time.perf_counter() - t0
+    value = len(sample) * args.steps / el
+    return {"impl": "reference", "metric": "extension solves/s at rel-res 1e-8",
+            "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * el / args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded; paper-shaped interfaces and fields)",
+            "config": dict(cfg, sample=f"{len(sample)} problem(s) per step"),
+            "cpu_baseline": {"value": round(value, 5), "unit": "solves/s", "cores": 1,
+                             "kind": "oracle",
+                             "sample": f"{len(sample)} complete oracle solve(s) per step"},
+            "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)))
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        dist.init_process_group("nccl")
+    out, probs = run_ours(args, rank, world)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args, probs)
+        print(json.dumps(out))
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,200 @@
+/*
+ * biharm_ext.h -- C ABI of the GB300 biharmonic field extension library (libbiharm_ext.so).
+ *
+ * The library extends a field f, known on the part Omega of a rectangular grid picked by the sign
+ * of a level set function phi, to the whole grid by solving the masked discrete biharmonic
+ * equation (Moroney, Lusmore, McCue, McElwain, "Extending fields in a level set method by solving
+ * a biharmonic equation", arXiv 1704.08897):
+ *
+ *   - Sec. 2.1, eq. (discrete_biharmonic): at every unknown node the 13-point stencil
+ *     20 f_ij - 8 (edge neighbours) + 2 (diagonals) + (nodes at distance 2) = 0, with the values
+ *     at known nodes acting as data; stencils at the domain edge use ghost nodes set by the
+ *     boundary rule of each axis.
+ *   - Sec. 2.2, Algorithm 1: the system is solved by conjugate gradients with the fast Poisson
+ *     solve on the whole rectangle (zero-augmentation of D\Omega into D, separable transforms,
+ *     division by the squared eigenvalue sums) as the preconditioner.
+ *
+ * Layout: every grid array is row-major [ny][nx] (x contiguous), float32.
+ * Pointers: phi, f and out may be device pointers or host pointers (pageable or pinned); host
+ * arrays are copied in and out on the context's stream inside the call.
+ * Ownership: the caller owns phi, f and out and keeps them alive until ext_solve / ext_solve_batch
+ * returns, or until ext_poll reports a final status for a submitted request.  The library owns
+ * every workspace, transform plan and CG state.  out may alias f.
+ * Errors: every entry point returns EXT_OK (0), EXT_PENDING (1) or a negative EXT_E* code;
+ * ext_strerror() names it.  No entry point aborts the process or traps on the GPU.
+ */
+#ifndef BIHARM_EXT_H
+#define BIHARM_EXT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Boundary rule of one axis.  SYMMETRIC is the Neumann case of Example 1 (half-sample reflection,
+ * cosine transform); PERIODIC wraps around (Examples 2 and 4, Fourier transform); DIRICHLET is
+ * Algorithm 1's padding (f = 0 and lap f = 0 on the boundary, sine transform). */
+typedef enum { EXT_BC_SYMMETRIC = 0, EXT_BC_PERIODIC = 1, EXT_BC_DIRICHLET = 2 } ext_bc;
+
+/* Fig. 1: extend out = field known inside the interface (phi < 0); extend in = field known
+ * outside (phi > 0).  phi == 0 is an unknown node in both directions. */
+typedef enum { EXT_EXTEND_OUT = 0, EXT_EXTEND_IN = 1 } ext_dir;
+
+/* Arithmetic of the iteration.  In every mode the CG inner products are FP64, the iterate x is
+ * updated in FP64 every iteration, and the recursive residual is replaced by the FP64 true
+ * residual b - A x whenever it has fallen by replace_factor since the last replacement, at
+ * least every true_res_every iterations, and before convergence is declared.
+ *   FP32        : FP32 vectors, compensated FP32 stencil, FP32 CUDA-core transform products.
+ *   MIXED_FP16  : as FP32, transforms on the tcgen05 tensor cores from FP16 hi/lo operand splits
+ *                 with FP32 accumulation (flexible CG).
+ *   MIXED_BF16  : as MIXED_FP16 with BF16 hi/mid/lo operand splits.                          */
+typedef enum {
+  EXT_PREC_FP32 = 1,
+  EXT_PREC_MIXED_BF16 = 2,
+  EXT_PREC_MIXED_FP16 = 3
+} ext_prec;
+
+typedef struct {
+  int32_t nx, ny;      /* grid nodes along x (contiguous) and y; each >= 4                     */
+  double hx, hy;       /* node spacings (> 0); only hx/hy matters, the solution is scale-free  */
+  int32_t bc_x, bc_y;  /* ext_bc of each axis                                                  */
+  int32_t dir;         /* ext_dir                                                              */
+} ext_problem;
+
+typedef struct {
+  int32_t prec;            /* ext_prec; default EXT_PREC_FP32                                  */
+  double rtol;             /* relative residual target ||b - A x|| / ||b||; default 1e-8       */
+  int32_t maxit;           /* iteration cap; 0 = 10 * max(nx, ny)                              */
+  int32_t true_res_every;  /* longest run of iterations between residual replacements; 200     */
+  double replace_factor;   /* replace once ||r|| < replace_factor * ||r at last replacement||;
+                              default 1e-2                                                     */
+  int32_t iters_per_launch;/* CG iterations per CUDA-graph replay; default 10                 */
+  size_t hbm_budget;       /* bytes the serving queue may hold for admitted requests; 0 = 50%
+                              of free device memory at ext_create                             */
+  int32_t flexible;        /* 1 = flexible (Polak-Ribiere) beta, 0 = Fletcher-Reeves beta;
+                              default 1 (required for the mixed modes)                        */
+  int32_t max_slots;       /* serving: most requests in flight at once; default 256            */
+  int32_t profile;         /* 1: launch every kernel directly (no CUDA graphs) and time each one
+                              with CUDA events on the context stream (ext_profile_read); 0    */
+} ext_options;
+
+/* Kernel kinds reported by ext_profile_read. */
+enum {
+  EXT_KERNEL_SETUP = 0,          /* mask, right-hand side, CG state                          */
+  EXT_KERNEL_STENCIL = 1,        /* p = z + beta p, q = M L^2 p, p.q                         */
+  EXT_KERNEL_UPDATE = 2,         /* x += alpha p, r -= alpha q, r.r                          */
+  EXT_KERNEL_TRUE_RESIDUAL = 3,  /* FP64 b - A x and residual replacement                    */
+  EXT_KERNEL_PREC0 = 4,          /* transform stages 0..3 of the fast Poisson preconditioner */
+  EXT_KERNEL_PREC1 = 5,
+  EXT_KERNEL_PREC2 = 6,
+  EXT_KERNEL_PREC3 = 7,
+  EXT_KERNEL_OUTPUT = 8,         /* out = f on Omega, x elsewhere                            */
+  EXT_KERNEL_KINDS = 9
+};
+
+typedef struct {
+  int32_t status;      /* EXT_OK, EXT_ENOTCONV, EXT_EBREAKDOWN, ...                            */
+  int32_t iters;       /* CG iterations taken                                                  */
+  double relres_true;  /* FP64 ||b - A x|| / ||b|| of the returned x, recomputed on the GPU     */
+  double relres_rec;   /* the recursively updated residual at exit                            */
+  int32_t n_unknown;   /* |D \ Omega|                                                          */
+  int32_t n_known;     /* |Omega|                                                              */
+  double ms_queue;     /* serving: submit -> admission                                         */
+  double ms_solve;     /* admission (or call start) -> result written                          */
+} ext_result;
+
+enum {
+  EXT_OK = 0,
+  EXT_PENDING = 1,
+  EXT_EINVAL = -1,      /* bad size, spacing, enum, null pointer or NaN in phi                 */
+  EXT_ENOKNOWN = -2,    /* no known node and no Dirichlet axis: solution not unique           */
+  EXT_ENOMEM = -3,      /* device allocation failed                                            */
+  EXT_EADMIT = -4,      /* request footprint exceeds the serving HBM budget                    */
+  EXT_ENOTCONV = -5,    /* maxit reached; out holds the best iterate                           */
+  EXT_EBREAKDOWN = -6,  /* p.Ap <= 0 or a non-finite scalar in CG                              */
+  EXT_ETIMEOUT = -7,    /* a bounded device wait ran out                                       */
+  EXT_ECUDA = -8,       /* a CUDA runtime call failed                                          */
+  EXT_ENOTSUP = -9,     /* mode not available on this device                                   */
+  EXT_ENOTFOUND = -10   /* unknown serving ticket                                              */
+};
+
+typedef struct ext_ctx ext_ctx;
+
+/* Fill *opt with the defaults listed above. */
+void ext_options_default(ext_options* opt);
+
+/* Create a context bound to the current CUDA device and to cuda_stream (a cudaStream_t; NULL =
+ * a stream the context creates).  opt may be NULL (defaults).  Returns EXT_ENOTSUP when the
+ * mixed modes are requested on a device without tcgen05 (compute capability 10.x). */
+int ext_create(const ext_options* opt, void* cuda_stream, ext_ctx** out);
+
+/* One extension (Sec. 2.1 problem, Algorithm 1 solve): out = f at known nodes (bit copy),
+ * the PCG solution at unknown nodes.  Blocks until the result is in out.  res may be NULL. */
+int ext_solve(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
+              float* out, ext_result* res);
+
+/* count independent extensions of possibly different sizes solved together: every CG stage is
+ * one launch over all still-iterating problems, iterations are replayed from CUDA graphs.
+ * Each result equals what ext_solve gives for that problem alone, within the stated tolerance. */
+int ext_solve_batch(ext_ctx* ctx, int count, const ext_problem* probs, const float* const* phi,
+                    const float* const* f, float* const* out, ext_result* results);
+
+/* Serving: enqueue one request (returns at once with a ticket).  A device-resident loop admits
+ * queued requests as slots and HBM free up (continuous batching: new requests join the
+ * iterations of those already running).  Thread-safe. */
+int ext_submit(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
+               float* out, uint64_t* ticket);
+
+/* EXT_PENDING while the request is queued or running, else its final status (and *res). */
+int ext_poll(ext_ctx* ctx, uint64_t ticket, ext_result* res);
+
+/* Block until every submitted request has finished. */
+int ext_drain(ext_ctx* ctx);
+
+/* Release every resource of the context (waits for in-flight work). */
+void ext_destroy(ext_ctx* ctx);
+
+const char* ext_strerror(int code);
+
+/* Accumulated CUDA-event time (ms) and launch count of each kernel kind since the last reset,
+ * recorded only by contexts created with profile = 1.  Arrays hold `kinds` entries; either may be
+ * NULL.  reset != 0 clears the totals after reading. */
+int ext_profile_read(ext_ctx* ctx, int kinds, double* total_ms, int64_t* launches, int reset);
+
+/* Number of kernels this context has launched (graph replays count every kernel node). */
+int64_t ext_launch_count(ext_ctx* ctx);
+
+/* Text of the last CUDA or allocation failure seen by the calling thread ("" if none). */
+const char* ext_last_error(void);
+
+/* ---- single stages of the path, for verification (device pointers, [ny][nx] float32) ---- */
+
+/* As ext_solve, but writes the FP64 iterate (device pointer): out64 = f at known nodes, x at
+ * unknown nodes, so a caller can recompute ||b - A x|| / ||b|| exactly (the FP32 out of
+ * ext_solve cannot carry a relative residual of 1e-8 for this ill-conditioned operator). */
+int ext_solve_f64(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
+                  double* out64, ext_result* res);
+
+/* q = M L^2 p on the full grid (eq. discrete_biharmonic with the boundary rules), M zeroing the
+ * known nodes picked by phi; p must be zero at known nodes for this to be A p (Algorithm 1,
+ * matvec).  Uses the same compensated kernel as the solver.  sum_pq (host, may be NULL)
+ * receives the FP64 dot p.q. */
+int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi,
+                         const float* p, float* q, double* sum_pq);
+
+/* b = -M L^2 (f at known nodes, zero elsewhere), in FP64 (Algorithm 1, right-hand side). */
+int ext_rhs(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f, double* b);
+
+/* z = M (L^2)^+ M r on the full grid with the context's precision (Algorithm 1, fast_poisson,
+ * pseudo-inverse when both axes are symmetric/periodic); r must be zero at known nodes.
+ * The result is scale-free: z is (L^2)^+ r times a positive constant reported in *scale
+ * (may be NULL), since CG does not depend on the preconditioner's scale. */
+int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float* phi,
+                             const float* r, float* z, double* scale);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIHARM_EXT_H */

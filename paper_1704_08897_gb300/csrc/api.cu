@@ -1,0 +1,867 @@
+// C ABI of the biharmonic extension library: contexts, transform plans, solve workspaces and
+// the host loop that replays CUDA-graph-captured blocks of PCG iterations.
+//
+// One solve (Algorithm 1): set-up kernel (mask from sign(phi), b = -M L^2 E_K f), one
+// preconditioner pass, then graph replays of G iterations
+//   [stencil (p = z + beta p, q = M L^2 p, p.q) -> update (x += alpha p in FP64, r, r.r) ->
+//    4 transform stages (z = M (L^2)^+ M r, r.z, z.q)] x G  +  tail [FP64 true residual for slots
+//    due a replacement -> 4 transform stages for slots that continue]
+// until every slot reports a final status.  Batches and the serving loop use the same kernels
+// over work lists that span all slots.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/biharm_ext.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace bx;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+#define BX_CUDA(call)                                                                        \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      g_last_error = std::string(#call) + ": " + cudaGetErrorString(e_);                     \
+      return EXT_ECUDA;                                                                      \
+    }                                                                                        \
+  } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct PlanDev {
+  int n = 0, np = 0, bc = 0;
+  float* q = nullptr;   // [np][np]
+  float* qt = nullptr;  // [np][np]
+  std::vector<double> lam;
+  void* tc = nullptr;   // tensor-core operand planes (kernels_gemm_tc.cu)
+};
+
+// One problem's device state inside a workspace.
+struct SlotHost {
+  ext_problem prob{};
+  SlotDesc d{};
+  char* arena = nullptr;
+  size_t bytes = 0;
+  float* phi_stage = nullptr;  // device copies when the caller passes host arrays
+  float* f_stage = nullptr;
+  float* out_stage = nullptr;
+};
+
+struct Workspace {
+  std::string key;
+  std::vector<SlotHost> slots;
+  SlotDesc* d_slots = nullptr;
+  SlotScalars* d_sc = nullptr;
+  SlotScalars* h_sc = nullptr;  // pinned
+  WorkItem *d_st = nullptr, *d_vec = nullptr, *d_gm = nullptr;
+  int *d_counts = nullptr;      // [0] stencil items, [1] vector items, [2] gemm items
+  int n_st = 0, n_vec = 0, n_gm = 0;
+  const float** d_phis = nullptr;
+  const float** d_fs = nullptr;
+  float** d_outs = nullptr;
+  int* d_dirs = nullptr;
+  void* h_ptrs = nullptr;       // pinned staging for the pointer arrays
+  cudaGraphExec_t graph = nullptr;
+  int graph_iters = 0;
+  int64_t graph_nodes = 0;
+  bool aniso = false;
+  bool host_io = false;
+};
+
+int plan_key(int n, int bc) { return n * 4 + bc; }
+
+}  // namespace
+
+struct ext_ctx {
+  int device = 0;
+  int sm_count = 148;
+  int cc_major = 0, cc_minor = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  ext_options opt{};
+  std::map<int, PlanDev> plans;
+  std::map<std::string, Workspace*> ws;
+  std::mutex api_mu;  // serialises ext_solve* and the serving worker on the stream
+  // launch accounting and optional per-kernel timing (ext_options.profile)
+  int64_t launches = 0;
+  struct Pending { int kind; cudaEvent_t a, b; };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> ev_pool;
+  double prof_ms[EXT_KERNEL_KINDS] = {0};
+  int64_t prof_n[EXT_KERNEL_KINDS] = {0};
+  // serving
+  struct Serve;
+  Serve* serve = nullptr;
+};
+
+// ---------------------------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------------------------
+static int validate(const ext_problem* p) {
+  if (!p) return EXT_EINVAL;
+  if (p->nx < 4 || p->ny < 4) return EXT_EINVAL;
+  if ((int64_t)p->nx * p->ny > (int64_t)1 << 30) return EXT_EINVAL;
+  if (!(p->hx > 0.0) || !(p->hy > 0.0) || !std::isfinite(p->hx) || !std::isfinite(p->hy))
+    return EXT_EINVAL;
+  if (p->bc_x < 0 || p->bc_x > 2 || p->bc_y < 0 || p->bc_y > 2) return EXT_EINVAL;
+  if (p->dir != 0 && p->dir != 1) return EXT_EINVAL;
+  return EXT_OK;
+}
+
+static bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {
+  const int key = plan_key(n, bc);
+  auto it = ctx->plans.find(key);
+  if (it != ctx->plans.end()) {
+    *out = &it->second;
+    return EXT_OK;
+  }
+  AxisBasis B = make_axis_basis(n, bc);
+  PlanDev P;
+  P.n = n;
+  P.bc = bc;
+  P.np = pad_to(n, kPad);
+  P.lam = B.lam;
+  std::vector<float> q, qt;
+  padded_f32(B, P.np, q, qt);
+  const size_t bytes = (size_t)P.np * P.np * sizeof(float);
+  if (cudaMalloc(&P.q, bytes) != cudaSuccess || cudaMalloc(&P.qt, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "cudaMalloc of transform plan failed";
+    return EXT_ENOMEM;
+  }
+  BX_CUDA(cudaMemcpy(P.q, q.data(), bytes, cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(P.qt, qt.data(), bytes, cudaMemcpyHostToDevice));
+  auto res = ctx->plans.emplace(key, std::move(P));
+  *out = &res.first->second;
+  return EXT_OK;
+}
+
+// Stencil weights of (L_y (+) L_x)^2 scaled by 1/max(a, c)^2, a = 1/hx^2, c = 1/hy^2
+// (eq. discrete_biharmonic for hx = hy: 20, -8, 2, 1).
+static void set_weights(SlotDesc& d, double hx, double hy) {
+  double a = 1.0 / (hx * hx), c = 1.0 / (hy * hy);
+  const double m = std::max(a, c);
+  a /= m;
+  c /= m;
+  const double w[6] = {6 * a * a + 8 * a * c + 6 * c * c, -4 * a * a - 4 * a * c,
+                       -4 * c * c - 4 * a * c, 2 * a * c, a * a, c * c};
+  float* hi[6] = {&d.wc, &d.wex, &d.wey, &d.wd, &d.wfx, &d.wfy};
+  float* lo[6] = {&d.wc_l, &d.wex_l, &d.wey_l, &d.wd_l, &d.wfx_l, &d.wfy_l};
+  double* dw[6] = {&d.dwc, &d.dwex, &d.dwey, &d.dwd, &d.dwfx, &d.dwfy};
+  for (int i = 0; i < 6; ++i) {
+    *hi[i] = (float)w[i];
+    *lo[i] = (float)(w[i] - (double)*hi[i]);
+    *dw[i] = w[i];
+  }
+  d.aniso = (a != c) ? 1 : 0;
+}
+
+static void free_workspace(Workspace* W) {
+  if (!W) return;
+  if (W->graph) cudaGraphExecDestroy(W->graph);
+  for (auto& s : W->slots) cudaFree(s.arena);
+  cudaFree(W->d_slots);
+  cudaFree(W->d_sc);
+  cudaFree(W->d_st);
+  cudaFree(W->d_vec);
+  cudaFree(W->d_gm);
+  cudaFree(W->d_counts);
+  cudaFree(W->d_phis);
+  cudaFree(W->d_fs);
+  cudaFree(W->d_outs);
+  cudaFree(W->d_dirs);
+  cudaFreeHost(W->h_sc);
+  cudaFreeHost(W->h_ptrs);
+  delete W;
+}
+
+static std::string shape_key(int count, const ext_problem* probs, bool host_io) {
+  std::string k = host_io ? "H" : "D";
+  char buf[160];
+  for (int i = 0; i < count; ++i) {
+    const ext_problem& p = probs[i];
+    snprintf(buf, sizeof(buf), "|%d,%d,%d,%d,%.17g", p.nx, p.ny, p.bc_x, p.bc_y, p.hx / p.hy);
+    k += buf;
+  }
+  return k;
+}
+
+// Build the device state of `count` problems (no inputs yet).
+static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bool host_io,
+                           Workspace** out) {
+  std::unique_ptr<Workspace> W(new Workspace());
+  W->key = shape_key(count, probs, host_io);
+  W->host_io = host_io;
+  W->slots.resize(count);
+  std::vector<WorkItem> st, vec, gm;
+  for (int i = 0; i < count; ++i) {
+    SlotHost& s = W->slots[i];
+    s.prob = probs[i];
+    const int nx = probs[i].nx, ny = probs[i].ny;
+    PlanDev *px, *py;
+    int rc = get_plan(ctx, nx, probs[i].bc_x, &px);
+    if (rc) return rc;
+    rc = get_plan(ctx, ny, probs[i].bc_y, &py);
+    if (rc) return rc;
+    SlotDesc& d = s.d;
+    d.nx = nx;
+    d.ny = ny;
+    d.nxp = px->np;
+    d.nyp = py->np;
+    d.bcx = probs[i].bc_x;
+    d.bcy = probs[i].bc_y;
+    d.n_st_tiles = ((nx + kStTileX - 1) / kStTileX) * ((ny + kStTileY - 1) / kStTileY);
+    const size_t N = (size_t)nx * ny;
+    d.n_vec_items = (int)((N + kVecChunk - 1) / kVecChunk);
+    const int n_gm = (d.nxp / 128) * (d.nyp / 64);
+    d.n_gm_tiles = n_gm;
+    set_weights(d, probs[i].hx, probs[i].hy);
+    if (d.aniso) W->aniso = true;
+    const int n_part = std::max(d.n_st_tiles, std::max(d.n_vec_items, n_gm));
+    const size_t Np = (size_t)d.nxp * d.nyp;
+    // arena layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+    const size_t o_b = take(8 * N), o_x = take(8 * N), o_part = take(8 * 4 * (size_t)n_part);
+    const size_t o_r = take(4 * N), o_p0 = take(4 * N), o_p1 = take(4 * N);
+    const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
+    const size_t o_t1 = take(4 * Np), o_t2 = take(4 * Np), o_t3 = take(4 * Np);
+    const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
+    size_t o_io = 0;
+    if (host_io) o_io = take(12 * N);
+    s.bytes = off;
+    if (cudaMalloc(&s.arena, s.bytes) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
+      g_last_error = "cudaMalloc of solve workspace failed";
+      return EXT_ENOMEM;
+    }
+    char* A = s.arena;
+    d.b = (double*)(A + o_b);
+    d.xhat = (double*)(A + o_x);
+    d.part = (double*)(A + o_part);
+    d.r = (float*)(A + o_r);
+    d.p[0] = (float*)(A + o_p0);
+    d.p[1] = (float*)(A + o_p1);
+    d.q = (float*)(A + o_q);
+    d.z = (float*)(A + o_z);
+    d.mask = (uint8_t*)(A + o_mask);
+    d.t1 = (float*)(A + o_t1);
+    d.t2 = (float*)(A + o_t2);
+    d.t3 = (float*)(A + o_t3);
+    d.rin = nullptr;
+    d.qx = px->q;
+    d.qxt = px->qt;
+    d.qy = py->q;
+    d.qyt = py->qt;
+    if (host_io) {
+      s.phi_stage = (float*)(A + o_io);
+      s.f_stage = s.phi_stage + N;
+      s.out_stage = s.f_stage + N;
+    }
+    // eigenvalues of L_x, L_y scaled like the stencil weights, and the weight normaliser
+    double a = 1.0 / (probs[i].hx * probs[i].hx), c = 1.0 / (probs[i].hy * probs[i].hy);
+    const double m = std::max(a, c);
+    a /= m;
+    c /= m;
+    std::vector<float> lx(d.nxp, 0.f), ly(d.nyp, 0.f);
+    for (int k = 0; k < nx; ++k) lx[k] = (float)(px->lam[k] * a);
+    for (int k = 0; k < ny; ++k) ly[k] = (float)(py->lam[k] * c);
+    double smin;
+    // smallest nonzero eigenvalue sum: min over the two axes' smallest entries
+    double mx0 = 1e300, mx1 = 1e300, my0 = 1e300, my1 = 1e300;  // smallest, smallest nonzero
+    for (int k = 0; k < nx; ++k) {
+      const double v = (float)(px->lam[k] * a);
+      mx0 = std::min(mx0, v);
+      if (v > 0) mx1 = std::min(mx1, v);
+    }
+    for (int k = 0; k < ny; ++k) {
+      const double v = (float)(py->lam[k] * c);
+      my0 = std::min(my0, v);
+      if (v > 0) my1 = std::min(my1, v);
+    }
+    smin = mx0 + my0;
+    if (!(smin > 0)) smin = std::min(mx0 + my1, mx1 + my0);
+    d.wnorm = (float)(smin * smin);
+    d.zero_mode = (probs[i].bc_x != EXT_BC_DIRICHLET && probs[i].bc_y != EXT_BC_DIRICHLET);
+    d.lamx = (const float*)(A + o_lx);
+    d.lamy = (const float*)(A + o_ly);
+    BX_CUDA(cudaMemcpy(A + o_lx, lx.data(), 4 * lx.size(), cudaMemcpyHostToDevice));
+    BX_CUDA(cudaMemcpy(A + o_ly, ly.data(), 4 * ly.size(), cudaMemcpyHostToDevice));
+    for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
+    for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
+    for (int t = 0; t < n_gm; ++t) gm.push_back({i, t});
+  }
+  W->n_st = (int)st.size();
+  W->n_vec = (int)vec.size();
+  W->n_gm = (int)gm.size();
+  BX_CUDA(cudaMalloc(&W->d_sc, sizeof(SlotScalars) * count));
+  BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * count));
+  BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * count));
+  for (int i = 0; i < count; ++i) W->slots[i].d.sc = W->d_sc + i;
+  std::vector<SlotDesc> descs(count);
+  for (int i = 0; i < count; ++i) descs[i] = W->slots[i].d;
+  BX_CUDA(cudaMalloc(&W->d_slots, sizeof(SlotDesc) * count));
+  BX_CUDA(cudaMemcpy(W->d_slots, descs.data(), sizeof(SlotDesc) * count, cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMalloc(&W->d_st, sizeof(WorkItem) * st.size()));
+  BX_CUDA(cudaMalloc(&W->d_vec, sizeof(WorkItem) * vec.size()));
+  BX_CUDA(cudaMalloc(&W->d_gm, sizeof(WorkItem) * gm.size()));
+  BX_CUDA(cudaMemcpy(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice));
+  int counts[3] = {W->n_st, W->n_vec, W->n_gm};
+  BX_CUDA(cudaMalloc(&W->d_counts, sizeof(counts)));
+  BX_CUDA(cudaMemcpy(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * count));
+  BX_CUDA(cudaMalloc(&W->d_fs, sizeof(void*) * count));
+  BX_CUDA(cudaMalloc(&W->d_outs, sizeof(void*) * count));
+  BX_CUDA(cudaMalloc(&W->d_dirs, sizeof(int) * count));
+  BX_CUDA(cudaMallocHost(&W->h_ptrs, (3 * sizeof(void*) + sizeof(int)) * count));
+  *out = W.release();
+  return EXT_OK;
+}
+
+static int get_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bool host_io,
+                         Workspace** out) {
+  const std::string key = shape_key(count, probs, host_io);
+  auto it = ctx->ws.find(key);
+  if (it != ctx->ws.end()) {
+    *out = it->second;
+    return EXT_OK;
+  }
+  // keep the cache small: drop everything else when it grows
+  if (ctx->ws.size() >= 8) {
+    cudaStreamSynchronize(ctx->stream);
+    for (auto& kv : ctx->ws) free_workspace(kv.second);
+    ctx->ws.clear();
+  }
+  Workspace* W = nullptr;
+  int rc = build_workspace(ctx, count, probs, host_io, &W);
+  if (rc) return rc;
+  ctx->ws[key] = W;
+  *out = W;
+  return EXT_OK;
+}
+
+static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
+  LaunchCfg c;
+  c.slots = W->d_slots;
+  c.stream = ctx->stream;
+  const int cap = ctx->sm_count * 8;
+  if (which == 0) {
+    c.items = W->d_st;
+    c.n_items = W->d_counts + 0;
+    c.grid = std::max(1, std::min(W->n_st, cap));
+  } else if (which == 1) {
+    c.items = W->d_vec;
+    c.n_items = W->d_counts + 1;
+    c.grid = std::max(1, std::min(W->n_vec, cap));
+  } else {
+    c.items = W->d_gm;
+    c.n_items = W->d_counts + 2;
+    c.grid = std::max(1, std::min(W->n_gm, ctx->sm_count * 2));
+  }
+  return c;
+}
+
+static cudaEvent_t ev_get(ext_ctx* ctx) {
+  if (!ctx->ev_pool.empty()) {
+    cudaEvent_t e = ctx->ev_pool.back();
+    ctx->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch one kernel (fn), counting it; in profiling mode bracket it with CUDA events on the
+// context's stream.  Never used while a graph is being captured with profiling on.
+template <class F>
+static void timed(ext_ctx* ctx, int kind, F&& fn) {
+  ctx->launches += 1;
+  if (!ctx->opt.profile) {
+    fn();
+    return;
+  }
+  cudaEvent_t a = ev_get(ctx), b = ev_get(ctx);
+  cudaEventRecord(a, ctx->stream);
+  fn();
+  cudaEventRecord(b, ctx->stream);
+  ctx->pending.push_back({kind, a, b});
+}
+
+// After a stream synchronisation: fold the recorded event pairs into the per-kind totals.
+static void harvest(ext_ctx* ctx) {
+  for (auto& p : ctx->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->prof_ms[p.kind] += ms;
+      ctx->prof_n[p.kind] += 1;
+    }
+    ctx->ev_pool.push_back(p.a);
+    ctx->ev_pool.push_back(p.b);
+  }
+  ctx->pending.clear();
+  cudaGetLastError();
+}
+
+static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
+  const LaunchCfg g = cfg_of(ctx, W, 2);
+  for (int s = 0; s < 4; ++s) {
+    timed(ctx, EXT_KERNEL_PREC0 + s, [&] {
+      if (ctx->opt.prec == EXT_PREC_FP32) launch_prec_simt(g, s, mode);
+      else launch_prec_tc(g, s, mode, ctx->opt.prec == EXT_PREC_MIXED_FP16 ? 0 : 1);
+    });
+  }
+}
+
+static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
+  const LaunchCfg st = cfg_of(ctx, W, 0), vc = cfg_of(ctx, W, 1);
+  for (int i = 0; i < iters; ++i) {
+    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(st, W->aniso); });
+    timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); });
+    launch_prec(ctx, W, 0);
+  }
+  timed(ctx, EXT_KERNEL_TRUE_RESIDUAL, [&] { launch_true_residual(st); });
+  launch_prec(ctx, W, 1);
+}
+
+static int ensure_graph(ext_ctx* ctx, Workspace* W) {
+  const int G = ctx->opt.iters_per_launch;
+  if (ctx->opt.profile) return EXT_OK;  // profiling launches every kernel directly
+  if (W->graph && W->graph_iters == G) return EXT_OK;
+  if (W->graph) {
+    cudaGraphExecDestroy(W->graph);
+    W->graph = nullptr;
+  }
+  cudaGraph_t g;
+  BX_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = ctx->launches;
+  enqueue_iterations(ctx, W, G);
+  W->graph_nodes = ctx->launches - before;
+  ctx->launches = before;  // captured, not launched
+  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("graph capture: ") + cudaGetErrorString(e);
+    return EXT_ECUDA;
+  }
+  e = cudaGraphInstantiate(&W->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    g_last_error = std::string("graph instantiate: ") + cudaGetErrorString(e);
+    return EXT_ECUDA;
+  }
+  W->graph_iters = G;
+  return EXT_OK;
+}
+
+static int map_status(int st, int n_known, const ext_problem& p) {
+  if (st == ST_OK && n_known == 0 && p.bc_x != EXT_BC_DIRICHLET && p.bc_y != EXT_BC_DIRICHLET)
+    return EXT_ENOKNOWN;
+  return st;
+}
+
+// Full solve of the slots of W (inputs already bound); writes outputs and results.
+static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const float* const* fs,
+                     float* const* outs, const int* dirs, ext_result* results,
+                     double* out64 = nullptr) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int count = (int)W->slots.size();
+  cudaStream_t s = ctx->stream;
+  // bind inputs (staging host arrays when needed)
+  char* hp = (char*)W->h_ptrs;
+  const float** h_phis = (const float**)hp;
+  const float** h_fs = h_phis + count;
+  float** h_outs = (float**)(h_fs + count);
+  int* h_dirs = (int*)(h_outs + count);
+  for (int i = 0; i < count; ++i) {
+    SlotHost& sl = W->slots[i];
+    const size_t N = (size_t)sl.prob.nx * sl.prob.ny;
+    if (W->host_io) {
+      BX_CUDA(cudaMemcpyAsync(sl.phi_stage, phis[i], 4 * N, cudaMemcpyHostToDevice, s));
+      BX_CUDA(cudaMemcpyAsync(sl.f_stage, fs[i], 4 * N, cudaMemcpyHostToDevice, s));
+      h_phis[i] = sl.phi_stage;
+      h_fs[i] = sl.f_stage;
+      h_outs[i] = sl.out_stage;
+    } else {
+      h_phis[i] = phis[i];
+      h_fs[i] = fs[i];
+      h_outs[i] = outs[i];
+    }
+    h_dirs[i] = dirs[i];
+  }
+  BX_CUDA(cudaMemcpyAsync(W->d_phis, h_phis, sizeof(void*) * count, cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(W->d_fs, h_fs, sizeof(void*) * count, cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(W->d_outs, h_outs, sizeof(void*) * count, cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(W->d_dirs, h_dirs, sizeof(int) * count, cudaMemcpyHostToDevice, s));
+  // scalars: parameters and zero counters
+  for (int i = 0; i < count; ++i) {
+    SlotScalars& sc = W->h_sc[i];
+    memset(&sc, 0, sizeof(sc));
+    const ext_problem& p = W->slots[i].prob;
+    sc.rtol2 = ctx->opt.rtol * ctx->opt.rtol;
+    sc.maxit = ctx->opt.maxit > 0 ? ctx->opt.maxit : 10 * std::max(p.nx, p.ny);
+    sc.fold_every = ctx->opt.true_res_every;
+    sc.delta2 = ctx->opt.replace_factor * ctx->opt.replace_factor;
+    sc.flexible = ctx->opt.flexible;
+    sc.pscale = 1.f;
+    sc.status = ST_RUNNING;
+  }
+  BX_CUDA(cudaMemcpyAsync(W->d_sc, W->h_sc, sizeof(SlotScalars) * count, cudaMemcpyHostToDevice, s));
+  int rc = ensure_graph(ctx, W);
+  if (rc) return rc;
+  timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(cfg_of(ctx, W, 0), W->d_phis, W->d_fs, W->d_dirs); });
+  launch_prec(ctx, W, 1);
+  BX_CUDA(cudaGetLastError());
+  int max_blocks = 0;
+  for (int i = 0; i < count; ++i) {
+    const ext_problem& p = W->slots[i].prob;
+    const int mi = ctx->opt.maxit > 0 ? ctx->opt.maxit : 10 * std::max(p.nx, p.ny);
+    max_blocks = std::max(max_blocks, mi);
+  }
+  max_blocks = max_blocks / std::max(1, W->graph_iters) + 8;
+  for (int blk = 0; blk < max_blocks; ++blk) {
+    if (ctx->opt.profile) {
+      enqueue_iterations(ctx, W, ctx->opt.iters_per_launch);
+    } else {
+      BX_CUDA(cudaGraphLaunch(W->graph, s));
+      ctx->launches += W->graph_nodes;
+    }
+    BX_CUDA(cudaMemcpyAsync(W->h_sc, W->d_sc, sizeof(SlotScalars) * count, cudaMemcpyDeviceToHost, s));
+    BX_CUDA(cudaStreamSynchronize(s));
+    harvest(ctx);
+    bool running = false;
+    for (int i = 0; i < count; ++i)
+      if (W->h_sc[i].status == ST_RUNNING) running = true;
+    if (!running) break;
+  }
+  if (out64) {
+    const SlotHost& sl = W->slots[0];
+    timed(ctx, EXT_KERNEL_OUTPUT, [&] {
+      launch_output64(W->d_slots, sl.prob.nx * sl.prob.ny, W->host_io ? sl.f_stage : fs[0], out64, s);
+    });
+  } else {
+    timed(ctx, EXT_KERNEL_OUTPUT, [&] { launch_output(cfg_of(ctx, W, 1), W->d_fs, W->d_outs); });
+  }
+  BX_CUDA(cudaGetLastError());
+  if (W->host_io && !out64) {
+    for (int i = 0; i < count; ++i) {
+      SlotHost& sl = W->slots[i];
+      const size_t N = (size_t)sl.prob.nx * sl.prob.ny;
+      BX_CUDA(cudaMemcpyAsync(outs[i], sl.out_stage, 4 * N, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  BX_CUDA(cudaStreamSynchronize(s));
+  harvest(ctx);
+  const double ms =
+      std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  int worst = EXT_OK;
+  for (int i = 0; i < count; ++i) {
+    const SlotScalars& sc = W->h_sc[i];
+    const ext_problem& p = W->slots[i].prob;
+    int st = sc.status == ST_RUNNING ? EXT_ETIMEOUT : map_status(sc.status, sc.n_known, p);
+    if (results) {
+      ext_result& r = results[i];
+      r.status = st;
+      r.iters = sc.it;
+      r.relres_true = sc.bb > 0 ? std::sqrt(sc.rr_true / sc.bb) : 0.0;
+      r.relres_rec = sc.bb > 0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
+      r.n_known = sc.n_known;
+      r.n_unknown = p.nx * p.ny - sc.n_known;
+      r.ms_queue = 0.0;
+      r.ms_solve = ms;
+    }
+    if (st != EXT_OK && worst == EXT_OK) worst = st;
+  }
+  return worst;
+}
+
+// ---------------------------------------------------------------------------------------------
+// public API
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+void ext_options_default(ext_options* o) {
+  if (!o) return;
+  memset(o, 0, sizeof(*o));
+  o->prec = EXT_PREC_FP32;
+  o->rtol = 1e-8;
+  o->maxit = 0;
+  o->true_res_every = 200;
+  o->replace_factor = 1e-2;
+  o->iters_per_launch = 10;
+  o->hbm_budget = 0;
+  o->flexible = 1;
+  o->max_slots = 256;
+}
+
+const char* ext_strerror(int code) {
+  switch (code) {
+    case EXT_OK: return "ok";
+    case EXT_PENDING: return "pending";
+    case EXT_EINVAL: return "invalid argument (size, spacing, enum, null pointer or NaN in phi)";
+    case EXT_ENOKNOWN: return "no known node and no Dirichlet edge: extension not unique";
+    case EXT_ENOMEM: return "device allocation failed";
+    case EXT_EADMIT: return "request footprint exceeds the serving HBM budget";
+    case EXT_ENOTCONV: return "not converged within maxit";
+    case EXT_EBREAKDOWN: return "CG breakdown (non-positive curvature or non-finite scalar)";
+    case EXT_ETIMEOUT: return "bounded wait ran out";
+    case EXT_ECUDA: return "CUDA runtime error";
+    case EXT_ENOTSUP: return "not supported on this device";
+    case EXT_ENOTFOUND: return "unknown ticket";
+    default: return "unknown error code";
+  }
+}
+
+const char* ext_last_error(void) { return g_last_error.c_str(); }
+
+int ext_create(const ext_options* opt, void* cuda_stream, ext_ctx** out) {
+  if (!out) return EXT_EINVAL;
+  *out = nullptr;
+  ext_options o;
+  ext_options_default(&o);
+  if (opt) o = *opt;
+  if (o.prec != EXT_PREC_FP32 && o.prec != EXT_PREC_MIXED_BF16 && o.prec != EXT_PREC_MIXED_FP16)
+    return EXT_EINVAL;
+  if (!(o.rtol > 0.0) || o.rtol >= 1.0) return EXT_EINVAL;
+  if (o.iters_per_launch <= 0) o.iters_per_launch = 10;
+  if (o.true_res_every <= 0) o.true_res_every = 200;
+  if (!(o.replace_factor > 0.0) || o.replace_factor >= 1.0) o.replace_factor = 1e-2;
+  // residual replacement happens at graph boundaries: make the period a multiple of G
+  o.true_res_every = (o.true_res_every + o.iters_per_launch - 1) / o.iters_per_launch * o.iters_per_launch;
+  if (o.max_slots <= 0) o.max_slots = 256;
+  std::unique_ptr<ext_ctx> ctx(new ext_ctx());
+  ctx->opt = o;
+  BX_CUDA(cudaGetDevice(&ctx->device));
+  cudaDeviceProp prop;
+  BX_CUDA(cudaGetDeviceProperties(&prop, ctx->device));
+  ctx->sm_count = prop.multiProcessorCount;
+  ctx->cc_major = prop.major;
+  ctx->cc_minor = prop.minor;
+  if (o.prec != EXT_PREC_FP32 && !(prop.major == 10 && tc_supported())) return EXT_ENOTSUP;
+  if (cuda_stream) {
+    ctx->stream = (cudaStream_t)cuda_stream;
+  } else {
+    BX_CUDA(cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking));
+    ctx->own_stream = true;
+  }
+  *out = ctx.release();
+  return EXT_OK;
+}
+
+void ext_serve_shutdown(ext_ctx* ctx);
+
+void ext_destroy(ext_ctx* ctx) {
+  if (!ctx) return;
+  ext_serve_shutdown(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  for (auto& kv : ctx->ws) free_workspace(kv.second);
+  for (auto& kv : ctx->plans) {
+    cudaFree(kv.second.q);
+    cudaFree(kv.second.qt);
+    cudaFree(kv.second.tc);
+  }
+  harvest(ctx);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+int ext_solve_batch(ext_ctx* ctx, int count, const ext_problem* probs, const float* const* phi,
+                    const float* const* f, float* const* out, ext_result* results) {
+  if (!ctx || count <= 0 || !probs || !phi || !f || !out) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  bool any_host = false, any_dev = false;
+  std::vector<int> dirs(count);
+  for (int i = 0; i < count; ++i) {
+    int rc = validate(&probs[i]);
+    if (rc) return rc;
+    if (!phi[i] || !f[i] || !out[i]) return EXT_EINVAL;
+    const bool d = is_device_ptr(phi[i]) && is_device_ptr(f[i]) && is_device_ptr(out[i]);
+    (d ? any_dev : any_host) = true;
+    dirs[i] = probs[i].dir;
+  }
+  if (any_host && any_dev) return EXT_EINVAL;  // one residency per call
+  Workspace* W = nullptr;
+  int rc = get_workspace(ctx, count, probs, any_host, &W);
+  if (rc) return rc;
+  return run_solve(ctx, W, phi, f, out, dirs.data(), results);
+}
+
+int ext_solve(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f, float* out,
+              ext_result* res) {
+  const float* phis[1] = {phi};
+  const float* fs[1] = {f};
+  float* outs[1] = {out};
+  return ext_solve_batch(ctx, 1, prob, phis, fs, outs, res);
+}
+
+int ext_solve_f64(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
+                  double* out64, ext_result* res) {
+  if (!ctx || !prob || !phi || !f || !out64) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  int rc = validate(prob);
+  if (rc) return rc;
+  if (!is_device_ptr(phi) || !is_device_ptr(f) || !is_device_ptr(out64)) return EXT_EINVAL;
+  Workspace* W = nullptr;
+  rc = get_workspace(ctx, 1, prob, false, &W);
+  if (rc) return rc;
+  const float* phis[1] = {phi};
+  const float* fs[1] = {f};
+  float* outs[1] = {nullptr};
+  const int dirs[1] = {prob->dir};
+  return run_solve(ctx, W, phis, fs, outs, dirs, res, out64);
+}
+
+int ext_profile_read(ext_ctx* ctx, int kinds, double* total_ms, int64_t* launches, int reset) {
+  if (!ctx || kinds < 0) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  for (int k = 0; k < kinds && k < EXT_KERNEL_KINDS; ++k) {
+    if (total_ms) total_ms[k] = ctx->prof_ms[k];
+    if (launches) launches[k] = ctx->prof_n[k];
+  }
+  if (reset) {
+    for (int k = 0; k < EXT_KERNEL_KINDS; ++k) {
+      ctx->prof_ms[k] = 0.0;
+      ctx->prof_n[k] = 0;
+    }
+  }
+  return EXT_OK;
+}
+
+int64_t ext_launch_count(ext_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+// ---- verification entry points (device pointers) ----
+
+static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
+                        Workspace** Wout) {
+  int rc = validate(prob);
+  if (rc) return rc;
+  if (!phi || !f) return EXT_EINVAL;
+  Workspace* W = nullptr;
+  rc = get_workspace(ctx, 1, prob, false, &W);
+  if (rc) return rc;
+  cudaStream_t s = ctx->stream;
+  const float** h_phis = (const float**)W->h_ptrs;
+  const float** h_fs = h_phis + 1;
+  int* h_dirs = (int*)(h_fs + 2);
+  h_phis[0] = phi;
+  h_fs[0] = f;
+  h_dirs[0] = prob->dir;
+  BX_CUDA(cudaMemcpyAsync(W->d_phis, h_phis, sizeof(void*), cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(W->d_fs, h_fs, sizeof(void*), cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(W->d_dirs, h_dirs, sizeof(int), cudaMemcpyHostToDevice, s));
+  memset(W->h_sc, 0, sizeof(SlotScalars));
+  W->h_sc[0].rtol2 = ctx->opt.rtol * ctx->opt.rtol;
+  W->h_sc[0].maxit = 1;
+  W->h_sc[0].fold_every = ctx->opt.true_res_every;
+  W->h_sc[0].delta2 = 1e-4;
+  W->h_sc[0].pscale = 1.f;
+  BX_CUDA(cudaMemcpyAsync(W->d_sc, W->h_sc, sizeof(SlotScalars), cudaMemcpyHostToDevice, s));
+  timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(cfg_of(ctx, W, 0), W->d_phis, W->d_fs, W->d_dirs); });
+  BX_CUDA(cudaGetLastError());
+  *Wout = W;
+  return EXT_OK;
+}
+
+int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* p,
+                         float* q, double* sum_pq) {
+  if (!ctx || !p || !q) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  Workspace* W = nullptr;
+  int rc = single_setup(ctx, prob, phi, p, &W);
+  if (rc) return rc;
+  SlotHost& sl = W->slots[0];
+  timed(ctx, EXT_KERNEL_STENCIL, [&] {
+    launch_apply(W->d_slots, sl.d.n_st_tiles, W->aniso, p, q, sl.d.part, ctx->stream);
+  });
+  BX_CUDA(cudaGetLastError());
+  std::vector<double> part(sl.d.n_st_tiles);
+  BX_CUDA(cudaMemcpyAsync(part.data(), sl.d.part, 8 * part.size(), cudaMemcpyDeviceToHost, ctx->stream));
+  BX_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (sum_pq) {
+    double s = 0.0;
+    for (double v : part) s += v;
+    *sum_pq = s;
+  }
+  return EXT_OK;
+}
+
+int ext_rhs(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f, double* b) {
+  if (!ctx || !b) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  Workspace* W = nullptr;
+  int rc = single_setup(ctx, prob, phi, f, &W);
+  if (rc) return rc;
+  const size_t N = (size_t)prob->nx * prob->ny;
+  BX_CUDA(cudaMemcpyAsync(b, W->slots[0].d.b, 8 * N, cudaMemcpyDefault, ctx->stream));
+  BX_CUDA(cudaStreamSynchronize(ctx->stream));
+  return EXT_OK;
+}
+
+int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float* phi,
+                             const float* r, float* z, double* scale) {
+  if (!ctx || !r || !z) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  Workspace* W = nullptr;
+  int rc = single_setup(ctx, prob, phi, r, &W);
+  if (rc) return rc;
+  SlotHost& sl = W->slots[0];
+  const size_t N = (size_t)prob->nx * prob->ny;
+  BX_CUDA(cudaMemcpyAsync(sl.d.r, r, 4 * N, cudaMemcpyDefault, ctx->stream));
+  BX_CUDA(cudaMemsetAsync(sl.d.q, 0, 4 * N, ctx->stream));
+  launch_prec(ctx, W, 2);
+  BX_CUDA(cudaGetLastError());
+  BX_CUDA(cudaMemcpyAsync(z, sl.d.z, 4 * N, cudaMemcpyDefault, ctx->stream));
+  BX_CUDA(cudaStreamSynchronize(ctx->stream));
+  if (scale) {
+    const double a = 1.0 / (prob->hx * prob->hx), c = 1.0 / (prob->hy * prob->hy);
+    const double m = std::max(a, c);
+    *scale = (double)sl.d.wnorm * m * m;
+  }
+  return EXT_OK;
+}
+
+}  // extern "C"
+
+// Serving loop lives in serve.cu; until it is linked these stubs keep the ABI complete.
+extern "C" {
+__attribute__((weak)) int ext_submit(ext_ctx*, const ext_problem*, const float*, const float*,
+                                     float*, uint64_t*) {
+  return EXT_ENOTSUP;
+}
+__attribute__((weak)) int ext_poll(ext_ctx*, uint64_t, ext_result*) { return EXT_ENOTSUP; }
+__attribute__((weak)) int ext_drain(ext_ctx*) { return EXT_OK; }
+__attribute__((weak)) void ext_serve_shutdown(ext_ctx*) {}
+}

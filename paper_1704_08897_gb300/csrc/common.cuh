@@ -1,0 +1,204 @@
+// Shared device-side definitions of the biharmonic extension library.
+//
+// One "slot" is one extension problem being solved; a batch (or the serving loop) is a set of
+// slots.  Every CG stage is one launch over a work list of (slot, tile) items drawn from all
+// iterating slots; per-slot scalars live in device memory and are reduced deterministically by
+// the last work item of the slot to finish (fixed order, no floating-point atomics).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bx {
+
+constexpr int kPad = 128;           // transform buffers are padded to multiples of this
+constexpr int kStTileX = 64;        // stencil tile (x contiguous)
+constexpr int kStTileY = 16;
+constexpr int kStThreads = 256;
+constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels
+constexpr int kVecThreads = 256;
+
+enum Bc : int { BC_SYM = 0, BC_PER = 1, BC_DIR = 2 };
+
+// Status words (match the public EXT_* codes).
+enum : int { ST_OK = 0, ST_RUNNING = 1, ST_ENOTCONV = -5, ST_EBREAKDOWN = -6 };
+
+// Per-slot scalars, FP64 where they feed CG.  Written only by the last work item of a slot.
+struct __align__(16) SlotScalars {
+  double bb;        // ||b||^2
+  double rho;       // r.z of the current z
+  double pq;        // p.Ap of the current direction
+  double zq;        // z_new.q_old (flexible beta)
+  double rr;        // ||r||^2, recursive
+  double rr_true;   // ||b - A xhat||^2 at the last replacement
+  double alpha, beta;
+  double rtol2;     // rtol^2
+  double rr_ref;    // ||r||^2 at the last residual replacement
+  double delta2;    // replace the residual once ||r||^2 < delta2 * rr_ref
+  float pscale;     // power-of-two scale applied to r before the preconditioner
+  int it;           // completed iterations
+  int maxit;
+  int fold_every;   // longest stretch of iterations between residual replacements
+  int active;       // 1 while the slot iterates
+  int fold;         // 1: the tail replaces r by the FP64 true residual b - A xhat
+  int need_prec;    // 1: the tail preconditioner runs (after a replacement that continues)
+  int status;       // ST_RUNNING until final
+  int flexible;
+  unsigned cnt[6];  // completion counters of the last-item reductions, one per kernel kind
+  int n_known;      // known nodes, counted by the set-up kernel
+};
+
+// Static description of one slot (device copy).  Padded transform dims are multiples of kPad.
+struct SlotDesc {
+  int nx, ny, nxp, nyp;
+  int bcx, bcy;
+  int n_st_tiles;    // stencil tiles: ceil(nx/64) * ceil(ny/16)
+  int n_vec_items;   // vector chunks: ceil(nx*ny / kVecChunk)
+  int n_gm_tiles;    // output tiles of one transform stage
+  float wc, wex, wey, wd, wfx, wfy;  // stencil weights (hi), scaled so that max(a, c) = 1
+  float wc_l, wex_l, wey_l, wd_l, wfx_l, wfy_l;  // low parts (anisotropic grids only)
+  double dwc, dwex, dwey, dwd, dwfx, dwfy;       // FP64 weights for the true residual
+  int aniso;
+  // grid vectors [ny][nx]
+  uint8_t* mask;     // 1 = unknown node
+  double* b;
+  double* xhat;      // the iterate, FP64, updated every iteration
+  float* r;
+  float* p[2];
+  float* q;
+  float* z;
+  // transform operands and intermediates, padded [.][.] row-major, float32 (SIMT path)
+  float* rin;        // r scaled, padded [nyp][nxp]
+  float* t1;         // [nxp][nyp]
+  float* t2;         // [nyp][nxp]
+  float* t3;         // [nxp][nyp]
+  const float* qx;   // [nxp][nxp]  Qx[x][k]
+  const float* qxt;  // [nxp][nxp]  Qx^T
+  const float* qy;
+  const float* qyt;
+  const float* lamx; // [nxp] eigenvalues of T_x (scaled), padding entries never read
+  const float* lamy;
+  float wnorm;       // 1 / w_max, so that the scaled weights are <= 1
+  int zero_mode;     // 1: drop the (0,0) mode (both axes symmetric/periodic)
+  SlotScalars* sc;
+  double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
+};
+
+struct WorkItem {
+  int slot;
+  int tile;   // tile / chunk index within the slot
+};
+
+// ------------------------------------------------------------------------------------------
+// Reductions
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of up to two values; result valid in thread 0.  `sh` holds >= 2*32 doubles.
+template <int NT>
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) { sh[w] = a; sh[32 + w] = b; }
+  __syncthreads();
+  if (w == 0) {
+    a = (l < NT / 32) ? sh[l] : 0.0;
+    b = (l < NT / 32) ? sh[32 + l] : 0.0;
+    a = warp_sum(a);
+    b = warp_sum(b);
+  }
+  __syncthreads();
+}
+
+// Last-item protocol, called by every thread of the block after thread 0 has written the item's
+// partials.  Returns true in all threads of the item that completes the slot.
+__device__ __forceinline__ bool last_item_block(unsigned* counter, unsigned total, int* sflag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    const int last = (prev == total - 1) ? 1 : 0;
+    if (last) {
+      __threadfence();
+      *counter = 0u;
+    }
+    *sflag = last;
+  }
+  __syncthreads();
+  return *sflag != 0;
+}
+
+// Sums of partials part[t*4 + k] (k = 0..K-1) over t < n, by the whole block: thread i adds
+// t = i, i + NT, ... in order, then a fixed tree.  The order depends only on n, so the result is
+// the same whichever block runs the reduction.  Results valid in thread 0.
+template <int NT, int K>
+__device__ __forceinline__ void reduce_partials(const double* part, int n, double (&out)[K],
+                                                double* sh) {
+  double acc[3] = {0.0, 0.0, 0.0};
+  for (int t = threadIdx.x; t < n; t += NT) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] += __ldcg(&part[t * 4 + k]);
+  }
+  double a = acc[0], b = K > 1 ? acc[1] : 0.0;
+  block_sum2<NT>(a, b, sh);
+  out[0] = a;
+  if (K > 1) out[1] = b;
+  if (K > 2) {
+    double c = acc[2], d = 0.0;
+    block_sum2<NT>(c, d, sh);
+    out[2] = c;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Error-free transformations in FP32 (Knuth TwoSum, FMA-based TwoProd).  The _rn intrinsics
+// are never contracted into FMAs, which keeps the transformations exact.
+// ------------------------------------------------------------------------------------------
+struct f2 { float hi, lo; };
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated accumulator (Ogita-Rump-Oishi Sum2): s + c carries about twice FP32 precision.
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float e;
+    two_sum(s, x, s, e);
+    c = __fadd_rn(c, e);
+  }
+  // add w*x for an FP32 weight w (exact product split by FMA)
+  __device__ __forceinline__ void add_prod(float w, float x) {
+    const float p = __fmul_rn(w, x);
+    const float pe = __fmaf_rn(w, x, -p);
+    add(p);
+    c = __fadd_rn(c, pe);
+  }
+  __device__ __forceinline__ float result() const { return __fadd_rn(s, c); }
+};
+
+// ------------------------------------------------------------------------------------------
+// Ghost-node maps of one axis (Algorithm 1 padding; symmetric = half-sample reflection;
+// periodic = wrap).  Input index i in [-2, n+1].  Returns the node index and a sign
+// (+1, -1, or 0 for the zero Dirichlet boundary node).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int ghost(int i, int n, int bc, float& sgn) {
+  sgn = 1.f;
+  if (i >= 0 && i < n) return i;
+  if (bc == BC_PER) return i < 0 ? i + n : i - n;
+  if (bc == BC_SYM) return i < 0 ? -1 - i : 2 * n - 1 - i;
+  // Dirichlet: distance 1 is the boundary node (zero), distance 2 the negated first node
+  if (i == -1 || i == n) { sgn = 0.f; return 0; }
+  sgn = -1.f;
+  return i < 0 ? -i - 2 : 2 * n - i;
+}
+
+}  // namespace bx

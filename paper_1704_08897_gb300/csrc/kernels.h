@@ -1,0 +1,39 @@
+// Host-side launchers of the device kernels (internal to the library).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace bx {
+
+struct LaunchCfg {
+  const SlotDesc* slots;   // device array of slot descriptors
+  const WorkItem* items;   // device work list
+  const int* n_items;      // device count of valid items (persistent kernels read it)
+  int grid;
+  cudaStream_t stream;
+};
+
+// grid kernels (kernels_grid.cu)
+void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
+                  const int* dirs);
+void launch_stencil(const LaunchCfg& c, bool aniso);
+void launch_update(const LaunchCfg& c);
+void launch_true_residual(const LaunchCfg& c);
+void launch_output(const LaunchCfg& c, const float* const* fs, float* const* outs);
+void launch_output64(const SlotDesc* slot, int n, const float* f, double* out, cudaStream_t s);
+void launch_apply(const SlotDesc* slot, int n_tiles, bool aniso, const float* p, float* q,
+                  double* part, cudaStream_t s);
+
+// fast Poisson preconditioner, FP32 CUDA-core transform products (kernels_gemm_simt.cu).
+// stage 0..3 = forward x, forward y (+ eigenvalue weights), inverse x, inverse y (+ mask, dots).
+// mode 0: slots with active iterations; mode 1: slots with a pending preconditioner pass;
+// mode 2: every slot (verification entry point).
+void launch_prec_simt(const LaunchCfg& c, int stage, int mode);
+
+// tensor-core variant (kernels_gemm_tc.cu): FP16 hi/lo or BF16 hi/mid/lo operand splits.
+void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind);
+bool tc_supported();
+
+}  // namespace bx

@@ -1,0 +1,484 @@
+// Grid kernels of the PCG extension solve: right-hand side, masked biharmonic apply, CG vector
+// update, residual replacement and output.  All are persistent launches over a work list of
+// (slot, tile) items so that one launch serves a single solve, a batch or the serving loop.
+//
+// The operator is eq. (discrete_biharmonic) of Sec. 2.1 with the boundary rules of Algorithm 1
+// (Dirichlet padding), half-sample reflection (symmetric) or wrap-around (periodic), evaluated
+// matrix-free ("no need to form the 13-banded matrix", Sec. 2.2).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace bx {
+
+constexpr int kHX = kStTileX + 4;  // 68
+constexpr int kHY = kStTileY + 4;  // 20
+constexpr int kHalo = kHX * kHY;
+
+__device__ __forceinline__ void tile_origin(const SlotDesc& S, int tile, int& x0, int& y0) {
+  const int tx = (S.nx + kStTileX - 1) / kStTileX;
+  x0 = (tile % tx) * kStTileX;
+  y0 = (tile / tx) * kStTileY;
+}
+
+// Map halo position i of the tile to (global index, sign); sign 0 = outside / zero node.
+__device__ __forceinline__ int halo_src(const SlotDesc& S, int x0, int y0, int i, float& s) {
+  const int ly = i / kHX, lx = i - ly * kHX;
+  const int gy = y0 - 2 + ly, gx = x0 - 2 + lx;
+  if (gx > S.nx + 1 || gy > S.ny + 1) { s = 0.f; return 0; }
+  float sx, sy;
+  const int mx = ghost(gx, S.nx, S.bcx, sx);
+  const int my = ghost(gy, S.ny, S.bcy, sy);
+  s = sx * sy;
+  return my * S.nx + mx;
+}
+
+// 13-point masked biharmonic of a smem tile at local (ly+2, lx+2), compensated FP32.
+template <bool ANISO>
+__device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, int ly, int lx) {
+  const float* c = t + (ly + 2) * kHX + (lx + 2);
+  const float C = c[0];
+  const float E0 = c[-1], E1 = c[1], N0 = c[-kHX], N1 = c[kHX];
+  const float D0 = c[-kHX - 1], D1 = c[-kHX + 1], D2 = c[kHX - 1], D3 = c[kHX + 1];
+  const float F0 = c[-2], F1 = c[2], G0 = c[-2 * kHX], G1 = c[2 * kHX];
+  CompSum acc;
+  if (!ANISO) {
+    // 20 C - 8 (edges) + 2 (diagonals) + (distance 2); every term is an exact FP32 value
+    acc.add(16.f * C);
+    acc.add(4.f * C);
+    acc.add(-8.f * E0); acc.add(-8.f * E1); acc.add(-8.f * N0); acc.add(-8.f * N1);
+    acc.add(2.f * D0); acc.add(2.f * D1); acc.add(2.f * D2); acc.add(2.f * D3);
+    acc.add(F0); acc.add(F1); acc.add(G0); acc.add(G1);
+  } else {
+    acc.add_prod(S.wc, C);
+    acc.add_prod(S.wex, E0); acc.add_prod(S.wex, E1);
+    acc.add_prod(S.wey, N0); acc.add_prod(S.wey, N1);
+    acc.add_prod(S.wd, D0); acc.add_prod(S.wd, D1); acc.add_prod(S.wd, D2); acc.add_prod(S.wd, D3);
+    acc.add_prod(S.wfx, F0); acc.add_prod(S.wfx, F1);
+    acc.add_prod(S.wfy, G0); acc.add_prod(S.wfy, G1);
+    // low parts of the weights: products far below the result's ulp, plain FP32 suffices
+    float lo = S.wc_l * C + S.wex_l * (E0 + E1) + S.wey_l * (N0 + N1) +
+               S.wd_l * ((D0 + D1) + (D2 + D3)) + S.wfx_l * (F0 + F1) + S.wfy_l * (G0 + G1);
+    acc.c = __fadd_rn(acc.c, lo);
+  }
+  return acc.result();
+}
+
+__device__ __forceinline__ double stencil13_f64(const SlotDesc& S, const double* t, int ly, int lx) {
+  const double* c = t + (ly + 2) * kHX + (lx + 2);
+  return S.dwc * c[0] + S.dwex * (c[-1] + c[1]) + S.dwey * (c[-kHX] + c[kHX]) +
+         S.dwd * ((c[-kHX - 1] + c[-kHX + 1]) + (c[kHX - 1] + c[kHX + 1])) +
+         S.dwfx * (c[-2] + c[2]) + S.dwfy * (c[-2 * kHX] + c[2 * kHX]);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Setup: known mask from sign(phi) (Sec. 2.1), b = -M L^2 E_K f in FP64 (Algorithm 1, first
+// statement), zero CG state.  Partials: ||b||^2, number of known nodes, number of NaN phi.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kStThreads)
+k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+        const int* __restrict__ n_items, const float* const* __restrict__ phis,
+        const float* const* __restrict__ fs, const int* __restrict__ dirs) {
+  __shared__ double sf[kHalo];
+  __shared__ double red[64];
+  __shared__ int s_last;
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    const float* phi = phis[it.slot];
+    const float* f = fs[it.slot];
+    const bool out_dir = dirs[it.slot] == 0;
+    int x0, y0;
+    tile_origin(S, it.tile, x0, y0);
+    for (int i = threadIdx.x; i < kHalo; i += blockDim.x) {
+      float s;
+      const int g = halo_src(S, x0, y0, i, s);
+      double v = 0.0;
+      if (s != 0.f) {
+        const float ph = phi[g];
+        const bool known = out_dir ? (ph < 0.f) : (ph > 0.f);
+        v = known ? (double)s * (double)f[g] : 0.0;
+      }
+      sf[i] = v;
+    }
+    __syncthreads();
+    double bb = 0.0, cnt = 0.0, nan = 0.0;
+    for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
+      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= S.nx || gy >= S.ny) continue;
+      const int g = gy * S.nx + gx;
+      const float ph = phi[g];
+      const bool known = out_dir ? (ph < 0.f) : (ph > 0.f);
+      if (ph != ph) nan += 1.0;
+      double bv = 0.0;
+      if (!known) bv = -stencil13_f64(S, sf, ly, lx);
+      S.mask[g] = known ? 0 : 1;
+      S.b[g] = bv;
+      S.xhat[g] = 0.0;
+      S.r[g] = (float)bv;
+      S.p[0][g] = 0.f;
+      S.p[1][g] = 0.f;
+      S.q[g] = 0.f;
+      S.z[g] = 0.f;
+      bb += bv * bv;
+      cnt += known ? 1.0 : 0.0;
+    }
+    block_sum2<kStThreads>(bb, cnt, red);
+    double nn = nan, dummy = 0.0;
+    block_sum2<kStThreads>(nn, dummy, red);
+    if (threadIdx.x == 0) {
+      S.part[it.tile * 4 + 0] = bb;
+      S.part[it.tile * 4 + 1] = cnt;
+      S.part[it.tile * 4 + 2] = nn;
+    }
+    if (last_item_block(&S.sc->cnt[0], S.n_st_tiles, &s_last)) {
+      double sums[3];
+      reduce_partials<kStThreads, 3>(S.part, S.n_st_tiles, sums, red);
+      if (threadIdx.x == 0) {
+        const double sb = sums[0], sk = sums[1], sn = sums[2];
+        SlotScalars* sc = S.sc;
+        sc->bb = sb;
+        sc->rr = sb;
+        sc->rr_true = sb;
+        sc->rr_ref = sb;
+        sc->rho = 0.0;
+        sc->beta = 0.0;
+        sc->alpha = 0.0;
+        sc->it = 0;
+        sc->fold = 0;
+        sc->n_known = (int)sk;
+        if (sn > 0.0) {
+          sc->status = -1;  // EXT_EINVAL: NaN in phi
+          sc->active = 0;
+          sc->need_prec = 0;
+        } else if (sb == 0.0) {
+          sc->status = ST_OK;  // b = 0: x = 0 is exact
+          sc->active = 0;
+          sc->need_prec = 0;
+        } else {
+          sc->status = ST_RUNNING;
+          sc->active = 1;
+          sc->need_prec = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo),
+// q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), partial p.q in FP64.
+// The last item of the slot forms alpha = rho / p.q and flags breakdown.
+// ---------------------------------------------------------------------------------------------
+template <bool ANISO>
+__global__ void __launch_bounds__(kStThreads)
+k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+          const int* __restrict__ n_items) {
+  __shared__ float sp[kHalo];
+  __shared__ double red[64];
+  __shared__ int s_last;
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    SlotScalars* sc = S.sc;
+    if (!sc->active) continue;
+    const float beta = (float)sc->beta;
+    const int par = sc->it & 1;
+    const float* __restrict__ pold = S.p[par];
+    float* __restrict__ pnew = S.p[par ^ 1];
+    const float* __restrict__ z = S.z;
+    int x0, y0;
+    tile_origin(S, it.tile, x0, y0);
+    for (int i = threadIdx.x; i < kHalo; i += blockDim.x) {
+      float s;
+      const int g = halo_src(S, x0, y0, i, s);
+      float v = 0.f;
+      if (s != 0.f) v = s * __fmaf_rn(beta, pold[g], z[g]);
+      sp[i] = v;
+    }
+    __syncthreads();
+    double pq = 0.0;
+    for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
+      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= S.nx || gy >= S.ny) continue;
+      const int g = gy * S.nx + gx;
+      const float pv = sp[(ly + 2) * kHX + lx + 2];
+      float qv = 0.f;
+      if (S.mask[g]) qv = stencil13<ANISO>(S, sp, ly, lx);
+      pnew[g] = pv;
+      S.q[g] = qv;
+      pq += (double)pv * (double)qv;
+    }
+    double d2 = 0.0;
+    block_sum2<kStThreads>(pq, d2, red);
+    if (threadIdx.x == 0) S.part[it.tile * 4 + 0] = pq;
+    if (last_item_block(&sc->cnt[1], S.n_st_tiles, &s_last)) {
+      double sums[1];
+      reduce_partials<kStThreads, 1>(S.part, S.n_st_tiles, sums, red);
+      if (threadIdx.x == 0) {
+        const double s = sums[0];
+        sc->pq = s;
+        if (!(s > 0.0) || !isfinite(s) || !isfinite(sc->rho)) {
+          sc->status = ST_EBREAKDOWN;
+          sc->active = 0;
+          sc->fold = 1;  // the tail folds and reports the best iterate
+        } else {
+          sc->alpha = sc->rho / s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Iteration, stage 2: xhat += alpha p (FP64), r -= alpha q (FP32), partial ||r||^2 (FP64).  The
+// last item advances the iteration count and decides stop / residual replacement.
+// Keeping the iterate in FP64 matters: an FP32 increment carries rounding errors of size
+// eps |x|, which for this operator pin the true residual near 1e-6 while the recursive one
+// keeps falling.  Each thread moves 16-byte vectors (4 elements per access).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecThreads)
+k_update(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+         const int* __restrict__ n_items) {
+  __shared__ double red[64];
+  __shared__ int s_last;
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    SlotScalars* sc = S.sc;
+    if (!sc->active) continue;
+    const float alpha = (float)sc->alpha;
+    const double alpha_d = (double)alpha;
+    const float* __restrict__ p = S.p[(sc->it & 1) ^ 1];
+    const int n = S.nx * S.ny;
+    const int e0 = it.tile * kVecChunk;
+    const int e1 = min(n, e0 + kVecChunk);
+    double rr = 0.0;
+    constexpr int kStep = 4 * kVecThreads;
+#pragma unroll
+    for (int j = 0; j < kVecChunk / kStep; ++j) {
+      const int e = e0 + j * kStep + 4 * threadIdx.x;
+      if (e + 3 < e1) {
+        const float4 pv = *reinterpret_cast<const float4*>(p + e);
+        const float4 qv = *reinterpret_cast<const float4*>(S.q + e);
+        float4 rv = *reinterpret_cast<const float4*>(S.r + e);
+        double2 x0 = *reinterpret_cast<const double2*>(S.xhat + e);
+        double2 x1 = *reinterpret_cast<const double2*>(S.xhat + e + 2);
+        x0.x = fma(alpha_d, (double)pv.x, x0.x);
+        x0.y = fma(alpha_d, (double)pv.y, x0.y);
+        x1.x = fma(alpha_d, (double)pv.z, x1.x);
+        x1.y = fma(alpha_d, (double)pv.w, x1.y);
+        rv.x = __fmaf_rn(-alpha, qv.x, rv.x);
+        rv.y = __fmaf_rn(-alpha, qv.y, rv.y);
+        rv.z = __fmaf_rn(-alpha, qv.z, rv.z);
+        rv.w = __fmaf_rn(-alpha, qv.w, rv.w);
+        *reinterpret_cast<double2*>(S.xhat + e) = x0;
+        *reinterpret_cast<double2*>(S.xhat + e + 2) = x1;
+        *reinterpret_cast<float4*>(S.r + e) = rv;
+        rr += ((double)rv.x * rv.x + (double)rv.y * rv.y) + ((double)rv.z * rv.z + (double)rv.w * rv.w);
+      } else {
+        for (int k = e; k < e1 && k < e + 4; ++k) {
+          S.xhat[k] = fma(alpha_d, (double)p[k], S.xhat[k]);
+          const float rv = __fmaf_rn(-alpha, S.q[k], S.r[k]);
+          S.r[k] = rv;
+          rr += (double)rv * (double)rv;
+        }
+      }
+    }
+    double d2 = 0.0;
+    block_sum2<kVecThreads>(rr, d2, red);
+    if (threadIdx.x == 0) S.part[it.tile * 4 + 0] = rr;
+    if (last_item_block(&sc->cnt[2], S.n_vec_items, &s_last)) {
+      double sums[1];
+      reduce_partials<kVecThreads, 1>(S.part, S.n_vec_items, sums, red);
+      if (threadIdx.x == 0) {
+        const double s = sums[0];
+        sc->rr = s;
+        const int itn = sc->it + 1;
+        sc->it = itn;
+        if (s <= sc->rtol2 * sc->bb || itn >= sc->maxit || !isfinite(s)) {
+          sc->active = 0;
+          sc->fold = 1;
+        } else if (s < sc->delta2 * sc->rr_ref || itn % sc->fold_every == 0) {
+          sc->fold = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Tail: true residual r = b - M L^2 xhat in FP64, replace the recursive residual, and decide: converged / not converged at maxit / continue (with a fresh preconditioner pass).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kStThreads)
+k_true_residual(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+                const int* __restrict__ n_items) {
+  __shared__ double sx[kHalo];
+  __shared__ double red[64];
+  __shared__ int s_last;
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    SlotScalars* sc = S.sc;
+    if (!sc->fold) continue;
+    int x0, y0;
+    tile_origin(S, it.tile, x0, y0);
+    for (int i = threadIdx.x; i < kHalo; i += blockDim.x) {
+      float s;
+      const int g = halo_src(S, x0, y0, i, s);
+      sx[i] = (s != 0.f) ? (double)s * S.xhat[g] : 0.0;
+    }
+    __syncthreads();
+    double rr = 0.0;
+    for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
+      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= S.nx || gy >= S.ny) continue;
+      const int g = gy * S.nx + gx;
+      double rv = 0.0;
+      if (S.mask[g]) rv = S.b[g] - stencil13_f64(S, sx, ly, lx);
+      S.r[g] = (float)rv;
+      rr += rv * rv;
+    }
+    double d2 = 0.0;
+    block_sum2<kStThreads>(rr, d2, red);
+    if (threadIdx.x == 0) S.part[it.tile * 4 + 0] = rr;
+    if (last_item_block(&sc->cnt[3], S.n_st_tiles, &s_last)) {
+      double sums[1];
+      reduce_partials<kStThreads, 1>(S.part, S.n_st_tiles, sums, red);
+      if (threadIdx.x == 0) {
+        const double s = sums[0];
+        sc->rr_true = s;
+        sc->rr = s;
+        sc->rr_ref = s;
+        sc->fold = 0;
+        if (sc->status == ST_EBREAKDOWN) {
+          sc->active = 0;
+          sc->need_prec = 0;
+          if (s <= sc->rtol2 * sc->bb) sc->status = ST_OK;
+        } else if (s <= sc->rtol2 * sc->bb) {
+          sc->status = ST_OK;
+          sc->active = 0;
+          sc->need_prec = 0;
+        } else if (sc->it >= sc->maxit || !isfinite(s)) {
+          sc->status = ST_ENOTCONV;
+          sc->active = 0;
+          sc->need_prec = 0;
+        } else {
+          sc->active = 1;
+          sc->need_prec = 1;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Output (Algorithm 1, last statement): out = f at known nodes (bit copy), xhat at unknowns.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kVecThreads)
+k_output(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+         const int* __restrict__ n_items, const float* const* __restrict__ fs,
+         float* const* __restrict__ outs) {
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    const float* f = fs[it.slot];
+    float* out = outs[it.slot];
+    const int n = S.nx * S.ny;
+    const int e0 = it.tile * kVecChunk;
+    const int e1 = min(n, e0 + kVecChunk);
+    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
+      out[e] = S.mask[e] ? (float)S.xhat[e] : f[e];
+  }
+}
+
+// FP64 variant of the output for one slot (lets the caller recompute the residual exactly).
+__global__ void __launch_bounds__(kVecThreads)
+k_output64(const SlotDesc* __restrict__ slots, const float* __restrict__ f, double* __restrict__ out) {
+  const SlotDesc& S = slots[0];
+  const int n = S.nx * S.ny;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
+    out[e] = S.mask[e] ? S.xhat[e] : (double)f[e];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Verification entry: q = M L^2 p for a caller-supplied p (same compensated evaluation).
+// ---------------------------------------------------------------------------------------------
+template <bool ANISO>
+__global__ void __launch_bounds__(kStThreads)
+k_apply(const SlotDesc* __restrict__ slots, const float* __restrict__ p, float* __restrict__ q,
+        double* __restrict__ part) {
+  __shared__ float sp[kHalo];
+  __shared__ double red[64];
+  const SlotDesc& S = slots[0];
+  for (int tile = blockIdx.x; tile < S.n_st_tiles; tile += gridDim.x) {
+    int x0, y0;
+    tile_origin(S, tile, x0, y0);
+    for (int i = threadIdx.x; i < kHalo; i += blockDim.x) {
+      float s;
+      const int g = halo_src(S, x0, y0, i, s);
+      sp[i] = (s != 0.f) ? s * p[g] : 0.f;
+    }
+    __syncthreads();
+    double pq = 0.0;
+    for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
+      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= S.nx || gy >= S.ny) continue;
+      const int g = gy * S.nx + gx;
+      float qv = 0.f;
+      if (S.mask[g]) qv = stencil13<ANISO>(S, sp, ly, lx);
+      q[g] = qv;
+      pq += (double)p[g] * (double)qv;
+    }
+    double d2 = 0.0;
+    block_sum2<kStThreads>(pq, d2, red);
+    if (threadIdx.x == 0) part[tile] = pq;
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------------------------
+void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
+                  const int* dirs) {
+  k_setup<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, phis, fs, dirs);
+}
+void launch_stencil(const LaunchCfg& c, bool aniso) {
+  if (aniso) k_stencil<true><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
+  else k_stencil<false><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
+}
+void launch_update(const LaunchCfg& c) {
+  k_update<<<c.grid, kVecThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
+}
+void launch_true_residual(const LaunchCfg& c) {
+  k_true_residual<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
+}
+void launch_output(const LaunchCfg& c, const float* const* fs, float* const* outs) {
+  k_output<<<c.grid, kVecThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, fs, outs);
+}
+void launch_output64(const SlotDesc* slot, int n, const float* f, double* out, cudaStream_t s) {
+  int grid = (n + kVecThreads - 1) / kVecThreads;
+  grid = grid < 4096 ? grid : 4096;
+  k_output64<<<grid, kVecThreads, 0, s>>>(slot, f, out);
+}
+void launch_apply(const SlotDesc* slot, int n_tiles, bool aniso, const float* p, float* q,
+                  double* part, cudaStream_t s) {
+  const int grid = n_tiles < 4096 ? n_tiles : 4096;
+  if (aniso) k_apply<true><<<grid, kStThreads, 0, s>>>(slot, p, q, part);
+  else k_apply<false><<<grid, kStThreads, 0, s>>>(slot, p, q, part);
+}
+
+}  // namespace bx

@@ -1,0 +1,297 @@
+"""Thin Python binding of libbiharm_ext.so (ctypes).  Argument marshalling only.
+
+Every name mirrors an ``ext_*`` entry point of ``include/biharm_ext.h``.  Arrays may be torch
+tensors (CUDA or CPU, float32, contiguous) or numpy float32 arrays (host); shapes are [ny][nx].
+There is no fallback: if the library is missing or fails to load, ``load()`` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbiharm_ext.so")
+
+BC = {"symmetric": 0, "periodic": 1, "dirichlet": 2}
+DIR = {"out": 0, "in": 1}
+PREC = {"fp32": 1, "mixed_bf16": 2, "mixed_fp16": 3}
+
+EXT_OK, EXT_PENDING = 0, 1
+EXT_EINVAL, EXT_ENOKNOWN, EXT_ENOMEM, EXT_EADMIT = -1, -2, -3, -4
+EXT_ENOTCONV, EXT_EBREAKDOWN, EXT_ETIMEOUT, EXT_ECUDA = -5, -6, -7, -8
+EXT_ENOTSUP, EXT_ENOTFOUND = -9, -10
+
+EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch", "ext_submit",
+            "ext_poll", "ext_drain", "ext_destroy", "ext_strerror", "ext_last_error",
+            "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
+            "ext_profile_read", "ext_launch_count"]
+KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
+                "prec_stage2", "prec_stage3", "output"]
+
+
+class ExtProblem(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("hx", C.c_double), ("hy", C.c_double),
+                ("bc_x", C.c_int32), ("bc_y", C.c_int32), ("dir", C.c_int32)]
+
+
+class ExtOptions(C.Structure):
+    _fields_ = [("prec", C.c_int32), ("rtol", C.c_double), ("maxit", C.c_int32),
+                ("true_res_every", C.c_int32), ("replace_factor", C.c_double),
+                ("iters_per_launch", C.c_int32),
+                ("hbm_budget", C.c_size_t), ("flexible", C.c_int32), ("max_slots", C.c_int32),
+                ("profile", C.c_int32)]
+
+
+class ExtResult(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("relres_true", C.c_double),
+                ("relres_rec", C.c_double), ("n_unknown", C.c_int32), ("n_known", C.c_int32),
+                ("ms_queue", C.c_double), ("ms_solve", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ExtError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code}) {last_error()}")
+
+
+_lib = None
+
+
+def load():
+    """Load the library (building it first if it is absent).  Raises if that fails."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        from . import build_ext
+        build_ext.build()
+    lib = C.CDLL(LIB_PATH)
+    P, I, D = C.c_void_p, C.c_int, C.c_double
+    lib.ext_options_default.argtypes = [C.POINTER(ExtOptions)]
+    lib.ext_options_default.restype = None
+    lib.ext_create.argtypes = [C.POINTER(ExtOptions), P, C.POINTER(P)]
+    lib.ext_create.restype = I
+    lib.ext_solve.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(ExtResult)]
+    lib.ext_solve.restype = I
+    lib.ext_solve_f64.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(ExtResult)]
+    lib.ext_solve_f64.restype = I
+    lib.ext_solve_batch.argtypes = [P, I, C.POINTER(ExtProblem), C.POINTER(P), C.POINTER(P),
+                                    C.POINTER(P), C.POINTER(ExtResult)]
+    lib.ext_solve_batch.restype = I
+    lib.ext_submit.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(C.c_uint64)]
+    lib.ext_submit.restype = I
+    lib.ext_poll.argtypes = [P, C.c_uint64, C.POINTER(ExtResult)]
+    lib.ext_poll.restype = I
+    lib.ext_drain.argtypes = [P]
+    lib.ext_drain.restype = I
+    lib.ext_destroy.argtypes = [P]
+    lib.ext_destroy.restype = None
+    lib.ext_strerror.argtypes = [I]
+    lib.ext_strerror.restype = C.c_char_p
+    lib.ext_last_error.argtypes = []
+    lib.ext_last_error.restype = C.c_char_p
+    lib.ext_apply_biharmonic.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(D)]
+    lib.ext_apply_biharmonic.restype = I
+    lib.ext_rhs.argtypes = [P, C.POINTER(ExtProblem), P, P, P]
+    lib.ext_rhs.restype = I
+    lib.ext_apply_preconditioner.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(D)]
+    lib.ext_apply_preconditioner.restype = I
+    lib.ext_profile_read.argtypes = [P, I, C.POINTER(D), C.POINTER(C.c_int64), I]
+    lib.ext_profile_read.restype = I
+    lib.ext_launch_count.argtypes = [P]
+    lib.ext_launch_count.restype = C.c_int64
+    _lib = lib
+    return lib
+
+
+def strerror(code: int) -> str:
+    return load().ext_strerror(int(code)).decode()
+
+
+def last_error() -> str:
+    return load().ext_last_error().decode()
+
+
+# ------------------------------------------------------------------------------------------------
+# marshalling helpers
+# ------------------------------------------------------------------------------------------------
+def _ptr(a):
+    """Raw data pointer of a contiguous float32/float64 torch tensor or numpy array."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("array must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def problem(nx, ny, bc_x="symmetric", bc_y=None, direction="out", hx=1.0, hy=None):
+    bc_y = bc_x if bc_y is None else bc_y
+    hy = hx if hy is None else hy
+    return ExtProblem(int(nx), int(ny), float(hx), float(hy), BC[bc_x] if isinstance(bc_x, str)
+                      else int(bc_x), BC[bc_y] if isinstance(bc_y, str) else int(bc_y),
+                      DIR[direction] if isinstance(direction, str) else int(direction))
+
+
+def problem_of(p):
+    """ExtProblem from a synth.Problem-like object."""
+    return problem(p.nx, p.ny, p.bc_x, p.bc_y, p.direction, p.hx, p.hy)
+
+
+def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launch=10,
+            hbm_budget=0, flexible=1, max_slots=256, replace_factor=1e-2, profile=0):
+    o = ExtOptions()
+    load().ext_options_default(C.byref(o))
+    o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
+    o.rtol, o.maxit, o.true_res_every = float(rtol), int(maxit), int(true_res_every)
+    o.replace_factor = float(replace_factor)
+    o.iters_per_launch, o.hbm_budget = int(iters_per_launch), int(hbm_budget)
+    o.flexible, o.max_slots, o.profile = int(flexible), int(max_slots), int(profile)
+    return o
+
+
+def _check(rc, what, ok=(EXT_OK,)):
+    if rc not in ok:
+        raise ExtError(rc, what)
+    return rc
+
+
+# ------------------------------------------------------------------------------------------------
+# entry points (same names as the C ABI)
+# ------------------------------------------------------------------------------------------------
+def ext_create(opts=None, stream=None):
+    """Returns an opaque context handle (int).  ``stream``: a torch.cuda.Stream, raw handle or None."""
+    lib = load()
+    h = C.c_void_p()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    o = opts if opts is not None else options()
+    _check(lib.ext_create(C.byref(o), s, C.byref(h)), "ext_create")
+    return h.value
+
+
+def ext_destroy(ctx):
+    load().ext_destroy(ctx)
+
+
+def ext_solve(ctx, prob, phi, f, out, check=True):
+    """Solve one extension; returns the result as a dict (status may be a non-OK code if
+    check=False)."""
+    res = ExtResult()
+    rc = load().ext_solve(ctx, C.byref(prob), _ptr(phi), _ptr(f), _ptr(out), C.byref(res))
+    if check:
+        _check(rc, "ext_solve")
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def ext_solve_f64(ctx, prob, phi, f, out64, check=True):
+    """As ext_solve with a float64 device output (f at known nodes, the FP64 iterate elsewhere)."""
+    res = ExtResult()
+    rc = load().ext_solve_f64(ctx, C.byref(prob), _ptr(phi), _ptr(f), _ptr(out64), C.byref(res))
+    if check:
+        _check(rc, "ext_solve_f64")
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def ext_solve_batch(ctx, probs, phis, fs, outs, check=True):
+    n = len(probs)
+    PA = C.c_void_p * n
+    parr = (ExtProblem * n)(*probs)
+    res = (ExtResult * n)()
+    rc = load().ext_solve_batch(ctx, n, parr, PA(*[_ptr(a) for a in phis]),
+                                PA(*[_ptr(a) for a in fs]), PA(*[_ptr(a) for a in outs]), res)
+    if check:
+        _check(rc, "ext_solve_batch")
+    return rc, [r.as_dict() for r in res]
+
+
+def ext_submit(ctx, prob, phi, f, out):
+    t = C.c_uint64()
+    _check(load().ext_submit(ctx, C.byref(prob), _ptr(phi), _ptr(f), _ptr(out), C.byref(t)),
+           "ext_submit")
+    return t.value
+
+
+def ext_poll(ctx, ticket):
+    res = ExtResult()
+    rc = load().ext_poll(ctx, C.c_uint64(ticket), C.byref(res))
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def ext_drain(ctx):
+    return _check(load().ext_drain(ctx), "ext_drain")
+
+
+def ext_apply_biharmonic(ctx, prob, phi, p, q):
+    s = C.c_double()
+    _check(load().ext_apply_biharmonic(ctx, C.byref(prob), _ptr(phi), _ptr(p), _ptr(q),
+                                       C.byref(s)), "ext_apply_biharmonic")
+    return s.value
+
+
+def ext_rhs(ctx, prob, phi, f, b):
+    _check(load().ext_rhs(ctx, C.byref(prob), _ptr(phi), _ptr(f), _ptr(b)), "ext_rhs")
+
+
+def ext_apply_preconditioner(ctx, prob, phi, r, z):
+    s = C.c_double()
+    _check(load().ext_apply_preconditioner(ctx, C.byref(prob), _ptr(phi), _ptr(r), _ptr(z),
+                                           C.byref(s)), "ext_apply_preconditioner")
+    return s.value
+
+
+def ext_profile_read(ctx, reset=True):
+    """{kind: (total_ms, launches)} for a context created with profile=1."""
+    n = len(KERNEL_KINDS)
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _check(load().ext_profile_read(ctx, n, ms, cnt, int(reset)), "ext_profile_read")
+    return {KERNEL_KINDS[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def ext_launch_count(ctx):
+    return int(load().ext_launch_count(ctx))
+
+
+@dataclass
+class Extender:
+    """Convenience wrapper owning one context."""
+    prec: str = "fp32"
+    rtol: float = 1e-8
+    maxit: int = 0
+
+    def __post_init__(self):
+        self.ctx = ext_create(options(self.prec, self.rtol, self.maxit))
+
+    def solve(self, prob, phi, f, out):
+        return ext_solve(self.ctx, prob, phi, f, out)
+
+    def close(self):
+        if self.ctx:
+            ext_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
