@@ -194,6 +194,26 @@ int ext_rhs(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float
 int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float* phi,
                              const float* r, float* z, double* scale);
 
+/* ---- operator apply that allocates nothing ----
+ *
+ * Same result as ext_apply_biharmonic (q = M L^2 p, and the FP64 sum p.q into *sum_pq, which may
+ * be NULL), for callers that cannot allocate device memory when they need it: code running inside
+ * a stream capture in global mode (cudaMalloc is refused there), latency-critical loops where
+ * cudaMalloc/cudaFree would synchronise the device, and hosts that own the whole device-memory
+ * budget.  The paper has no counterpart; this is a property of the library, not of the method.
+ * No context is needed.  phi, p and q are device pointers, [ny][nx] float32; the call runs on
+ * cuda_stream (NULL = the default stream) and returns after that stream has finished its work.
+ * Scratch: one fixed 2 MiB array per device (grids up to 1,048,576 nodes and 32,768 stencil
+ * tiles of 64x16; larger grids return EXT_EINVAL, see ext_noalloc_last_error).  The first call on
+ * a device looks up that array's device address; make that first call before any stream capture.
+ * All calls on a device share the array: calls whose GPU work overlaps race and must be
+ * serialised by the caller.  Nothing in it needs to start at zero. */
+int ext_apply_biharmonic_noalloc(const ext_problem* prob, const float* phi, const float* p,
+                                 float* q, double* sum_pq, void* cuda_stream);
+
+/* Reason for the last EXT_EINVAL / EXT_ECUDA of ext_apply_biharmonic_noalloc in this thread. */
+const char* ext_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

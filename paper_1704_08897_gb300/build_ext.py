@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiharm_ext.so")
 SOURCES = ["api.cu", "serve.cu", "kernels_grid.cu", "kernels_gemm_simt.cu", "kernels_gemm_tc.cu",
-           "plan.cpp"]
+           "plan.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -168,7 +168,7 @@ static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {
 
 // Stencil weights of (L_y (+) L_x)^2 scaled by 1/max(a, c)^2, a = 1/hx^2, c = 1/hy^2
 // (eq. discrete_biharmonic for hx = hy: 20, -8, 2, 1).
-static void set_weights(SlotDesc& d, double hx, double hy) {
+void bx::set_weights(SlotDesc& d, double hx, double hy) {
   double a = 1.0 / (hx * hx), c = 1.0 / (hy * hy);
   const double m = std::max(a, c);
   a /= m;

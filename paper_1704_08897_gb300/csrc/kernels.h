@@ -15,6 +15,9 @@ struct LaunchCfg {
   cudaStream_t stream;
 };
 
+// host helper (api.cu): stencil weights of (L_y (+) L_x)^2 for spacings hx, hy
+void set_weights(SlotDesc& d, double hx, double hy);
+
 // grid kernels (kernels_grid.cu)
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
                   const int* dirs);

@@ -28,7 +28,8 @@ EXT_ENOTSUP, EXT_ENOTFOUND = -9, -10
 EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch", "ext_submit",
             "ext_poll", "ext_drain", "ext_destroy", "ext_strerror", "ext_last_error",
             "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
-            "ext_profile_read", "ext_launch_count"]
+            "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
+            "ext_noalloc_last_error"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output"]
 
@@ -107,6 +108,10 @@ def load():
     lib.ext_profile_read.restype = I
     lib.ext_launch_count.argtypes = [P]
     lib.ext_launch_count.restype = C.c_int64
+    lib.ext_apply_biharmonic_noalloc.argtypes = [C.POINTER(ExtProblem), P, P, P, C.POINTER(D), P]
+    lib.ext_apply_biharmonic_noalloc.restype = I
+    lib.ext_noalloc_last_error.argtypes = []
+    lib.ext_noalloc_last_error.restype = C.c_char_p
     _lib = lib
     return lib
 
@@ -257,6 +262,17 @@ def ext_apply_preconditioner(ctx, prob, phi, r, z):
     _check(load().ext_apply_preconditioner(ctx, C.byref(prob), _ptr(phi), _ptr(r), _ptr(z),
                                            C.byref(s)), "ext_apply_preconditioner")
     return s.value
+
+
+def ext_apply_biharmonic_noalloc(prob, phi, p, q, stream=None, check=True):
+    """q = M L^2 p without any device allocation (fixed per-device scratch; see the header).
+    Returns (rc, sum p.q)."""
+    s = C.c_double()
+    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = load().ext_apply_biharmonic_noalloc(C.byref(prob), _ptr(phi), _ptr(p), _ptr(q), C.byref(s), st)
+    if check and rc != EXT_OK:
+        raise ExtError(rc, "ext_apply_biharmonic_noalloc: " + load().ext_noalloc_last_error().decode())
+    return rc, s.value
 
 
 def ext_profile_read(ctx, reset=True):
