@@ -91,7 +91,8 @@ enum {
   EXT_KERNEL_PREC2 = 6,
   EXT_KERNEL_PREC3 = 7,
   EXT_KERNEL_OUTPUT = 8,         /* out = f on Omega, x elsewhere                            */
-  EXT_KERNEL_KINDS = 9
+  EXT_KERNEL_SPLIT = 9,          /* residual -> scaled 16-bit planes (mixed modes)            */
+  EXT_KERNEL_KINDS = 10
 };
 
 typedef struct {

@@ -9,6 +9,8 @@
 // until every slot reports a final status.  Batches and the serving loop use the same kernels
 // over work lists that span all slots.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -54,7 +56,8 @@ struct PlanDev {
   float* q = nullptr;   // [np][np]
   float* qt = nullptr;  // [np][np]
   std::vector<double> lam;
-  void* tc = nullptr;   // tensor-core operand planes (kernels_gemm_tc.cu)
+  void* tc = nullptr;   // tensor-core operand planes: [Q planes][Q^T planes], 2-byte elements
+  int tc_split = -1;
 };
 
 // One problem's device state inside a workspace.
@@ -85,6 +88,9 @@ struct Workspace {
   cudaGraphExec_t graph = nullptr;
   int graph_iters = 0;
   int64_t graph_nodes = 0;
+  void* d_tmaps = nullptr;      // per slot 8 CUtensorMap (tensor-core modes)
+  struct Ev { int kind; cudaEvent_t a, b; };
+  std::vector<Ev> graph_events;  // profiling: event-record nodes of the graph
   bool aniso = false;
   bool host_io = false;
 };
@@ -103,9 +109,13 @@ struct ext_ctx {
   std::map<int, PlanDev> plans;
   std::map<std::string, Workspace*> ws;
   std::mutex api_mu;  // serialises ext_solve* and the serving worker on the stream
+  bool tc = false;    // mixed modes: tensor-core preconditioner
+  int split = 0;      // 0 = FP16 hi/lo, 1 = BF16 hi/mid/lo
+  int* d_err = nullptr;   // device flag raised by a bounded wait that ran out
+  int* h_err = nullptr;   // pinned copy
   // launch accounting and optional per-kernel timing (ext_options.profile)
   int64_t launches = 0;
-  struct Pending { int kind; cudaEvent_t a, b; };
+  using Pending = Workspace::Ev;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[EXT_KERNEL_KINDS] = {0};
@@ -136,6 +146,94 @@ static bool is_device_ptr(const void* p) {
     return false;
   }
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---- tensor-core operands --------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                  CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                  CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encoder() {
+  static EncodeTiledFn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+    cudaGetLastError();
+  }
+  return fn;
+}
+
+// 2-D map over `rows` rows of `inner` 2-byte elements; boxes of 64 x box_rows, 128-byte swizzle.
+static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  EncodeTiledFn enc = get_encoder();
+  if (!enc) {
+    g_last_error = "cuTensorMapEncodeTiled not available";
+    return EXT_ENOTSUP;
+  }
+  const cuuint64_t dims[2] = {inner, rows};
+  const cuuint64_t strides[1] = {inner * 2};
+  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base,
+                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    g_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return EXT_ECUDA;
+  }
+  return EXT_OK;
+}
+
+// Planes of v (exact FP64 input): FP16 hi/lo of v * 2^6, or BF16 hi/mid/lo of v.
+static void split_host(double v, int split, uint16_t* out, size_t plane, size_t idx) {
+  if (split == 0) {
+    v *= 64.0;
+    const __half h = __double2half(v);
+    const double r = v - (double)__half2float(h);
+    out[idx] = __half_as_ushort(h);
+    out[plane + idx] = __half_as_ushort(__double2half(r));
+  } else {
+    const __nv_bfloat16 h = __double2bfloat16(v);
+    const double r1 = v - (double)__bfloat162float(h);
+    const __nv_bfloat16 m = __double2bfloat16(r1);
+    const double r2 = r1 - (double)__bfloat162float(m);
+    out[idx] = __bfloat16_as_ushort(h);
+    out[plane + idx] = __bfloat16_as_ushort(m);
+    out[2 * plane + idx] = __bfloat16_as_ushort(__double2bfloat16(r2));
+  }
+}
+
+// Q and Q^T of one axis as split planes, zero-padded to np x np: [Q planes][Q^T planes].
+static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
+  if (P->tc && P->tc_split == ctx->split) return EXT_OK;
+  if (P->tc) {
+    cudaFree(P->tc);
+    P->tc = nullptr;
+  }
+  const int NS = tc_planes(ctx->split);
+  const size_t plane = (size_t)P->np * P->np;
+  std::vector<uint16_t> h(2 * NS * plane, 0);
+  AxisBasis B = make_axis_basis(P->n, P->bc);
+  for (int i = 0; i < P->n; ++i)
+    for (int k = 0; k < P->n; ++k) {
+      const double v = B.Q[(size_t)i * P->n + k];
+      split_host(v, ctx->split, h.data(), plane, (size_t)i * P->np + k);                 // Q[i][k]
+      split_host(v, ctx->split, h.data() + NS * plane, plane, (size_t)k * P->np + i);    // Q^T[k][i]
+    }
+  if (cudaMalloc(&P->tc, 2 * h.size()) != cudaSuccess) {
+    cudaGetLastError();
+    g_last_error = "cudaMalloc of tensor-core plan failed";
+    return EXT_ENOMEM;
+  }
+  BX_CUDA(cudaMemcpy(P->tc, h.data(), 2 * h.size(), cudaMemcpyHostToDevice));
+  P->tc_split = ctx->split;
+  return EXT_OK;
 }
 
 static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {
@@ -189,6 +287,10 @@ void bx::set_weights(SlotDesc& d, double hx, double hy) {
 static void free_workspace(Workspace* W) {
   if (!W) return;
   if (W->graph) cudaGraphExecDestroy(W->graph);
+  for (auto& e : W->graph_events) {
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
   for (auto& s : W->slots) cudaFree(s.arena);
   cudaFree(W->d_slots);
   cudaFree(W->d_sc);
@@ -259,6 +361,15 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
     size_t o_io = 0;
     if (host_io) o_io = take(12 * N);
+    const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
+    size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0;
+    if (ctx->tc) {
+      o_tr = take(2 * NS * Np);
+      o_tt1 = take(2 * NS * Np);
+      o_tt2 = take(2 * NS * Np);
+      o_tt3 = take(2 * NS * Np);
+      o_maps = take(8 * sizeof(CUtensorMap));
+    }
     s.bytes = off;
     if (cudaMalloc(&s.arena, s.bytes) != cudaSuccess) {
       cudaGetLastError();
@@ -280,6 +391,45 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     d.t2 = (float*)(A + o_t2);
     d.t3 = (float*)(A + o_t3);
     d.rin = nullptr;
+    d.n_tc_tiles = n_gm;
+    if (ctx->tc) {
+      int rc2 = ensure_tc_plan(ctx, px);
+      if (!rc2) rc2 = ensure_tc_plan(ctx, py);
+      if (rc2) {
+        cudaFree(s.arena);
+        for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
+        return rc2;
+      }
+      d.tc_r = A + o_tr;
+      d.tc_t1 = A + o_tt1;
+      d.tc_t2 = A + o_tt2;
+      d.tc_t3 = A + o_tt3;
+      d.tmaps = A + o_maps;
+      BX_CUDA(cudaMemset(d.tc_r, 0, 2 * NS * Np));
+      const bool bf = ctx->split == 1;
+      const size_t qplane = 0;
+      (void)qplane;
+      CUtensorMap maps[8];
+      const size_t pxp = (size_t)d.nxp * d.nxp, pyp = (size_t)d.nyp * d.nyp;
+      uint16_t* qxb = (uint16_t*)px->tc;
+      uint16_t* qyb = (uint16_t*)py->tc;
+      // A operands: r planes [P][nyp][nxp], T1 [P][nxp][nyp], T2 [P][nyp][nxp], T3 [P][nxp][nyp]
+      int rc3 = make_tmap(&maps[0], d.tc_r, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
+      if (!rc3) rc3 = make_tmap(&maps[1], d.tc_t1, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
+      if (!rc3) rc3 = make_tmap(&maps[2], d.tc_t2, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
+      if (!rc3) rc3 = make_tmap(&maps[3], d.tc_t3, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
+      // B operands: Qx^T, Qy^T, Qx, Qy planes
+      if (!rc3) rc3 = make_tmap(&maps[4], qxb + NS * pxp, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
+      if (!rc3) rc3 = make_tmap(&maps[5], qyb + NS * pyp, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
+      if (!rc3) rc3 = make_tmap(&maps[6], qxb, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
+      if (!rc3) rc3 = make_tmap(&maps[7], qyb, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
+      if (rc3) {
+        cudaFree(s.arena);
+        for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
+        return rc3;
+      }
+      BX_CUDA(cudaMemcpy(A + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+    }
     d.qx = px->q;
     d.qxt = px->qt;
     d.qy = py->q;
@@ -415,10 +565,23 @@ static void timed(ext_ctx* ctx, int kind, F&& fn) {
     return;
   }
   cudaEvent_t a = ev_get(ctx), b = ev_get(ctx);
-  cudaEventRecord(a, ctx->stream);
+  // External: under stream capture the records become timing nodes of the graph
+  cudaEventRecordWithFlags(a, ctx->stream, cudaEventRecordExternal);
   fn();
-  cudaEventRecord(b, ctx->stream);
+  cudaEventRecordWithFlags(b, ctx->stream, cudaEventRecordExternal);
   ctx->pending.push_back({kind, a, b});
+}
+
+// Elapsed time of event pairs that are nodes of a replayed graph (the events stay owned by it).
+static void harvest_graph(ext_ctx* ctx, const std::vector<Workspace::Ev>& ev) {
+  for (const auto& p : ev) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->prof_ms[p.kind] += ms;
+      ctx->prof_n[p.kind] += 1;
+    }
+  }
+  cudaGetLastError();
 }
 
 // After a stream synchronisation: fold the recorded event pairs into the per-kind totals.
@@ -437,11 +600,16 @@ static void harvest(ext_ctx* ctx) {
 }
 
 static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
-  const LaunchCfg g = cfg_of(ctx, W, 2);
+  LaunchCfg g = cfg_of(ctx, W, 2);
+  if (ctx->tc) {
+    const LaunchCfg vc = cfg_of(ctx, W, 1);
+    timed(ctx, EXT_KERNEL_SPLIT, [&] { launch_prec_tc_prepare(vc, mode, ctx->split); });
+    g.grid = std::max(1, std::min(W->n_gm, ctx->sm_count));
+  }
   for (int s = 0; s < 4; ++s) {
     timed(ctx, EXT_KERNEL_PREC0 + s, [&] {
-      if (ctx->opt.prec == EXT_PREC_FP32) launch_prec_simt(g, s, mode);
-      else launch_prec_tc(g, s, mode, ctx->opt.prec == EXT_PREC_MIXED_FP16 ? 0 : 1);
+      if (!ctx->tc) launch_prec_simt(g, s, mode);
+      else launch_prec_tc(g, s, mode, ctx->split, ctx->d_err);
     });
   }
 }
@@ -458,8 +626,8 @@ static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
 }
 
 static int ensure_graph(ext_ctx* ctx, Workspace* W) {
+  // with profiling on, the graph holds an event-record node before and after every kernel
   const int G = ctx->opt.iters_per_launch;
-  if (ctx->opt.profile) return EXT_OK;  // profiling launches every kernel directly
   if (W->graph && W->graph_iters == G) return EXT_OK;
   if (W->graph) {
     cudaGraphExecDestroy(W->graph);
@@ -468,9 +636,12 @@ static int ensure_graph(ext_ctx* ctx, Workspace* W) {
   cudaGraph_t g;
   BX_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   const int64_t before = ctx->launches;
+  const size_t pend0 = ctx->pending.size();
   enqueue_iterations(ctx, W, G);
   W->graph_nodes = ctx->launches - before;
   ctx->launches = before;  // captured, not launched
+  W->graph_events.assign(ctx->pending.begin() + pend0, ctx->pending.end());
+  ctx->pending.resize(pend0);
   cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
   if (e != cudaSuccess) {
     g_last_error = std::string("graph capture: ") + cudaGetErrorString(e);
@@ -552,15 +723,19 @@ static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const
   }
   max_blocks = max_blocks / std::max(1, W->graph_iters) + 8;
   for (int blk = 0; blk < max_blocks; ++blk) {
-    if (ctx->opt.profile) {
-      enqueue_iterations(ctx, W, ctx->opt.iters_per_launch);
-    } else {
-      BX_CUDA(cudaGraphLaunch(W->graph, s));
-      ctx->launches += W->graph_nodes;
-    }
+    BX_CUDA(cudaGraphLaunch(W->graph, s));
+    ctx->launches += W->graph_nodes;
     BX_CUDA(cudaMemcpyAsync(W->h_sc, W->d_sc, sizeof(SlotScalars) * count, cudaMemcpyDeviceToHost, s));
+    BX_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     BX_CUDA(cudaStreamSynchronize(s));
     harvest(ctx);
+    if (ctx->opt.profile) harvest_graph(ctx, W->graph_events);
+    if (*ctx->h_err) {
+      BX_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+      BX_CUDA(cudaStreamSynchronize(s));
+      g_last_error = "a bounded device wait in the tensor-core preconditioner ran out";
+      return EXT_ETIMEOUT;
+    }
     bool running = false;
     for (int i = 0; i < count; ++i)
       if (W->h_sc[i].status == ST_RUNNING) running = true;
@@ -670,6 +845,13 @@ int ext_create(const ext_options* opt, void* cuda_stream, ext_ctx** out) {
   ctx->cc_major = prop.major;
   ctx->cc_minor = prop.minor;
   if (o.prec != EXT_PREC_FP32 && !(prop.major == 10 && tc_supported())) return EXT_ENOTSUP;
+  ctx->tc = o.prec != EXT_PREC_FP32;
+  ctx->split = o.prec == EXT_PREC_MIXED_BF16 ? 1 : 0;
+  if (ctx->tc) BX_CUDA(tc_init());
+  BX_CUDA(cudaMalloc(&ctx->d_err, sizeof(int)));
+  BX_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
+  BX_CUDA(cudaMallocHost(&ctx->h_err, sizeof(int)));
+  *ctx->h_err = 0;
   if (cuda_stream) {
     ctx->stream = (cudaStream_t)cuda_stream;
   } else {
@@ -693,6 +875,8 @@ void ext_destroy(ext_ctx* ctx) {
     cudaFree(kv.second.tc);
   }
   harvest(ctx);
+  cudaFree(ctx->d_err);
+  cudaFreeHost(ctx->h_err);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
   delete ctx;

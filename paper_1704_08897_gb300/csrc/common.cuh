@@ -80,6 +80,13 @@ struct SlotDesc {
   const float* lamy;
   float wnorm;       // 1 / w_max, so that the scaled weights are <= 1
   int zero_mode;     // 1: drop the (0,0) mode (both axes symmetric/periodic)
+  // tensor-core path: split operand planes (2-byte elements) and their TMA descriptors
+  void* tc_r;        // [P][nyp][nxp]  scaled residual
+  void* tc_t1;       // [P][nxp][nyp]
+  void* tc_t2;       // [P][nyp][nxp]
+  void* tc_t3;       // [P][nxp][nyp]
+  const void* tmaps; // 8 CUtensorMap (64-byte aligned): A operand of stages 0..3, B of 0..3
+  int n_tc_tiles;    // output tiles of one tensor-core transform stage
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
 };
@@ -199,6 +206,37 @@ __device__ __forceinline__ int ghost(int i, int n, int bc, float& sgn) {
   if (i == -1 || i == n) { sgn = 0.f; return 0; }
   sgn = -1.f;
   return i < 0 ? -i - 2 : 2 * n - i;
+}
+
+// Spectral weight 1/(lam_y + lam_x)^2, normalised to <= 1; zero for padding and the constant
+// mode when both axes are symmetric/periodic (pseudo-inverse).
+__device__ __forceinline__ float spectral_weight(const SlotDesc& S, int kx, int ky) {
+  if (kx >= S.nx || ky >= S.ny) return 0.f;
+  const float s = S.lamy[ky] + S.lamx[kx];
+  if (!(s > 0.f)) return 0.f;
+  return S.wnorm / (s * s);
+}
+
+// Last item of stage 3 (thread 0): r.z, z.q -> rho, beta (flexible or Fletcher-Reeves).
+__device__ __forceinline__ void finish_preconditioner(const SlotDesc& S, double rz, double zq,
+                                                      int mode) {
+  SlotScalars* sc = S.sc;
+  if (mode == 2) {
+    sc->rho = rz;
+    sc->zq = zq;
+    return;
+  }
+  double beta = 0.0;
+  if (sc->it > 0) beta = sc->flexible ? -zq / sc->pq : rz / sc->rho;
+  sc->rho = rz;
+  sc->zq = zq;
+  sc->beta = beta;
+  if (!isfinite(rz) || !isfinite(beta)) {
+    sc->status = ST_EBREAKDOWN;
+    sc->active = 0;
+    sc->fold = 1;
+  }
+  if (mode == 1) sc->need_prec = 0;
 }
 
 }  // namespace bx

@@ -35,8 +35,14 @@ void launch_apply(const SlotDesc* slot, int n_tiles, bool aniso, const float* p,
 // mode 2: every slot (verification entry point).
 void launch_prec_simt(const LaunchCfg& c, int stage, int mode);
 
-// tensor-core variant (kernels_gemm_tc.cu): FP16 hi/lo or BF16 hi/mid/lo operand splits.
-void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind);
+// tensor-core variant (kernels_gemm_tc.cu): FP16 hi/lo (split_kind 0) or BF16 hi/mid/lo
+// (split_kind 1) operand planes; err receives 1 if a bounded wait ran out.
+void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int* err);
+// residual -> scaled planes of the first stage's A operand (vector work list)
+void launch_prec_tc_prepare(const LaunchCfg& c, int mode, int split_kind);
+int tc_planes(int split_kind);
 bool tc_supported();
+// opt the tensor-core kernels into their dynamic shared memory (once per process and device)
+cudaError_t tc_init();
 
 }  // namespace bx

@@ -49,37 +49,6 @@ __device__ __forceinline__ StageView stage_view(const SlotDesc& S, int stage) {
 
 }  // namespace
 
-// Spectral weight 1/(lam_y + lam_x)^2, normalised to <= 1; zero for padding and the constant
-// mode when both axes are symmetric/periodic (pseudo-inverse).
-__device__ __forceinline__ float spectral_weight(const SlotDesc& S, int kx, int ky) {
-  if (kx >= S.nx || ky >= S.ny) return 0.f;
-  const float s = S.lamy[ky] + S.lamx[kx];
-  if (!(s > 0.f)) return 0.f;
-  return S.wnorm / (s * s);
-}
-
-// Last item of stage 3 (thread 0): r.z, z.q -> rho, beta (flexible or Fletcher-Reeves).
-__device__ __forceinline__ void finish_preconditioner(const SlotDesc& S, double rz, double zq,
-                                                      int mode) {
-  SlotScalars* sc = S.sc;
-  if (mode == 2) {
-    sc->rho = rz;
-    sc->zq = zq;
-    return;
-  }
-  double beta = 0.0;
-  if (sc->it > 0) beta = sc->flexible ? -zq / sc->pq : rz / sc->rho;
-  sc->rho = rz;
-  sc->zq = zq;
-  sc->beta = beta;
-  if (!isfinite(rz) || !isfinite(beta)) {
-    sc->status = ST_EBREAKDOWN;
-    sc->active = 0;
-    sc->fold = 1;
-  }
-  if (mode == 1) sc->need_prec = 0;
-}
-
 template <int STAGE>
 __global__ void __launch_bounds__(NT)
 k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
