@@ -154,7 +154,9 @@ def run_ours(args, rank, world):
     prec = args.prec or cfg["prec"]
     cfg["prec"] = prec
     stream = torch.cuda.Stream()
-    ctx = ext.ext_create(ext.options(prec, rtol=1e-8), stream=stream)
+    # hard extend-out grids need up to ~10 n iterations at 1e-8 in FP32 arithmetic
+    maxit = 20 * max(max(p.nx, p.ny) for p in probs)
+    ctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=maxit), stream=stream)
     dprobs = [ext.problem_of(p) for p in probs]
     phis = [torch.from_numpy(p.phi).cuda() for p in probs]
     fs = [torch.from_numpy(p.f).cuda() for p in probs]
@@ -227,7 +229,7 @@ def run_ours(args, rank, world):
     # per-kernel CUDA-event durations of the same workload (a profiled pass: no graphs)
     roofline, kernels = None, None
     if not args.no_profile and rank == 0:
-        pctx = ext.ext_create(ext.options(prec, rtol=1e-8, profile=1), stream=stream)
+        pctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=maxit, profile=1), stream=stream)
         if len(probs) == 1:
             ext.ext_solve(pctx, dprobs[0], phis[0], fs[0], outs[0])
         else:

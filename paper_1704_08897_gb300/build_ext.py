@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiharm_ext.so")
-SOURCES = ["api.cu", "serve.cu", "kernels_grid.cu", "kernels_gemm_simt.cu", "kernels_gemm_tc.cu",
+SOURCES = ["api.cu", "kernels_grid.cu", "kernels_gemm_simt.cu", "kernels_gemm_tc.cu",
            "plan.cpp", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

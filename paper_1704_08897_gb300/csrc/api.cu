@@ -93,6 +93,7 @@ struct Workspace {
   std::vector<Ev> graph_events;  // profiling: event-record nodes of the graph
   bool aniso = false;
   bool host_io = false;
+  cudaStream_t stream = nullptr;  // the context's stream, or the serving worker's own
 };
 
 int plan_key(int n, int bc) { return n * 4 + bc; }
@@ -114,7 +115,8 @@ struct ext_ctx {
   int* d_err = nullptr;   // device flag raised by a bounded wait that ran out
   int* h_err = nullptr;   // pinned copy
   // launch accounting and optional per-kernel timing (ext_options.profile)
-  int64_t launches = 0;
+  std::atomic<int64_t> launches{0};
+  std::recursive_mutex plan_mu;  // plan cache: shared by user threads and the serving worker
   using Pending = Workspace::Ev;
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> ev_pool;
@@ -190,26 +192,34 @@ static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint
   return EXT_OK;
 }
 
-// Planes of v (exact FP64 input): FP16 hi/lo of v * 2^6, or BF16 hi/mid/lo of v.
-static void split_host(double v, int split, uint16_t* out, size_t plane, size_t idx) {
-  if (split == 0) {
-    v *= 64.0;
-    const __half h = __double2half(v);
-    const double r = v - (double)__half2float(h);
-    out[idx] = __half_as_ushort(h);
-    out[plane + idx] = __half_as_ushort(__double2half(r));
-  } else {
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    const double r1 = v - (double)__bfloat162float(h);
-    const __nv_bfloat16 m = __double2bfloat16(r1);
-    const double r2 = r1 - (double)__bfloat162float(m);
-    out[idx] = __bfloat16_as_ushort(h);
-    out[plane + idx] = __bfloat16_as_ushort(m);
-    out[2 * plane + idx] = __bfloat16_as_ushort(__double2bfloat16(r2));
-  }
+// Three integer slices of v for block exponent E (v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24)),
+// stored as FP16 or BF16 (integers of at most 9 bits are exact in both).
+static void slice_host(double v, int E, int split, uint16_t* out, size_t plane, size_t idx) {
+  const double c0 = std::nearbyint(std::ldexp(v, 8 - E));
+  const double r1 = v - std::ldexp(c0, E - 8);
+  const double c1 = std::nearbyint(std::ldexp(r1, 16 - E));
+  const double r2 = r1 - std::ldexp(c1, E - 16);
+  const double c2 = std::nearbyint(std::ldexp(r2, 24 - E));
+  const double c[3] = {c0, c1, c2};
+  for (int k = 0; k < 3; ++k)
+    out[k * plane + idx] = split == 0 ? __half_as_ushort(__double2half(c[k]))
+                                      : __bfloat16_as_ushort(__double2bfloat16(c[k]));
 }
 
-// Q and Q^T of one axis as split planes, zero-padded to np x np: [Q planes][Q^T planes].
+// Block exponent of `count` values: max |v| < 2^E and max |v| 2^(8-E) < 255.5 (the leading
+// slice stays within +-255); 0 for an all-zero block.
+static int block_exp_host(const double* v, size_t stride, int count) {
+  double m = 0.0;
+  for (int k = 0; k < count; ++k) m = std::max(m, std::fabs(v[k * stride]));
+  if (!(m > 0.0)) return 0;
+  int e;
+  std::frexp(m, &e);
+  if (std::ldexp(m, 8 - e) >= 255.5) ++e;
+  return std::max(e, -100);
+}
+
+// Q and Q^T of one axis as block-scaled slices (zero-padded to np x np) with their exponents:
+// [Q slices (3 planes)][Q^T slices (3 planes)][exponents of Q rows][exponents of Q^T rows].
 static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
   if (P->tc && P->tc_split == ctx->split) return EXT_OK;
   if (P->tc) {
@@ -217,23 +227,46 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
     P->tc = nullptr;
   }
   const int NS = tc_planes(ctx->split);
-  const size_t plane = (size_t)P->np * P->np;
+  const int np = P->np, n = P->n, nkb = np / 128;
+  const size_t plane = (size_t)np * np;
   std::vector<uint16_t> h(2 * NS * plane, 0);
-  AxisBasis B = make_axis_basis(P->n, P->bc);
-  for (int i = 0; i < P->n; ++i)
-    for (int k = 0; k < P->n; ++k) {
-      const double v = B.Q[(size_t)i * P->n + k];
-      split_host(v, ctx->split, h.data(), plane, (size_t)i * P->np + k);                 // Q[i][k]
-      split_host(v, ctx->split, h.data() + NS * plane, plane, (size_t)k * P->np + i);    // Q^T[k][i]
+  std::vector<int8_t> ex(2 * (size_t)np * nkb, 0);
+  AxisBasis B = make_axis_basis(n, P->bc);
+  std::vector<double> Qp((size_t)np * np, 0.0), QTp((size_t)np * np, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) {
+      Qp[(size_t)i * np + k] = B.Q[(size_t)i * n + k];
+      QTp[(size_t)k * np + i] = B.Q[(size_t)i * n + k];
     }
-  if (cudaMalloc(&P->tc, 2 * h.size()) != cudaSuccess) {
+  for (int t = 0; t < 2; ++t) {
+    const std::vector<double>& M = t == 0 ? Qp : QTp;
+    uint16_t* out = h.data() + t * NS * plane;
+    int8_t* eo = ex.data() + t * (size_t)np * nkb;
+    for (int row = 0; row < np; ++row)
+      for (int kb = 0; kb < nkb; ++kb) {
+        const double* blk = M.data() + (size_t)row * np + kb * 128;
+        const int E = block_exp_host(blk, 1, 128);
+        eo[(size_t)row * nkb + kb] = (int8_t)E;
+        for (int k = 0; k < 128; ++k) slice_host(blk[k], E, ctx->split, out, plane, (size_t)row * np + kb * 128 + k);
+      }
+  }
+  const size_t bytes = 2 * h.size() + ex.size();
+  if (cudaMalloc(&P->tc, bytes) != cudaSuccess) {
     cudaGetLastError();
     g_last_error = "cudaMalloc of tensor-core plan failed";
     return EXT_ENOMEM;
   }
   BX_CUDA(cudaMemcpy(P->tc, h.data(), 2 * h.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy((char*)P->tc + 2 * h.size(), ex.data(), ex.size(), cudaMemcpyHostToDevice));
   P->tc_split = ctx->split;
   return EXT_OK;
+}
+
+// Exponent arrays of a plan: t = 0 for Q rows, 1 for Q^T rows.
+static const int8_t* plan_exps(const PlanDev* P, int t) {
+  const size_t plane = (size_t)P->np * P->np;
+  const size_t nkb = P->np / 128;
+  return (const int8_t*)((const char*)P->tc + 2 * 2 * 3 * plane) + t * (size_t)P->np * nkb;
 }
 
 static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {
@@ -319,6 +352,160 @@ static std::string shape_key(int count, const ext_problem* probs, bool host_io) 
 }
 
 // Build the device state of `count` problems (no inputs yet).
+// Device state of one problem: plans, arena layout (allocated here unless `arena` is given),
+// slot descriptor and tensor maps.  With size_only, only s.bytes is computed.
+static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotHost& s,
+                      char* arena = nullptr, bool size_only = false) {
+  std::lock_guard<std::recursive_mutex> plk(ctx->plan_mu);
+  s.prob = prob;
+  s.d = SlotDesc{};
+  const int nx = prob.nx, ny = prob.ny;
+  PlanDev *px, *py;
+  int rc = get_plan(ctx, nx, prob.bc_x, &px);
+  if (rc) return rc;
+  rc = get_plan(ctx, ny, prob.bc_y, &py);
+  if (rc) return rc;
+  SlotDesc& d = s.d;
+  d.nx = nx;
+  d.ny = ny;
+  d.nxp = px->np;
+  d.nyp = py->np;
+  d.bcx = prob.bc_x;
+  d.bcy = prob.bc_y;
+  d.n_st_tiles = ((nx + kStTileX - 1) / kStTileX) * ((ny + kStTileY - 1) / kStTileY);
+  const size_t N = (size_t)nx * ny;
+  d.n_vec_items = (int)((N + kVecChunk - 1) / kVecChunk);
+  const int n_gm = (d.nxp / 128) * (d.nyp / 64);
+  d.n_gm_tiles = n_gm;
+  set_weights(d, prob.hx, prob.hy);
+  const int n_part = std::max(d.n_st_tiles, std::max(d.n_vec_items, n_gm));
+  const size_t Np = (size_t)d.nxp * d.nyp;
+  // arena layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
+  const size_t o_b = take(8 * N), o_x = take(4 * N), o_xl = take(4 * N);
+  const size_t o_part = take(8 * 4 * (size_t)n_part);
+  const size_t o_r = take(4 * N), o_p0 = take(4 * N), o_p1 = take(4 * N);
+  const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
+  const size_t fp = ctx->tc ? 0 : 4 * Np;  // SIMT transform intermediates
+  const size_t o_t1 = take(fp), o_t2 = take(fp), o_t3 = take(fp);
+  const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
+  size_t o_io = 0;
+  if (host_io) o_io = take(12 * N);
+  const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
+  size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0;
+  const size_t nex = Np / 64;  // block exponents of one operand
+  if (ctx->tc) {
+    o_tr = take(2 * NS * Np);
+    o_tt1 = take(2 * NS * Np);
+    o_tt2 = take(2 * NS * Np);
+    o_tt3 = take(2 * NS * Np);
+    o_maps = take(8 * sizeof(CUtensorMap));
+    o_ex = take(4 * nex);
+  }
+  s.bytes = off;
+  if (size_only) return EXT_OK;
+  if (arena) {
+    s.arena = arena;
+  } else if (cudaMalloc(&s.arena, s.bytes) != cudaSuccess) {
+    cudaGetLastError();
+    s.arena = nullptr;
+    g_last_error = "cudaMalloc of solve workspace failed";
+    return EXT_ENOMEM;
+  }
+  char* A = s.arena;
+  d.b = (double*)(A + o_b);
+  d.xhi = (float*)(A + o_x);
+  d.xlo = (float*)(A + o_xl);  // own 256-byte aligned slot: the update kernel loads float4
+  d.part = (double*)(A + o_part);
+  d.r = (float*)(A + o_r);
+  d.p[0] = (float*)(A + o_p0);
+  d.p[1] = (float*)(A + o_p1);
+  d.q = (float*)(A + o_q);
+  d.z = (float*)(A + o_z);
+  d.mask = (uint8_t*)(A + o_mask);
+  d.t1 = (float*)(A + o_t1);
+  d.t2 = (float*)(A + o_t2);
+  d.t3 = (float*)(A + o_t3);
+  d.rin = nullptr;
+  d.n_tc_tiles = n_gm;
+  if (ctx->tc) {
+    int rc2 = ensure_tc_plan(ctx, px);
+    if (!rc2) rc2 = ensure_tc_plan(ctx, py);
+    if (rc2) return rc2;
+    d.tc_r = A + o_tr;
+    d.tc_t1 = A + o_tt1;
+    d.tc_t2 = A + o_tt2;
+    d.tc_t3 = A + o_tt3;
+    d.tmaps = A + o_maps;
+    for (int k = 0; k < 4; ++k) d.tc_e[k] = (int8_t*)(A + o_ex + k * nex);
+    d.tc_eb[0] = plan_exps(px, 1);  // Qx^T rows
+    d.tc_eb[1] = plan_exps(py, 1);  // Qy^T rows
+    d.tc_eb[2] = plan_exps(px, 0);  // Qx rows
+    d.tc_eb[3] = plan_exps(py, 0);  // Qy rows
+    BX_CUDA(cudaMemset(d.tc_r, 0, 2 * NS * Np));
+    BX_CUDA(cudaMemset(A + o_ex, 0, 4 * nex));
+    const bool bf = ctx->split == 1;
+    const size_t qplane = 0;
+    (void)qplane;
+    CUtensorMap maps[8];
+    const size_t pxp = (size_t)d.nxp * d.nxp, pyp = (size_t)d.nyp * d.nyp;
+    uint16_t* qxb = (uint16_t*)px->tc;
+    uint16_t* qyb = (uint16_t*)py->tc;
+    // A operands: r planes [P][nyp][nxp], T1 [P][nxp][nyp], T2 [P][nyp][nxp], T3 [P][nxp][nyp]
+    int rc3 = make_tmap(&maps[0], d.tc_r, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
+    if (!rc3) rc3 = make_tmap(&maps[1], d.tc_t1, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
+    if (!rc3) rc3 = make_tmap(&maps[2], d.tc_t2, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
+    if (!rc3) rc3 = make_tmap(&maps[3], d.tc_t3, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
+    // B operands: Qx^T, Qy^T, Qx, Qy planes
+    if (!rc3) rc3 = make_tmap(&maps[4], qxb + NS * pxp, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
+    if (!rc3) rc3 = make_tmap(&maps[5], qyb + NS * pyp, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
+    if (!rc3) rc3 = make_tmap(&maps[6], qxb, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
+    if (!rc3) rc3 = make_tmap(&maps[7], qyb, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
+    if (rc3) return rc3;
+    BX_CUDA(cudaMemcpy(A + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  }
+  d.qx = px->q;
+  d.qxt = px->qt;
+  d.qy = py->q;
+  d.qyt = py->qt;
+  if (host_io) {
+    s.phi_stage = (float*)(A + o_io);
+    s.f_stage = s.phi_stage + N;
+    s.out_stage = s.f_stage + N;
+  }
+  // eigenvalues of L_x, L_y scaled like the stencil weights, and the weight normaliser
+  double a = 1.0 / (prob.hx * prob.hx), c = 1.0 / (prob.hy * prob.hy);
+  const double m = std::max(a, c);
+  a /= m;
+  c /= m;
+  std::vector<float> lx(d.nxp, 0.f), ly(d.nyp, 0.f);
+  for (int k = 0; k < nx; ++k) lx[k] = (float)(px->lam[k] * a);
+  for (int k = 0; k < ny; ++k) ly[k] = (float)(py->lam[k] * c);
+  double smin;
+  // smallest nonzero eigenvalue sum: min over the two axes' smallest entries
+  double mx0 = 1e300, mx1 = 1e300, my0 = 1e300, my1 = 1e300;  // smallest, smallest nonzero
+  for (int k = 0; k < nx; ++k) {
+    const double v = (float)(px->lam[k] * a);
+    mx0 = std::min(mx0, v);
+    if (v > 0) mx1 = std::min(mx1, v);
+  }
+  for (int k = 0; k < ny; ++k) {
+    const double v = (float)(py->lam[k] * c);
+    my0 = std::min(my0, v);
+    if (v > 0) my1 = std::min(my1, v);
+  }
+  smin = mx0 + my0;
+  if (!(smin > 0)) smin = std::min(mx0 + my1, mx1 + my0);
+  d.wnorm = (float)(smin * smin);
+  d.zero_mode = (prob.bc_x != EXT_BC_DIRICHLET && prob.bc_y != EXT_BC_DIRICHLET);
+  d.lamx = (const float*)(A + o_lx);
+  d.lamy = (const float*)(A + o_ly);
+  BX_CUDA(cudaMemcpy(A + o_lx, lx.data(), 4 * lx.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(A + o_ly, ly.data(), 4 * ly.size(), cudaMemcpyHostToDevice));
+  return EXT_OK;
+}
+
 static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bool host_io,
                            Workspace** out) {
   std::unique_ptr<Workspace> W(new Workspace());
@@ -328,149 +515,17 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   std::vector<WorkItem> st, vec, gm;
   for (int i = 0; i < count; ++i) {
     SlotHost& s = W->slots[i];
-    s.prob = probs[i];
-    const int nx = probs[i].nx, ny = probs[i].ny;
-    PlanDev *px, *py;
-    int rc = get_plan(ctx, nx, probs[i].bc_x, &px);
-    if (rc) return rc;
-    rc = get_plan(ctx, ny, probs[i].bc_y, &py);
-    if (rc) return rc;
-    SlotDesc& d = s.d;
-    d.nx = nx;
-    d.ny = ny;
-    d.nxp = px->np;
-    d.nyp = py->np;
-    d.bcx = probs[i].bc_x;
-    d.bcy = probs[i].bc_y;
-    d.n_st_tiles = ((nx + kStTileX - 1) / kStTileX) * ((ny + kStTileY - 1) / kStTileY);
-    const size_t N = (size_t)nx * ny;
-    d.n_vec_items = (int)((N + kVecChunk - 1) / kVecChunk);
-    const int n_gm = (d.nxp / 128) * (d.nyp / 64);
-    d.n_gm_tiles = n_gm;
-    set_weights(d, probs[i].hx, probs[i].hy);
-    if (d.aniso) W->aniso = true;
-    const int n_part = std::max(d.n_st_tiles, std::max(d.n_vec_items, n_gm));
-    const size_t Np = (size_t)d.nxp * d.nyp;
-    // arena layout
-    size_t off = 0;
-    auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
-    const size_t o_b = take(8 * N), o_x = take(8 * N), o_part = take(8 * 4 * (size_t)n_part);
-    const size_t o_r = take(4 * N), o_p0 = take(4 * N), o_p1 = take(4 * N);
-    const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
-    const size_t o_t1 = take(4 * Np), o_t2 = take(4 * Np), o_t3 = take(4 * Np);
-    const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
-    size_t o_io = 0;
-    if (host_io) o_io = take(12 * N);
-    const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
-    size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0;
-    if (ctx->tc) {
-      o_tr = take(2 * NS * Np);
-      o_tt1 = take(2 * NS * Np);
-      o_tt2 = take(2 * NS * Np);
-      o_tt3 = take(2 * NS * Np);
-      o_maps = take(8 * sizeof(CUtensorMap));
-    }
-    s.bytes = off;
-    if (cudaMalloc(&s.arena, s.bytes) != cudaSuccess) {
-      cudaGetLastError();
+    int rc = build_slot(ctx, probs[i], host_io, s);
+    if (rc) {
       for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
-      g_last_error = "cudaMalloc of solve workspace failed";
-      return EXT_ENOMEM;
+      cudaFree(s.arena);
+      return rc;
     }
-    char* A = s.arena;
-    d.b = (double*)(A + o_b);
-    d.xhat = (double*)(A + o_x);
-    d.part = (double*)(A + o_part);
-    d.r = (float*)(A + o_r);
-    d.p[0] = (float*)(A + o_p0);
-    d.p[1] = (float*)(A + o_p1);
-    d.q = (float*)(A + o_q);
-    d.z = (float*)(A + o_z);
-    d.mask = (uint8_t*)(A + o_mask);
-    d.t1 = (float*)(A + o_t1);
-    d.t2 = (float*)(A + o_t2);
-    d.t3 = (float*)(A + o_t3);
-    d.rin = nullptr;
-    d.n_tc_tiles = n_gm;
-    if (ctx->tc) {
-      int rc2 = ensure_tc_plan(ctx, px);
-      if (!rc2) rc2 = ensure_tc_plan(ctx, py);
-      if (rc2) {
-        cudaFree(s.arena);
-        for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
-        return rc2;
-      }
-      d.tc_r = A + o_tr;
-      d.tc_t1 = A + o_tt1;
-      d.tc_t2 = A + o_tt2;
-      d.tc_t3 = A + o_tt3;
-      d.tmaps = A + o_maps;
-      BX_CUDA(cudaMemset(d.tc_r, 0, 2 * NS * Np));
-      const bool bf = ctx->split == 1;
-      const size_t qplane = 0;
-      (void)qplane;
-      CUtensorMap maps[8];
-      const size_t pxp = (size_t)d.nxp * d.nxp, pyp = (size_t)d.nyp * d.nyp;
-      uint16_t* qxb = (uint16_t*)px->tc;
-      uint16_t* qyb = (uint16_t*)py->tc;
-      // A operands: r planes [P][nyp][nxp], T1 [P][nxp][nyp], T2 [P][nyp][nxp], T3 [P][nxp][nyp]
-      int rc3 = make_tmap(&maps[0], d.tc_r, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
-      if (!rc3) rc3 = make_tmap(&maps[1], d.tc_t1, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
-      if (!rc3) rc3 = make_tmap(&maps[2], d.tc_t2, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
-      if (!rc3) rc3 = make_tmap(&maps[3], d.tc_t3, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
-      // B operands: Qx^T, Qy^T, Qx, Qy planes
-      if (!rc3) rc3 = make_tmap(&maps[4], qxb + NS * pxp, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
-      if (!rc3) rc3 = make_tmap(&maps[5], qyb + NS * pyp, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
-      if (!rc3) rc3 = make_tmap(&maps[6], qxb, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
-      if (!rc3) rc3 = make_tmap(&maps[7], qyb, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
-      if (rc3) {
-        cudaFree(s.arena);
-        for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
-        return rc3;
-      }
-      BX_CUDA(cudaMemcpy(A + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
-    }
-    d.qx = px->q;
-    d.qxt = px->qt;
-    d.qy = py->q;
-    d.qyt = py->qt;
-    if (host_io) {
-      s.phi_stage = (float*)(A + o_io);
-      s.f_stage = s.phi_stage + N;
-      s.out_stage = s.f_stage + N;
-    }
-    // eigenvalues of L_x, L_y scaled like the stencil weights, and the weight normaliser
-    double a = 1.0 / (probs[i].hx * probs[i].hx), c = 1.0 / (probs[i].hy * probs[i].hy);
-    const double m = std::max(a, c);
-    a /= m;
-    c /= m;
-    std::vector<float> lx(d.nxp, 0.f), ly(d.nyp, 0.f);
-    for (int k = 0; k < nx; ++k) lx[k] = (float)(px->lam[k] * a);
-    for (int k = 0; k < ny; ++k) ly[k] = (float)(py->lam[k] * c);
-    double smin;
-    // smallest nonzero eigenvalue sum: min over the two axes' smallest entries
-    double mx0 = 1e300, mx1 = 1e300, my0 = 1e300, my1 = 1e300;  // smallest, smallest nonzero
-    for (int k = 0; k < nx; ++k) {
-      const double v = (float)(px->lam[k] * a);
-      mx0 = std::min(mx0, v);
-      if (v > 0) mx1 = std::min(mx1, v);
-    }
-    for (int k = 0; k < ny; ++k) {
-      const double v = (float)(py->lam[k] * c);
-      my0 = std::min(my0, v);
-      if (v > 0) my1 = std::min(my1, v);
-    }
-    smin = mx0 + my0;
-    if (!(smin > 0)) smin = std::min(mx0 + my1, mx1 + my0);
-    d.wnorm = (float)(smin * smin);
-    d.zero_mode = (probs[i].bc_x != EXT_BC_DIRICHLET && probs[i].bc_y != EXT_BC_DIRICHLET);
-    d.lamx = (const float*)(A + o_lx);
-    d.lamy = (const float*)(A + o_ly);
-    BX_CUDA(cudaMemcpy(A + o_lx, lx.data(), 4 * lx.size(), cudaMemcpyHostToDevice));
-    BX_CUDA(cudaMemcpy(A + o_ly, ly.data(), 4 * ly.size(), cudaMemcpyHostToDevice));
+    SlotDesc& d = s.d;
+    if (d.aniso) W->aniso = true;
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
-    for (int t = 0; t < n_gm; ++t) gm.push_back({i, t});
+    for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
   }
   W->n_st = (int)st.size();
   W->n_vec = (int)vec.size();
@@ -526,7 +581,7 @@ static int get_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bool
 static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
   LaunchCfg c;
   c.slots = W->d_slots;
-  c.stream = ctx->stream;
+  c.stream = W->stream ? W->stream : ctx->stream;
   const int cap = ctx->sm_count * 8;
   if (which == 0) {
     c.items = W->d_st;
@@ -558,17 +613,21 @@ static cudaEvent_t ev_get(ext_ctx* ctx) {
 // Launch one kernel (fn), counting it; in profiling mode bracket it with CUDA events on the
 // context's stream.  Never used while a graph is being captured with profiling on.
 template <class F>
-static void timed(ext_ctx* ctx, int kind, F&& fn) {
+static void timed(ext_ctx* ctx, int kind, F&& fn, cudaStream_t st = nullptr) {
   ctx->launches += 1;
   if (!ctx->opt.profile) {
     fn();
     return;
   }
+  if (!st) st = ctx->stream;
   cudaEvent_t a = ev_get(ctx), b = ev_get(ctx);
-  // External: under stream capture the records become timing nodes of the graph
-  cudaEventRecordWithFlags(a, ctx->stream, cudaEventRecordExternal);
+  // under stream capture the records must be external to become timing nodes of the graph
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  const unsigned flags = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : cudaEventRecordDefault;
+  cudaEventRecordWithFlags(a, st, flags);
   fn();
-  cudaEventRecordWithFlags(b, ctx->stream, cudaEventRecordExternal);
+  cudaEventRecordWithFlags(b, st, flags);
   ctx->pending.push_back({kind, a, b});
 }
 
@@ -602,26 +661,26 @@ static void harvest(ext_ctx* ctx) {
 static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
   LaunchCfg g = cfg_of(ctx, W, 2);
   if (ctx->tc) {
-    const LaunchCfg vc = cfg_of(ctx, W, 1);
-    timed(ctx, EXT_KERNEL_SPLIT, [&] { launch_prec_tc_prepare(vc, mode, ctx->split); });
+    const LaunchCfg st = cfg_of(ctx, W, 0);
+    timed(ctx, EXT_KERNEL_SPLIT, [&] { launch_prec_tc_prepare(st, mode, ctx->split); }, g.stream);
     g.grid = std::max(1, std::min(W->n_gm, ctx->sm_count));
   }
   for (int s = 0; s < 4; ++s) {
     timed(ctx, EXT_KERNEL_PREC0 + s, [&] {
       if (!ctx->tc) launch_prec_simt(g, s, mode);
       else launch_prec_tc(g, s, mode, ctx->split, ctx->d_err);
-    });
+    }, g.stream);
   }
 }
 
 static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
   const LaunchCfg st = cfg_of(ctx, W, 0), vc = cfg_of(ctx, W, 1);
   for (int i = 0; i < iters; ++i) {
-    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(st, W->aniso); });
-    timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); });
+    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(st, W->aniso); }, st.stream);
+    timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); }, st.stream);
     launch_prec(ctx, W, 0);
   }
-  timed(ctx, EXT_KERNEL_TRUE_RESIDUAL, [&] { launch_true_residual(st); });
+  timed(ctx, EXT_KERNEL_TRUE_RESIDUAL, [&] { launch_true_residual(st); }, st.stream);
   launch_prec(ctx, W, 1);
 }
 
@@ -634,15 +693,25 @@ static int ensure_graph(ext_ctx* ctx, Workspace* W) {
     W->graph = nullptr;
   }
   cudaGraph_t g;
-  BX_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-  const int64_t before = ctx->launches;
+  if (ctx->opt.profile) {
+    // events for the graph's timing nodes are created before capture begins
+    const size_t need = 2 * (size_t)(8 * G + 16);
+    while (ctx->ev_pool.size() < need) {
+      cudaEvent_t e = nullptr;
+      BX_CUDA(cudaEventCreate(&e));
+      ctx->ev_pool.push_back(e);
+    }
+  }
+  cudaStream_t cstream = W->stream ? W->stream : ctx->stream;
+  BX_CUDA(cudaStreamBeginCapture(cstream, cudaStreamCaptureModeThreadLocal));
+  const int64_t before = ctx->launches.load();
   const size_t pend0 = ctx->pending.size();
   enqueue_iterations(ctx, W, G);
   W->graph_nodes = ctx->launches - before;
   ctx->launches = before;  // captured, not launched
   W->graph_events.assign(ctx->pending.begin() + pend0, ctx->pending.end());
   ctx->pending.resize(pend0);
-  cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+  cudaError_t e = cudaStreamEndCapture(cstream, &g);
   if (e != cudaSuccess) {
     g_last_error = std::string("graph capture: ") + cudaGetErrorString(e);
     return EXT_ECUDA;
@@ -944,7 +1013,7 @@ int ext_profile_read(ext_ctx* ctx, int kinds, double* total_ms, int64_t* launche
   return EXT_OK;
 }
 
-int64_t ext_launch_count(ext_ctx* ctx) { return ctx ? ctx->launches : 0; }
+int64_t ext_launch_count(ext_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
 // ---- verification entry points (device pointers) ----
 
@@ -1039,13 +1108,472 @@ int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float*
 
 }  // extern "C"
 
-// Serving loop lives in serve.cu; until it is linked these stubs keep the ABI complete.
+
+// ---------------------------------------------------------------------------------------------
+// Serving: continuous batching of independent extension requests.
+//
+// A worker thread owns its own stream and a fixed table of max_slots slots.  Between blocks of
+// G iterations it (1) admits queued requests while the HBM footprint of the admitted slots
+// stays within the budget, runs their set-up and first preconditioner pass, (2) replays the
+// iteration graph over every slot that is still iterating (new and old together), and (3)
+// retires slots whose solve has a final status: output kernel, copy-out for host buffers,
+// result record, arena back to a size-keyed pool.  Work lists live in fixed device buffers
+// that are rewritten when slots join or leave, so one captured graph serves every mix.
+// ---------------------------------------------------------------------------------------------
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Req {
+  uint64_t ticket = 0;
+  ext_problem prob{};
+  const float* phi = nullptr;
+  const float* f = nullptr;
+  float* out = nullptr;
+  bool host_io = false;
+  int status = EXT_PENDING;
+  ext_result res{};
+  Clock::time_point t_submit, t_admit;
+};
+
+struct ServeSlot {
+  bool used = false;
+  Req* req = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct ext_ctx::Serve {
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv, cv_done;
+  bool stop = false;
+  std::deque<Req*> queue;
+  std::unordered_map<uint64_t, Req*> reqs;
+  uint64_t next_ticket = 1;
+  int in_flight = 0;
+  int worker_error = EXT_OK;
+  Workspace* W = nullptr;       // capacity-sized slot table, work lists and graph
+  std::vector<ServeSlot> slots;
+  std::multimap<size_t, char*> pool;  // free arenas by size
+  size_t budget = 0, used = 0;
+  int cap_items = 0;
+  WorkItem *d_new = nullptr, *d_ret = nullptr;
+  int* d_aux = nullptr;          // [0] new stencil items, [1] retiring vector items
+  int* h_aux = nullptr;
+};
+
+static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
+  Workspace* W = S->W;
+  cudaFree(W->d_st);
+  cudaFree(W->d_vec);
+  cudaFree(W->d_gm);
+  cudaFree(S->d_new);
+  cudaFree(S->d_ret);
+  W->d_st = W->d_vec = W->d_gm = S->d_new = S->d_ret = nullptr;
+  BX_CUDA(cudaMalloc(&W->d_st, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_vec, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_gm, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&S->d_new, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&S->d_ret, sizeof(WorkItem) * cap));
+  S->cap_items = cap;
+  W->n_st = W->n_vec = W->n_gm = cap;  // persistent grids sized for the capacity
+  if (W->graph) {
+    cudaGraphExecDestroy(W->graph);
+    W->graph = nullptr;
+  }
+  return EXT_OK;
+}
+
+static int serve_init(ext_ctx* ctx) {
+  std::unique_ptr<ext_ctx::Serve> S(new ext_ctx::Serve());
+  const int cap = ctx->opt.max_slots;
+  S->slots.resize(cap);
+  Workspace* W = new Workspace();
+  S->W = W;
+  W->slots.resize(cap);
+  BX_CUDA(cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking));
+  BX_CUDA(cudaMalloc(&W->d_slots, sizeof(SlotDesc) * cap));
+  BX_CUDA(cudaMalloc(&W->d_sc, sizeof(SlotScalars) * cap));
+  BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * cap));
+  BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * cap));
+  memset(W->h_sc, 0, sizeof(SlotScalars) * cap);
+  BX_CUDA(cudaMalloc(&W->d_counts, 3 * sizeof(int)));
+  BX_CUDA(cudaMemset(W->d_counts, 0, 3 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * cap));
+  BX_CUDA(cudaMalloc(&W->d_fs, sizeof(void*) * cap));
+  BX_CUDA(cudaMalloc(&W->d_outs, sizeof(void*) * cap));
+  BX_CUDA(cudaMalloc(&W->d_dirs, sizeof(int) * cap));
+  BX_CUDA(cudaMallocHost(&W->h_ptrs, (3 * sizeof(void*) + sizeof(int)) * cap));
+  BX_CUDA(cudaMalloc(&S->d_aux, 2 * sizeof(int)));
+  BX_CUDA(cudaMallocHost(&S->h_aux, 2 * sizeof(int)));
+  int rc = serve_alloc_lists(S.get(), 1 << 16);
+  if (rc) return rc;
+  size_t fr = 0, tot = 0;
+  BX_CUDA(cudaMemGetInfo(&fr, &tot));
+  S->budget = ctx->opt.hbm_budget ? ctx->opt.hbm_budget : fr / 2;
+  ctx->serve = S.release();
+  return EXT_OK;
+}
+
+// Rewrite the device work lists from the slots in use (in slot order).
+static int serve_rebuild_lists(ext_ctx* ctx) {
+  ext_ctx::Serve* S = ctx->serve;
+  Workspace* W = S->W;
+  std::vector<WorkItem> st, vec, gm;
+  bool aniso = false;
+  for (int i = 0; i < (int)S->slots.size(); ++i) {
+    if (!S->slots[i].used) continue;
+    const SlotDesc& d = W->slots[i].d;
+    aniso |= d.aniso != 0;
+    for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
+    for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
+    for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
+  }
+  const int need = (int)std::max(st.size(), std::max(vec.size(), gm.size()));
+  if (need > S->cap_items) {
+    int cap = S->cap_items;
+    while (cap < need) cap *= 2;
+    BX_CUDA(cudaStreamSynchronize(W->stream));
+    int rc = serve_alloc_lists(S, cap);
+    if (rc) return rc;
+  }
+  if (aniso != W->aniso && W->graph) {
+    cudaGraphExecDestroy(W->graph);
+    W->graph = nullptr;
+  }
+  W->aniso = aniso;
+  cudaStream_t s = W->stream;
+  if (!st.empty()) BX_CUDA(cudaMemcpyAsync(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice, s));
+  if (!vec.empty()) BX_CUDA(cudaMemcpyAsync(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice, s));
+  if (!gm.empty()) BX_CUDA(cudaMemcpyAsync(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice, s));
+  int counts[3] = {(int)st.size(), (int)vec.size(), (int)gm.size()};
+  BX_CUDA(cudaMemcpyAsync(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
+  // the host vectors die here: the copies above must finish first (pageable sources are staged)
+  BX_CUDA(cudaStreamSynchronize(s));
+  return EXT_OK;
+}
+
+static void finish_req(ext_ctx::Serve* S, Req* r, int status) {
+  r->status = status;
+  S->in_flight -= 1;
+  S->cv_done.notify_all();
+}
+
+// Admit queued requests into free slots while the footprint fits; returns admitted slot indices.
+static std::vector<int> serve_admit(ext_ctx* ctx) {
+  ext_ctx::Serve* S = ctx->serve;
+  std::vector<int> admitted;
+  while (!S->queue.empty()) {
+    int free_slot = -1;
+    for (int i = 0; i < (int)S->slots.size(); ++i)
+      if (!S->slots[i].used) {
+        free_slot = i;
+        break;
+      }
+    if (free_slot < 0) break;
+    Req* r = S->queue.front();
+    SlotHost probe;
+    int rc = build_slot(ctx, r->prob, r->host_io, probe, nullptr, true);
+    if (rc) {
+      S->queue.pop_front();
+      finish_req(S, r, rc);
+      continue;
+    }
+    if (probe.bytes > S->budget) {
+      S->queue.pop_front();
+      finish_req(S, r, EXT_EADMIT);
+      continue;
+    }
+    if (S->used + probe.bytes > S->budget) break;  // wait for running solves to free memory
+    S->queue.pop_front();
+    S->slots[free_slot].used = true;
+    S->slots[free_slot].req = r;
+    S->slots[free_slot].bytes = probe.bytes;
+    S->used += probe.bytes;
+    r->t_admit = Clock::now();
+    admitted.push_back(free_slot);
+  }
+  return admitted;
+}
+
+static int serve_setup_slots(ext_ctx* ctx, const std::vector<int>& admitted) {
+  ext_ctx::Serve* S = ctx->serve;
+  Workspace* W = S->W;
+  cudaStream_t s = W->stream;
+  const int cap = (int)S->slots.size();
+  const float** h_phis = (const float**)W->h_ptrs;
+  const float** h_fs = h_phis + cap;
+  float** h_outs = (float**)(h_fs + cap);
+  int* h_dirs = (int*)(h_outs + cap);
+  std::vector<WorkItem> fresh;
+  for (int i : admitted) {
+    Req* r = S->slots[i].req;
+    SlotHost& sl = W->slots[i];
+    char* arena = nullptr;
+    auto it = S->pool.find(S->slots[i].bytes);
+    if (it != S->pool.end()) {
+      arena = it->second;
+      S->pool.erase(it);
+    }
+    int rc = build_slot(ctx, r->prob, r->host_io, sl, arena);
+    if (rc) return rc;
+    sl.d.sc = W->d_sc + i;
+    const size_t N = (size_t)r->prob.nx * r->prob.ny;
+    if (r->host_io) {
+      BX_CUDA(cudaMemcpyAsync(sl.phi_stage, r->phi, 4 * N, cudaMemcpyHostToDevice, s));
+      BX_CUDA(cudaMemcpyAsync(sl.f_stage, r->f, 4 * N, cudaMemcpyHostToDevice, s));
+      h_phis[i] = sl.phi_stage;
+      h_fs[i] = sl.f_stage;
+      h_outs[i] = sl.out_stage;
+    } else {
+      h_phis[i] = r->phi;
+      h_fs[i] = r->f;
+      h_outs[i] = r->out;
+    }
+    h_dirs[i] = r->prob.dir;
+    BX_CUDA(cudaMemcpyAsync(W->d_phis + i, &h_phis[i], sizeof(void*), cudaMemcpyHostToDevice, s));
+    BX_CUDA(cudaMemcpyAsync(W->d_fs + i, &h_fs[i], sizeof(void*), cudaMemcpyHostToDevice, s));
+    BX_CUDA(cudaMemcpyAsync(W->d_outs + i, &h_outs[i], sizeof(void*), cudaMemcpyHostToDevice, s));
+    BX_CUDA(cudaMemcpyAsync(W->d_dirs + i, &h_dirs[i], sizeof(int), cudaMemcpyHostToDevice, s));
+    BX_CUDA(cudaMemcpyAsync(W->d_slots + i, &sl.d, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
+    SlotScalars& sc = W->h_sc[i];
+    memset(&sc, 0, sizeof(sc));
+    sc.rtol2 = ctx->opt.rtol * ctx->opt.rtol;
+    sc.maxit = ctx->opt.maxit > 0 ? ctx->opt.maxit : 10 * std::max(r->prob.nx, r->prob.ny);
+    sc.fold_every = ctx->opt.true_res_every;
+    sc.delta2 = ctx->opt.replace_factor * ctx->opt.replace_factor;
+    sc.flexible = ctx->opt.flexible;
+    sc.pscale = 1.f;
+    sc.status = ST_RUNNING;
+    BX_CUDA(cudaMemcpyAsync(W->d_sc + i, &sc, sizeof(SlotScalars), cudaMemcpyHostToDevice, s));
+    for (int t = 0; t < sl.d.n_st_tiles; ++t) fresh.push_back({i, t});
+  }
+  int rc = serve_rebuild_lists(ctx);
+  if (rc) return rc;
+  // set-up of the new slots only, then their first preconditioner pass (need_prec gates it)
+  BX_CUDA(cudaMemcpyAsync(S->d_new, fresh.data(), sizeof(WorkItem) * fresh.size(), cudaMemcpyHostToDevice, s));
+  S->h_aux[0] = (int)fresh.size();
+  BX_CUDA(cudaMemcpyAsync(S->d_aux, S->h_aux, sizeof(int), cudaMemcpyHostToDevice, s));
+  LaunchCfg c;
+  c.slots = W->d_slots;
+  c.items = S->d_new;
+  c.n_items = S->d_aux;
+  c.grid = std::max(1, std::min((int)fresh.size(), ctx->sm_count * 8));
+  c.stream = s;
+  timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(c, W->d_phis, W->d_fs, W->d_dirs); }, s);
+  launch_prec(ctx, W, 1);
+  BX_CUDA(cudaGetLastError());
+  BX_CUDA(cudaStreamSynchronize(s));  // `fresh` is a pageable source
+  return EXT_OK;
+}
+
+static int serve_retire(ext_ctx* ctx, const std::vector<int>& done) {
+  ext_ctx::Serve* S = ctx->serve;
+  Workspace* W = S->W;
+  cudaStream_t s = W->stream;
+  std::vector<WorkItem> ret;
+  for (int i : done)
+    for (int t = 0; t < W->slots[i].d.n_vec_items; ++t) ret.push_back({i, t});
+  BX_CUDA(cudaMemcpyAsync(S->d_ret, ret.data(), sizeof(WorkItem) * ret.size(), cudaMemcpyHostToDevice, s));
+  S->h_aux[1] = (int)ret.size();
+  BX_CUDA(cudaMemcpyAsync(S->d_aux + 1, S->h_aux + 1, sizeof(int), cudaMemcpyHostToDevice, s));
+  LaunchCfg c;
+  c.slots = W->d_slots;
+  c.items = S->d_ret;
+  c.n_items = S->d_aux + 1;
+  c.grid = std::max(1, std::min((int)ret.size(), ctx->sm_count * 8));
+  c.stream = s;
+  timed(ctx, EXT_KERNEL_OUTPUT, [&] { launch_output(c, W->d_fs, W->d_outs); }, s);
+  for (int i : done) {
+    Req* r = S->slots[i].req;
+    if (r->host_io) {
+      const size_t N = (size_t)r->prob.nx * r->prob.ny;
+      BX_CUDA(cudaMemcpyAsync(r->out, W->slots[i].out_stage, 4 * N, cudaMemcpyDeviceToHost, s));
+    }
+  }
+  BX_CUDA(cudaStreamSynchronize(s));
+  const auto now = Clock::now();
+  std::lock_guard<std::mutex> lk(S->mu);
+  for (int i : done) {
+    Req* r = S->slots[i].req;
+    const SlotScalars& sc = W->h_sc[i];
+    const int st = map_status(sc.status, sc.n_known, r->prob);
+    r->res.status = st;
+    r->res.iters = sc.it;
+    r->res.relres_true = sc.bb > 0 ? std::sqrt(sc.rr_true / sc.bb) : 0.0;
+    r->res.relres_rec = sc.bb > 0 ? std::sqrt(sc.rr / sc.bb) : 0.0;
+    r->res.n_known = sc.n_known;
+    r->res.n_unknown = r->prob.nx * r->prob.ny - sc.n_known;
+    r->res.ms_queue = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
+    r->res.ms_solve = std::chrono::duration<double, std::milli>(now - r->t_admit).count();
+    S->pool.emplace(S->slots[i].bytes, W->slots[i].arena);
+    W->slots[i].arena = nullptr;
+    S->used -= S->slots[i].bytes;
+    S->slots[i] = ServeSlot{};
+    finish_req(S, r, st);
+  }
+  return EXT_OK;
+}
+
+static void serve_fail_all(ext_ctx* ctx, int rc) {
+  ext_ctx::Serve* S = ctx->serve;
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->worker_error = rc;
+  for (auto& sl : S->slots)
+    if (sl.used) {
+      finish_req(S, sl.req, rc);
+      sl = ServeSlot{};
+    }
+  while (!S->queue.empty()) {
+    finish_req(S, S->queue.front(), rc);
+    S->queue.pop_front();
+  }
+}
+
+static void serve_loop(ext_ctx* ctx) {
+  ext_ctx::Serve* S = ctx->serve;
+  Workspace* W = S->W;
+  cudaSetDevice(ctx->device);
+  for (;;) {
+    std::vector<int> admitted;
+    int active = 0;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      for (auto& sl : S->slots) active += sl.used ? 1 : 0;
+      S->cv.wait(lk, [&] { return S->stop || !S->queue.empty() || active > 0; });
+      if (S->stop && S->queue.empty() && active == 0) return;
+      admitted = serve_admit(ctx);
+      active += (int)admitted.size();
+    }
+    int rc = EXT_OK;
+    if (!admitted.empty()) rc = serve_setup_slots(ctx, admitted);
+    if (!rc && active > 0) {
+      rc = ensure_graph(ctx, W);
+      if (!rc) {
+        if (cudaGraphLaunch(W->graph, W->stream) != cudaSuccess) rc = EXT_ECUDA;
+        ctx->launches += W->graph_nodes;
+      }
+    }
+    if (!rc) {
+      const int cap = (int)S->slots.size();
+      if (cudaMemcpyAsync(W->h_sc, W->d_sc, sizeof(SlotScalars) * cap, cudaMemcpyDeviceToHost, W->stream) != cudaSuccess ||
+          cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, W->stream) != cudaSuccess ||
+          cudaStreamSynchronize(W->stream) != cudaSuccess)
+        rc = EXT_ECUDA;
+      else if (*ctx->h_err)
+        rc = EXT_ETIMEOUT;
+    }
+    if (!rc) {
+      std::vector<int> done;
+      for (int i = 0; i < (int)S->slots.size(); ++i)
+        if (S->slots[i].used && W->h_sc[i].status != ST_RUNNING) done.push_back(i);
+      if (!done.empty()) {
+        rc = serve_retire(ctx, done);
+        if (!rc) rc = serve_rebuild_lists(ctx);
+      }
+    }
+    if (rc) {
+      cudaGetLastError();
+      serve_fail_all(ctx, rc);
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stop) return;
+    }
+  }
+}
+
 extern "C" {
-__attribute__((weak)) int ext_submit(ext_ctx*, const ext_problem*, const float*, const float*,
-                                     float*, uint64_t*) {
-  return EXT_ENOTSUP;
+
+int ext_submit(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f, float* out,
+               uint64_t* ticket) {
+  if (!ctx || !prob || !phi || !f || !out || !ticket) return EXT_EINVAL;
+  int rc = validate(prob);
+  if (rc) return rc;
+  const bool dev = is_device_ptr(phi) && is_device_ptr(f) && is_device_ptr(out);
+  const bool host = !is_device_ptr(phi) && !is_device_ptr(f) && !is_device_ptr(out);
+  if (!dev && !host) return EXT_EINVAL;
+  {
+    std::lock_guard<std::mutex> lk(ctx->api_mu);
+    if (!ctx->serve) {
+      rc = serve_init(ctx);
+      if (rc) return rc;
+      ctx->serve->worker = std::thread(serve_loop, ctx);
+    }
+  }
+  ext_ctx::Serve* S = ctx->serve;
+  Req* r = new Req();
+  r->prob = *prob;
+  r->phi = phi;
+  r->f = f;
+  r->out = out;
+  r->host_io = host;
+  r->t_submit = Clock::now();
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->worker_error) {
+      delete r;
+      return S->worker_error;
+    }
+    r->ticket = S->next_ticket++;
+    S->reqs[r->ticket] = r;
+    S->queue.push_back(r);
+    S->in_flight += 1;
+    *ticket = r->ticket;
+  }
+  S->cv.notify_all();
+  return EXT_OK;
 }
-__attribute__((weak)) int ext_poll(ext_ctx*, uint64_t, ext_result*) { return EXT_ENOTSUP; }
-__attribute__((weak)) int ext_drain(ext_ctx*) { return EXT_OK; }
-__attribute__((weak)) void ext_serve_shutdown(ext_ctx*) {}
+
+int ext_poll(ext_ctx* ctx, uint64_t ticket, ext_result* res) {
+  if (!ctx) return EXT_EINVAL;
+  if (!ctx->serve) return EXT_ENOTFOUND;
+  ext_ctx::Serve* S = ctx->serve;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->reqs.find(ticket);
+  if (it == S->reqs.end()) return EXT_ENOTFOUND;
+  Req* r = it->second;
+  if (r->status == EXT_PENDING) return EXT_PENDING;
+  const int st = r->status;
+  if (res) *res = r->res;
+  S->reqs.erase(it);
+  delete r;
+  return st;
 }
+
+int ext_drain(ext_ctx* ctx) {
+  if (!ctx) return EXT_EINVAL;
+  if (!ctx->serve) return EXT_OK;
+  ext_ctx::Serve* S = ctx->serve;
+  std::unique_lock<std::mutex> lk(S->mu);
+  S->cv_done.wait(lk, [&] { return S->in_flight == 0; });
+  return S->worker_error;
+}
+
+void ext_serve_shutdown(ext_ctx* ctx) {
+  if (!ctx || !ctx->serve) return;
+  ext_ctx::Serve* S = ctx->serve;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  Workspace* W = S->W;
+  cudaStreamSynchronize(W->stream);
+  for (auto& kv : S->pool) cudaFree(kv.second);
+  for (auto& sl : W->slots) cudaFree(sl.arena);
+  W->slots.clear();
+  cudaStream_t st = W->stream;
+  free_workspace(W);
+  cudaStreamDestroy(st);
+  cudaFree(S->d_new);
+  cudaFree(S->d_ret);
+  cudaFree(S->d_aux);
+  cudaFreeHost(S->h_aux);
+  for (auto& kv : S->reqs) delete kv.second;
+  delete S;
+  ctx->serve = nullptr;
+}
+
+}  // extern "C"

@@ -62,7 +62,8 @@ struct SlotDesc {
   // grid vectors [ny][nx]
   uint8_t* mask;     // 1 = unknown node
   double* b;
-  double* xhat;      // the iterate, FP64, updated every iteration
+  float* xhi;        // the iterate as a double-float pair x = xhi + xlo (about 48 bits),
+  float* xlo;        // updated every iteration with error-free FP32 transformations
   float* r;
   float* p[2];
   float* q;
@@ -80,11 +81,13 @@ struct SlotDesc {
   const float* lamy;
   float wnorm;       // 1 / w_max, so that the scaled weights are <= 1
   int zero_mode;     // 1: drop the (0,0) mode (both axes symmetric/periodic)
-  // tensor-core path: split operand planes (2-byte elements) and their TMA descriptors
-  void* tc_r;        // [P][nyp][nxp]  scaled residual
-  void* tc_t1;       // [P][nxp][nyp]
-  void* tc_t2;       // [P][nyp][nxp]
-  void* tc_t3;       // [P][nxp][nyp]
+  // tensor-core path: block-scaled integer slices (three 16-bit planes) and their TMA descriptors
+  void* tc_r;        // [3][nyp][nxp]  residual
+  void* tc_t1;       // [3][nxp][nyp]
+  void* tc_t2;       // [3][nyp][nxp]
+  void* tc_t3;       // [3][nxp][nyp]
+  int8_t* tc_e[4];   // block exponents of the A operand of stage s: [rows][K/64]
+  const int8_t* tc_eb[4];  // block exponents of the B operand of stage s (transform matrices)
   const void* tmaps; // 8 CUtensorMap (64-byte aligned): A operand of stages 0..3, B of 0..3
   int n_tc_tiles;    // output tiles of one tensor-core transform stage
   SlotScalars* sc;
@@ -191,6 +194,55 @@ struct CompSum {
   }
   __device__ __forceinline__ float result() const { return __fadd_rn(s, c); }
 };
+
+// Compensated FP32 dot-product accumulator (TwoProd + TwoSum per term).  GB300 runs FP64 at a
+// small fraction of its FP32 rate, so per-element FP64 arithmetic would dominate the
+// bandwidth-bound kernels; a thread's terms are summed here and only the per-thread totals are
+// combined in FP64.
+struct CompDot {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);
+    float e;
+    two_sum(s, p, s, e);
+    c = __fadd_rn(c, __fadd_rn(e, pe));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Block sum of compensated per-thread accumulators: FP32 TwoSum reductions inside each warp,
+// FP64 only across the block's warps (thread 0).  Result valid in thread 0.  `sh` >= 32 doubles.
+template <int NT>
+__device__ __forceinline__ double block_sum_comp(CompDot d, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, d.s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, d.c, o);
+    float e;
+    two_sum(d.s, s2, d.s, e);
+    d.c = __fadd_rn(d.c, __fadd_rn(c2, e));
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) sh[w] = d.value();
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < NT / 32; ++k) t += sh[k];
+  return t;
+}
+
+// x (hi, lo) += a * p with error-free transformations; |lo| stays below half an ulp of hi.
+__device__ __forceinline__ void df_axpy(float& hi, float& lo, float a, float p) {
+  const float prod = __fmul_rn(a, p);
+  const float perr = __fmaf_rn(a, p, -prod);
+  float s, e;
+  two_sum(hi, prod, s, e);
+  const float t = __fadd_rn(__fadd_rn(lo, e), perr);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
 
 // ------------------------------------------------------------------------------------------
 // Ghost-node maps of one axis (Algorithm 1 padding; symmetric = half-sample reflection;

@@ -137,7 +137,7 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
     }
 
     // epilogue: element (m, n) of D goes to Out[n][m]
-    double d_rz = 0.0, d_zq = 0.0;
+    CompDot c_rz, c_zq;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx * 4 + j;
@@ -163,8 +163,8 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
                 const int g = y * S.nx + x;
                 const float zv = S.mask[g] ? o[i] : 0.f;
                 S.z[g] = zv;
-                d_rz += (double)S.r[g] * (double)zv;
-                d_zq += (double)zv * (double)S.q[g];
+                c_rz.add(S.r[g], zv);
+                c_zq.add(zv, S.q[g]);
               }
             }
           }
@@ -172,6 +172,7 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
       }
     }
     if (STAGE == 3) {
+      double d_rz = c_rz.value(), d_zq = c_zq.value();
       block_sum2<NT>(d_rz, d_zq, red);
       if (t == 0) {
         S.part[item.tile * 4 + 0] = d_rz;

@@ -1,25 +1,29 @@
 // Fast Poisson preconditioner (Sec. 2.2 / Algorithm 1) on the 5th-generation tensor cores.
 //
-// The four separable transform products of the preconditioner (see kernels_gemm_simt.cu for the
-// stage equations) run as tcgen05 MMAs.  This operator is so ill-conditioned that a plain
-// 16-bit operand ruins the preconditioner (rounding noise after the 1/(lam+mu)^2 scaling lands
-// in rough modes, and CG stops converging), so every operand is stored as a sum of 16-bit planes:
-//   FP16: v = hi + lo            (22 significant bits), products hi*hi + hi*lo + lo*hi
-//   BF16: v = hi + mid + lo      (24 significant bits), the six products of order <= 2
-// with FP32 accumulation in TMEM.  FP16 planes carry power-of-two scales (data: from the residual
-// norm; transform matrices: 2^6) so neither overflow nor underflow occurs; the scales are
-// removed exactly in the epilogues.  The tensor core's FP32 accumulation truncates, so its error
-// grows with every k-step: each 64-wide k-block is therefore accumulated into a fresh TMEM buffer
-// (a ring of four) and the epilogue warps add the k-block sums into a compensated (hi, lo)
-// register pair, which keeps the product's error at the level of a 64-term FP32 sum.
+// The four separable transform products of the preconditioner (stage equations in
+// kernels_gemm_simt.cu) run as tcgen05 MMAs with FP16 or BF16 operands and FP32 accumulation.
+// This operator is so ill-conditioned that a plain 16-bit operand ruins the preconditioner, and
+// even float hi/lo operand splits lose too much in the tensor core's truncating FP32
+// accumulation.  The products are therefore made exact:
+//
+//  * every operand is cut into blocks of 128 consecutive k; a block with largest magnitude below
+//    2^E is stored as three integer slices, v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24),
+//    |c0| <= 255, |c1|, |c2| <= 128 (exact in FP16 and BF16), plus the exponent E (int8);
+//  * for each slice order d = i + j (products c_i c'_j, d <= 2: six MMAs per k-step) a separate
+//    TMEM accumulator sums one 128-wide k-block: for d = 2 at most 128 * (2*255*128 + 128^2)
+//    < 2^24, so every partial sum is an exact integer and so is the accumulation;
+//  * the epilogue warps scale the three exact sums by 2^(E_A + E_B - 16 - 8d) and add them into
+//    a compensated (hi, lo) register pair, k-block after k-block.
+// The result carries about 24 bits relative to each 128-block's largest value, with no error
+// growth along K.  The writer of the next stage's operand computes its block exponents with a
+// two-warp maximum and stores the slices transposed (Out[n][m], coalesced along m).
 //
 // Kernel structure (one CTA per SM, persistent over the (slot, tile) work list):
-//   warp 0      : TMA producer, 128B-swizzled K-major tiles of every plane into a smem ring
+//   warp 0      : TMA producer: 128B-swizzled K-major tiles of the three slices of A and B
 //   warp 1      : TMEM allocation; lane 0 issues the MMAs and the tcgen05.commit arrivals
-//   warps 2..5  : k-block sums TMEM -> compensated registers; then the epilogue: next stage's
-//                 planes written transposed
-//                 (Out[n][m], coalesced along m), with the stage's fused work (eigenvalue
-//                 weights; masking, FP64 dot products and the CG scalars in the last stage).
+//   warps 2..9  : two per TMEM lane quarter (32 rows), each owning 32 of the tile's 64 columns:
+//                 exact k-block sums -> compensated registers -> the stage's epilogue
+//                 (eigenvalue weights; masking, FP64 dot products and CG scalars in stage 3).
 // Every wait on an mbarrier is bounded; on time-out the CTA raises an error flag, drains its
 // outstanding copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
@@ -32,25 +36,24 @@
 namespace bx {
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int kEpiWarps = 4;
+constexpr int BM = 128, BN = 64, BK = 64;  // BK: one 128-byte swizzle atom per pipeline stage
+constexpr int KC = 128;                     // k per exact accumulation block (two pipeline stages)
+constexpr int NS = 3;                            // slices per operand
+constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at 2 GHz
-constexpr int kChunks = 4;                       // TMEM ring of k-block accumulators
-constexpr int kTmemCols = kChunks * BN;
-
-template <int NS>
-struct TcCfg {
-  static constexpr int STAGES = NS == 2 ? 4 : 3;
-  static constexpr int A_PLANE = BM * BK * 2;
-  static constexpr int B_PLANE = BN * BK * 2;
-  static constexpr int STAGE_BYTES = NS * (A_PLANE + B_PLANE);
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 512;
-};
+constexpr int kChunks = 2;                       // TMEM ring of k-block accumulator sets
+constexpr int kSetCols = 3 * BN;                 // one accumulator per slice order
+constexpr int kTmemCols = 512;                   // power of two >= kChunks * kSetCols
+constexpr int STAGES = 3;
+constexpr int A_PLANE = BM * BK * 2;
+constexpr int B_PLANE = BN * BK * 2;
+constexpr int STAGE_BYTES = NS * (A_PLANE + B_PLANE);
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 2048;
 
 struct Ctl {
-  uint64_t full[4];
-  uint64_t empty[4];
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
   uint64_t tfull[kChunks];
   uint64_t tempty[kChunks];
   uint64_t drain;
@@ -58,13 +61,14 @@ struct Ctl {
   int abort_flag;
   int last;
   int pad;
-  double red[8];
+  double red[2 * kEpiWarps];
+  float colmax[2][4][32];  // [column half][lane quarter][column]
 };
+static_assert(sizeof(Ctl) <= 2048, "control block too large");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
-
 __device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -98,7 +102,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
   return true;
 }
-
 __device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, uint64_t* bar, int c0, int c1) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
@@ -109,24 +112,21 @@ __device__ __forceinline__ void tmap_acquire(const void* tmap) {
   asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(tmap))
                : "memory");
 }
-
 // UMMA shared-memory descriptor: K-major operand, 128-byte swizzle, 8-row core groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
-  d |= static_cast<uint64_t>(1) << 16;            // leading-dimension offset (unused here)
-  d |= static_cast<uint64_t>(1024 >> 4) << 32;    // stride between 8-row groups
-  d |= static_cast<uint64_t>(1) << 46;            // descriptor version
-  d |= static_cast<uint64_t>(2) << 61;            // 128-byte swizzle
+  d |= static_cast<uint64_t>(1) << 16;          // leading-dimension offset (unused here)
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;  // stride between 8-row groups
+  d |= static_cast<uint64_t>(1) << 46;          // descriptor version
+  d |= static_cast<uint64_t>(2) << 61;          // 128-byte swizzle
   return d;
 }
-
 // Instruction descriptor of kind::f16: FP32 accumulator, both operands K-major, M x N tile.
 __host__ __device__ constexpr uint32_t idesc_f16(bool bf16, int M, int N) {
   return (1u << 4) | ((bf16 ? 1u : 0u) << 7) | ((bf16 ? 1u : 0u) << 10) |
          (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
 }
-
 __device__ __forceinline__ void umma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
@@ -139,12 +139,8 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
 }
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -156,61 +152,96 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
         "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+        "=r"(v[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// 2^e as a float for e in the normal range, 0 below it.
+__device__ __forceinline__ float pow2f(int e) {
+  return e < -126 ? 0.f : __int_as_float((min(e, 127) + 127) << 23);
 }
 
-// 16-bit planes of one value (exact differences: Sterbenz).
+// Exponent E of a block whose largest magnitude is amax: amax < 2^E and amax 2^(8-E) < 255.5,
+// so the leading slice stays within +-255 (0 for an all-zero block).
+__device__ __forceinline__ int block_exp(float amax) {
+  if (!(amax > 0.f)) return 0;
+  int e;
+  frexpf(amax, &e);
+  if (amax * pow2f(8 - e) >= 255.5f) ++e;
+  return max(e, -100);
+}
+
+// Three integer slices of v for block exponent E (exact residuals; last slice rounded).
 template <bool BF16>
-__device__ __forceinline__ void split_store(uint16_t* base, size_t plane, size_t idx, float v, int NS) {
+__device__ __forceinline__ void slice_store(uint16_t* base, size_t plane, size_t idx, float v, int E) {
+  const float c0 = rintf(v * pow2f(8 - E));
+  const float r1 = v - c0 * pow2f(E - 8);
+  const float c1 = rintf(r1 * pow2f(16 - E));
+  const float r2 = r1 - c1 * pow2f(E - 16);
+  const float c2 = rintf(r2 * pow2f(24 - E));
   if (BF16) {
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const float r1 = v - __bfloat162float(h);
-    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
-    base[idx] = __bfloat16_as_ushort(h);
-    base[plane + idx] = __bfloat16_as_ushort(m);
-    if (NS > 2) base[2 * plane + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(r1 - __bfloat162float(m)));
+    base[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c0));
+    base[plane + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c1));
+    base[2 * plane + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
   } else {
-    const __half h = __float2half_rn(v);
-    base[idx] = __half_as_ushort(h);
-    base[plane + idx] = __half_as_ushort(__float2half_rn(v - __half2float(h)));
+    base[idx] = __half_as_ushort(__float2half_rn(c0));
+    base[plane + idx] = __half_as_ushort(__float2half_rn(c1));
+    base[2 * plane + idx] = __half_as_ushort(__float2half_rn(c2));
   }
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 __device__ __forceinline__ bool slot_runs(const SlotScalars* sc, int mode) {
   return mode == 0 ? sc->active != 0 : (mode == 1 ? sc->need_prec != 0 : true);
 }
 
+__device__ __forceinline__ void epi_bar() {
+  asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+}
+
 struct TcStage {
   int M, N, K;
-  void* out;  // next stage's planes, or nullptr in the last stage
+  void* out;        // next stage's slices, or nullptr in the last stage
+  int8_t* eout;     // next stage's block exponents [N][M/64]
 };
 
 __device__ __forceinline__ TcStage tc_stage(const SlotDesc& S, int stage) {
   switch (stage) {
-    case 0: return {S.nyp, S.nxp, S.nxp, S.tc_t1};
-    case 1: return {S.nxp, S.nyp, S.nyp, S.tc_t2};
-    case 2: return {S.nyp, S.nxp, S.nxp, S.tc_t3};
-    default: return {S.nxp, S.nyp, S.nyp, nullptr};
+    case 0: return {S.nyp, S.nxp, S.nxp, S.tc_t1, S.tc_e[1]};
+    case 1: return {S.nxp, S.nyp, S.nyp, S.tc_t2, S.tc_e[2]};
+    case 2: return {S.nyp, S.nxp, S.nxp, S.tc_t3, S.tc_e[3]};
+    default: return {S.nxp, S.nyp, S.nyp, nullptr, nullptr};
   }
 }
 
-template <int NS, bool BF16, int STAGE>
+template <bool BF16, int STAGE>
 __global__ void __launch_bounds__(kThreads, 1)
 k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int mode, int* __restrict__ err) {
-  using C = TcCfg<NS>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-  Ctl* ctl = reinterpret_cast<Ctl*>(smem + C::STAGES * C::STAGE_BYTES);
+  Ctl* ctl = reinterpret_cast<Ctl*>(smem + STAGES * STAGE_BYTES);
   volatile int* abort_flag = &ctl->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = *n_items;
   constexpr uint32_t IDESC = idesc_f16(BF16, BM, BN);
-  const float bdescale = BF16 ? 1.f : 1.f / 64.f;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < C::STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&ctl->full[s], 1);
       mbar_init(&ctl->empty[s], 1);
     }
@@ -237,9 +268,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   if (warp == 0) {
     // ------------------------------------------------------------------ TMA producer
     if (lane == 0) {
-      int stage = 0;
+      int stage = 0, issued = 0;
       uint32_t phase = 0;
-      int issued = 0;
       for (int w = blockIdx.x; w < total && !*abort_flag; w += gridDim.x) {
         const WorkItem it = items[w];
         const SlotDesc& S = slots[it.slot];
@@ -253,15 +283,15 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int m0 = (it.tile % mt) * BM, n0 = (it.tile / mt) * BN;
         for (int kb = 0; kb < v.K / BK; ++kb) {
           if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_flag)) break;
-          mbar_expect_tx(&ctl->full[stage], C::STAGE_BYTES);
-          unsigned char* sa = smem + stage * C::STAGE_BYTES;
-          unsigned char* sb = sa + NS * C::A_PLANE;
+          mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
+          unsigned char* sa = smem + stage * STAGE_BYTES;
+          unsigned char* sb = sa + NS * A_PLANE;
 #pragma unroll
-          for (int p = 0; p < NS; ++p) tma_load_2d(sa + p * C::A_PLANE, ma, &ctl->full[stage], kb * BK, p * v.M + m0);
+          for (int p = 0; p < NS; ++p) tma_load_2d(sa + p * A_PLANE, ma, &ctl->full[stage], kb * BK, p * v.M + m0);
 #pragma unroll
-          for (int p = 0; p < NS; ++p) tma_load_2d(sb + p * C::B_PLANE, mb, &ctl->full[stage], kb * BK, p * v.N + n0);
+          for (int p = 0; p < NS; ++p) tma_load_2d(sb + p * B_PLANE, mb, &ctl->full[stage], kb * BK, p * v.N + n0);
           ++issued;
-          if (++stage == C::STAGES) {
+          if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
           }
@@ -271,9 +301,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         // let the copies already issued (at most one per ring slot) land before the CTA leaves
         int s = stage;
         uint32_t ph = phase;
-        for (int k = 0; k < C::STAGES && k < issued; ++k) {
+        for (int k = 0; k < STAGES && k < issued; ++k) {
           if (s == 0) {
-            s = C::STAGES - 1;
+            s = STAGES - 1;
             ph ^= 1;
           } else {
             --s;
@@ -288,9 +318,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   } else if (warp == 1) {
     // ------------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      int stage = 0;
+      int stage = 0, chunk = 0;
       uint32_t phase = 0;
-      int chunk = 0;  // k-blocks issued so far (position in the TMEM ring)
       bool ok = true;
       for (int w = blockIdx.x; w < total && ok && !*abort_flag; w += gridDim.x) {
         const WorkItem it = items[w];
@@ -298,36 +327,40 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         if (!slot_runs(S.sc, mode)) continue;
         const TcStage v = tc_stage(S, STAGE);
         for (int kb = 0; kb < v.K / BK; ++kb) {
+          const int half_kb = kb & 1;  // position inside the 128-wide accumulation block
           const int cb = chunk % kChunks;
-          if (!mbar_wait(&ctl->tempty[cb], ((chunk / kChunks) & 1) ^ 1, abort_flag) ||
+          if ((half_kb == 0 && !mbar_wait(&ctl->tempty[cb], ((chunk / kChunks) & 1) ^ 1, abort_flag)) ||
               !mbar_wait(&ctl->full[stage], phase, abort_flag)) {
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t d_tmem = tmem_base + cb * BN;
-          const uint32_t sa = smem_u32(smem + stage * C::STAGE_BYTES);
-          const uint32_t sb = sa + NS * C::A_PLANE;
+          const uint32_t dset = tmem_base + cb * kSetCols;
+          const uint32_t sa = smem_u32(smem + stage * STAGE_BYTES);
+          const uint32_t sb = sa + NS * A_PLANE;
 #pragma unroll
           for (int j = 0; j < BK / 16; ++j) {
-            // products of total order <= NS-1 (hi*hi, hi*lo, lo*hi, ...)
 #pragma unroll
             for (int pa = 0; pa < NS; ++pa) {
 #pragma unroll
-              for (int pb = 0; pb + pa < NS; ++pb) {
-                const uint64_t ad = sdesc(sa + pa * C::A_PLANE) + 2 * j;
-                const uint64_t bd = sdesc(sb + pb * C::B_PLANE) + 2 * j;
-                umma(d_tmem, ad, bd, IDESC, (j | pa | pb) != 0 ? 1u : 0u);
+              for (int pb = 0; pa + pb < NS; ++pb) {
+                const int d = pa + pb;
+                const uint64_t ad = sdesc(sa + pa * A_PLANE) + 2 * j;
+                const uint64_t bd = sdesc(sb + pb * B_PLANE) + 2 * j;
+                // the first product of each order in an accumulation block starts afresh
+                umma(dset + d * BN, ad, bd, IDESC, (half_kb > 0 || j > 0 || pa > 0) ? 1u : 0u);
               }
             }
           }
           umma_commit(&ctl->empty[stage]);
-          umma_commit(&ctl->tfull[cb]);
-          if (++stage == C::STAGES) {
+          if (half_kb == 1) {
+            umma_commit(&ctl->tfull[cb]);
+            ++chunk;
+          }
+          if (++stage == STAGES) {
             stage = 0;
             phase ^= 1;
           }
-          ++chunk;
         }
       }
       // all MMAs issued by this thread complete before TMEM can be released
@@ -339,7 +372,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     __syncwarp();
   } else {
     // ------------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;  // TMEM lanes 32*quarter .. +31 are this warp's
+    const int quarter = warp & 3;        // TMEM lanes 32*quarter .. +31
+    const int half = (warp - 2) >> 2;    // columns 32*half .. +31 of the tile
     const int ew = warp - 2;
     const int row = quarter * 32 + lane;
     int chunk = 0;
@@ -352,17 +386,22 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       const int mt = v.M / BM;
       const int m0 = (it.tile % mt) * BM, n0 = (it.tile / mt) * BN;
       const int m = m0 + row;
-      // compensated sum over the k-blocks of this tile
-      float hi[BN], lo[BN];
+      const int ncol0 = n0 + half * 32;
+      const int kblocks = v.K / KC;
+      const int8_t* ea_row = S.tc_e[STAGE] + static_cast<size_t>(m) * kblocks;
+      const int8_t* eb = S.tc_eb[STAGE];
+      float hi[32], lo[32];
 #pragma unroll
-      for (int i = 0; i < BN; ++i) {
+      for (int i = 0; i < 32; ++i) {
         hi[i] = 0.f;
         lo[i] = 0.f;
       }
       bool fail_all = false;
-      for (int kb = 0; kb < v.K / BK; ++kb) {
+      for (int kb = 0; kb < kblocks; ++kb) {
         const int cb = chunk % kChunks;
-        // all four epilogue warps leave together if any of them gave up waiting
+        const int ea = ea_row[kb];
+        const int eb_mine = eb[static_cast<size_t>(ncol0 + lane) * kblocks + kb];
+        // all epilogue warps leave together if any of them gave up waiting
         const uint32_t fail = mbar_wait(&ctl->tfull[cb], (chunk / kChunks) & 1, abort_flag) ? 0u : 1u;
         uint32_t any_fail;
         asm volatile(
@@ -378,61 +417,113 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           break;
         }
         tc_fence_after();
+        const uint32_t base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + cb * kSetCols + half * 32;
 #pragma unroll
-        for (int c = 0; c < BN / 32; ++c) {
-          uint32_t r[32];
-          tmem_ld32(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + cb * BN + c * 32, r);
+        for (int hc = 0; hc < 2; ++hc) {
+          uint32_t s0[16], s1[16], s2[16];
+          tmem_ld16(base + hc * 16, s0);
+          tmem_ld16(base + BN + hc * 16, s1);
+          tmem_ld16(base + 2 * BN + hc * 16, s2);
+          tmem_wait_ld();
+          if (hc == 1) {
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ctl->tempty[cb]);
+          }
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float e;
-            two_sum(hi[c * 32 + i], __uint_as_float(r[i]), hi[c * 32 + i], e);
-            lo[c * 32 + i] = __fadd_rn(lo[c * 32 + i], e);
+          for (int i = 0; i < 16; ++i) {
+            const int c = hc * 16 + i;
+            const int e = ea + __shfl_sync(0xffffffffu, eb_mine, c) - 16;
+            const float t0 = __uint_as_float(s0[i]) * pow2f(e);
+            const float t1 = __uint_as_float(s1[i]) * pow2f(e - 8);
+            const float t2 = __uint_as_float(s2[i]) * pow2f(e - 16);
+            float er;
+            two_sum(hi[c], t0, hi[c], er);
+            lo[c] = __fadd_rn(lo[c], er);
+            two_sum(hi[c], t1, hi[c], er);
+            lo[c] = __fadd_rn(lo[c], __fadd_rn(er, t2));
           }
         }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&ctl->tempty[cb]);
         ++chunk;
       }
       if (fail_all) break;
-      const float inv_scale = (STAGE == 3) ? 1.f / sc->pscale : 1.f;
-      const float lamx_m = (STAGE == 1 && m < S.nx) ? S.lamx[m] : 0.f;
-      double d_rz = 0.0, d_zq = 0.0;
-      const size_t plane = static_cast<size_t>(v.M) * v.N;
+      float val[32];
 #pragma unroll
-      for (int i = 0; i < BN; ++i) {
-        const int n = n0 + i;
-        float val = __fadd_rn(hi[i], lo[i]) * bdescale;
-        if (STAGE == 1) {
+      for (int i = 0; i < 32; ++i) val[i] = __fadd_rn(hi[i], lo[i]);
+      if (STAGE == 1) {
+        const float lamx_m = (m < S.nx) ? S.lamx[m] : 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int n = ncol0 + i;
           float wgt = 0.f;
           if (m < S.nx && n < S.ny) {
             const float s = S.lamy[n] + lamx_m;
             wgt = (s > 0.f) ? S.wnorm / (s * s) : 0.f;
           }
-          val *= wgt;
-        }
-        if (STAGE <= 2) {
-          split_store<BF16>(static_cast<uint16_t*>(v.out), plane, static_cast<size_t>(n) * v.M + m, val, NS);
-        } else if (n < S.ny && m < S.nx) {
-          const int g = n * S.nx + m;
-          const float zv = S.mask[g] ? val * inv_scale : 0.f;
-          S.z[g] = zv;
-          d_rz += (double)S.r[g] * (double)zv;
-          d_zq += (double)zv * (double)S.q[g];
+          val[i] *= wgt;
         }
       }
-      if (STAGE == 3) {
-        // tile partials of r.z and z.q, then the slot's last tile forms rho and beta
-        d_rz = warp_sum(d_rz);
-        d_zq = warp_sum(d_zq);
+      if (STAGE <= 2) {
+        // block exponents of the next operand: rows n, k-blocks of 128 consecutive m (this tile)
+        float mine = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float wm = warp_max(fabsf(val[i]));
+          if (lane == i) mine = wm;
+        }
+        ctl->colmax[half][quarter][lane] = mine;
+        epi_bar();
+        const float bmax = fmaxf(fmaxf(ctl->colmax[half][0][lane], ctl->colmax[half][1][lane]),
+                                 fmaxf(ctl->colmax[half][2][lane], ctl->colmax[half][3][lane]));
+        const int E_mine = block_exp(bmax);
+        epi_bar();
+        const size_t plane = static_cast<size_t>(v.M) * v.N;
+        uint16_t* out = static_cast<uint16_t*>(v.out);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int E = __shfl_sync(0xffffffffu, E_mine, i);
+          slice_store<BF16>(out, plane, static_cast<size_t>(ncol0 + i) * v.M + m, val[i], E);
+        }
+        if (quarter == 0)
+          v.eout[static_cast<size_t>(ncol0 + lane) * (v.M / KC) + m0 / KC] = static_cast<int8_t>(E_mine);
+      } else {
+        CompDot c_rz, c_zq;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int n = ncol0 + i;
+          if (n < S.ny && m < S.nx) {
+            const int g = n * S.nx + m;
+            const float zv = S.mask[g] ? val[i] : 0.f;
+            S.z[g] = zv;
+            c_rz.add(S.r[g], zv);
+            c_zq.add(zv, S.q[g]);
+          }
+        }
+        // tile partials of r.z and z.q (FP32-compensated inside the warp), then the slot's last
+        // tile forms rho and beta
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          float e;
+          const float a1 = __shfl_xor_sync(0xffffffffu, c_rz.s, o), a2 = __shfl_xor_sync(0xffffffffu, c_rz.c, o);
+          two_sum(c_rz.s, a1, c_rz.s, e);
+          c_rz.c = __fadd_rn(c_rz.c, __fadd_rn(a2, e));
+          const float b1 = __shfl_xor_sync(0xffffffffu, c_zq.s, o), b2 = __shfl_xor_sync(0xffffffffu, c_zq.c, o);
+          two_sum(c_zq.s, b1, c_zq.s, e);
+          c_zq.c = __fadd_rn(c_zq.c, __fadd_rn(b2, e));
+        }
+        const double d_rz = c_rz.value();
+        const double d_zq = c_zq.value();
         if (lane == 0) {
           ctl->red[2 * ew] = d_rz;
           ctl->red[2 * ew + 1] = d_zq;
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        epi_bar();
         if (ew == 0 && lane == 0) {
-          const double a = (ctl->red[0] + ctl->red[2]) + (ctl->red[4] + ctl->red[6]);
-          const double b = (ctl->red[1] + ctl->red[3]) + (ctl->red[5] + ctl->red[7]);
+          double a = 0.0, b = 0.0;
+          for (int k = 0; k < kEpiWarps; ++k) {
+            a += ctl->red[2 * k];
+            b += ctl->red[2 * k + 1];
+          }
           S.part[it.tile * 4 + 0] = a;
           S.part[it.tile * 4 + 1] = b;
           __threadfence();
@@ -444,29 +535,31 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           }
           ctl->last = last;
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        epi_bar();
         if (ctl->last) {
           double a = 0.0, b = 0.0;
-          const int t = ew * 32 + lane;
-          for (int k = t; k < S.n_tc_tiles; k += 32 * kEpiWarps) {
+          for (int k = ew * 32 + lane; k < S.n_tc_tiles; k += 32 * kEpiWarps) {
             a += __ldcg(&S.part[k * 4 + 0]);
             b += __ldcg(&S.part[k * 4 + 1]);
           }
           a = warp_sum(a);
           b = warp_sum(b);
-          asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+          epi_bar();
           if (lane == 0) {
             ctl->red[2 * ew] = a;
             ctl->red[2 * ew + 1] = b;
           }
-          asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+          epi_bar();
           if (ew == 0 && lane == 0) {
-            const double rz = (ctl->red[0] + ctl->red[2]) + (ctl->red[4] + ctl->red[6]);
-            const double zq = (ctl->red[1] + ctl->red[3]) + (ctl->red[5] + ctl->red[7]);
+            double rz = 0.0, zq = 0.0;
+            for (int k = 0; k < kEpiWarps; ++k) {
+              rz += ctl->red[2 * k];
+              zq += ctl->red[2 * k + 1];
+            }
             finish_preconditioner(S, rz, zq, mode);
           }
         }
-        asm volatile("bar.sync 1, %0;" ::"r"(32 * kEpiWarps) : "memory");
+        epi_bar();
       }
     }
   }
@@ -481,56 +574,60 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
 }
 
-// Residual -> scaled 16-bit planes of the first stage's A operand (padding stays zero).
-template <int NS, bool BF16>
-__global__ void __launch_bounds__(kVecThreads)
+// Residual -> slices of the first stage's A operand.  One warp per (row, 128-column block); the
+// work list is the stencil's (64 x 16 tiles): tiles starting at an even multiple of 64 take the
+// 128 columns of their block, the others have nothing to do.
+template <bool BF16>
+__global__ void __launch_bounds__(256)
 k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
              const int* __restrict__ n_items, int mode) {
   const int total = *n_items;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem it = items[w];
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
     if (!slot_runs(sc, mode)) continue;
-    // FP16: scale so that ||r||_2 is about 2^12; every transform stage keeps |values| <= ||r||_2
-    float s = 1.f;
-    if (!BF16 && mode != 2 && sc->rr > 0.0) {
-      int e;
-      frexp(sqrt(sc->rr), &e);
-      s = ldexpf(1.f, 12 - e);
-    }
-    if (it.tile == 0 && threadIdx.x == 0) sc->pscale = s;
-    const int n = S.nx * S.ny;
-    const int e0 = it.tile * kVecChunk;
-    const int e1 = min(n, e0 + kVecChunk);
+    if (it.tile == 0 && threadIdx.x == 0) sc->pscale = 1.f;
+    const int tx = (S.nx + kStTileX - 1) / kStTileX;
+    const int x0 = (it.tile % tx) * kStTileX;
+    const int y0 = (it.tile / tx) * kStTileY;
+    if (x0 % KC != 0) continue;
+    const int kblocks = S.nxp / KC;
     const size_t plane = static_cast<size_t>(S.nyp) * S.nxp;
     uint16_t* out = static_cast<uint16_t*>(S.tc_r);
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-      const int y = e / S.nx, x = e - y * S.nx;
-      split_store<BF16>(out, plane, static_cast<size_t>(y) * S.nxp + x, S.r[e] * s, NS);
+    for (int ly = warp; ly < kStTileY; ly += 8) {
+      const int y = y0 + ly;
+      if (y >= S.ny) break;
+      float v[4];
+      float amax = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int x = x0 + 32 * k + lane;
+        v[k] = x < S.nx ? S.r[y * S.nx + x] : 0.f;
+        amax = fmaxf(amax, fabsf(v[k]));
+      }
+      const int E = block_exp(warp_max(amax));
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        slice_store<BF16>(out, plane, static_cast<size_t>(y) * S.nxp + x0 + 32 * k + lane, v[k], E);
+      if (lane == 0) S.tc_e[0][static_cast<size_t>(y) * kblocks + x0 / KC] = static_cast<int8_t>(E);
     }
   }
 }
 
-template <int NS, bool BF16, int STAGE>
-void launch_stage(const LaunchCfg& c, int mode, int* err) {
-  using C = TcCfg<NS>;
-  k_prec_tc<NS, BF16, STAGE><<<c.grid, kThreads, C::SMEM, c.stream>>>(c.slots, c.items, c.n_items, mode, err);
-}
-
-template <int NS, bool BF16, int STAGE>
+template <bool BF16, int STAGE>
 cudaError_t set_attr() {
-  return cudaFuncSetAttribute(k_prec_tc<NS, BF16, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              TcCfg<NS>::SMEM);
+  return cudaFuncSetAttribute(k_prec_tc<BF16, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
 }
 
-template <int NS, bool BF16>
+template <bool BF16>
 void launch_all(const LaunchCfg& c, int stage, int mode, int* err) {
   switch (stage) {
-    case 0: launch_stage<NS, BF16, 0>(c, mode, err); break;
-    case 1: launch_stage<NS, BF16, 1>(c, mode, err); break;
-    case 2: launch_stage<NS, BF16, 2>(c, mode, err); break;
-    default: launch_stage<NS, BF16, 3>(c, mode, err); break;
+    case 0: k_prec_tc<BF16, 0><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
+    case 1: k_prec_tc<BF16, 1><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
+    case 2: k_prec_tc<BF16, 2><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
+    default: k_prec_tc<BF16, 3><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
   }
 }
 
@@ -543,29 +640,28 @@ bool tc_supported() {
     cudaGetLastError();
     return false;
   }
-  return p.major == 10 && p.sharedMemPerBlockOptin >= static_cast<size_t>(TcCfg<3>::SMEM);
+  return p.major == 10 && p.sharedMemPerBlockOptin >= static_cast<size_t>(SMEM_BYTES);
 }
 
-int tc_planes(int split_kind) { return split_kind == 0 ? 2 : 3; }
+int tc_planes(int) { return NS; }
 
 cudaError_t tc_init() {
   cudaError_t e = cudaSuccess;
-  cudaError_t r[8] = {set_attr<2, false, 0>(), set_attr<2, false, 1>(), set_attr<2, false, 2>(),
-                      set_attr<2, false, 3>(), set_attr<3, true, 0>(),  set_attr<3, true, 1>(),
-                      set_attr<3, true, 2>(),  set_attr<3, true, 3>()};
+  const cudaError_t r[8] = {set_attr<false, 0>(), set_attr<false, 1>(), set_attr<false, 2>(), set_attr<false, 3>(),
+                            set_attr<true, 0>(),  set_attr<true, 1>(),  set_attr<true, 2>(),  set_attr<true, 3>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
 }
 
 void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int* err) {
-  if (split_kind == 0) launch_all<2, false>(c, stage, mode, err);
-  else launch_all<3, true>(c, stage, mode, err);
+  if (split_kind == 0) launch_all<false>(c, stage, mode, err);
+  else launch_all<true>(c, stage, mode, err);
 }
 
 void launch_prec_tc_prepare(const LaunchCfg& c, int mode, int split_kind) {
-  if (split_kind == 0) k_tc_prepare<2, false><<<c.grid, kVecThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
-  else k_tc_prepare<3, true><<<c.grid, kVecThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
+  if (split_kind == 0) k_tc_prepare<false><<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
+  else k_tc_prepare<true><<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
 }
 
 }  // namespace bx
