@@ -3,10 +3,15 @@
 1e-8.
 
 Workloads (seeded synthetic inputs shaped like the paper's test problems):
+  batch  : (default) 256 uneven grids (sides drawn from {128,192,256,384,512}, wobbly interfaces,
+           field known inside, extend out, symmetric edges) solved together with the tensor-core
+           (mixed BF16) preconditioner; a step is the whole batch.  The plain FP32 single-solve
+           path is timed on a sample of the same grids for the comparison.
   single : one 1024x1024 extension (six-lobed star, field known outside, extend in, periodic
-           edges), plain FP32 path; a step is one complete solve (set-up, PCG to 1e-8, output).
-  batch  : 256 uneven grids (sides from {128,192,256,384,512}, wobbly interfaces, extend out,
-           symmetric edges) solved together; a step is the whole batch.
+           edges); a step is one complete solve (set-up, PCG to 1e-8, output).
+  serve  : a bounded sample of the serving workload: Poisson arrivals of requests with
+           log-uniform sides, star or multi-circle interfaces, random direction and edges;
+           reports p50/p99 latency beside throughput.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle (assembled sparse matrix and
 SuperLU direct solve, which reaches a residual far below 1e-8) on the same workload instead.
@@ -46,7 +51,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="single", choices=["single", "batch"])
+    ap.add_argument("--workload", default="batch", choices=["single", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=400, help="serve: requests per step")
+    ap.add_argument("--rate", type=float, default=500.0, help="serve: arrivals per second")
+    ap.add_argument("--plain-sample", type=int, default=16, help="batch: grids timed on the plain path")
     ap.add_argument("--prec", default=None, help="fp32 | mixed_fp16 | mixed_bf16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -57,16 +65,23 @@ def parse():
 # ----------------------------------------------------------------------------------------------
 # workloads
 # ----------------------------------------------------------------------------------------------
-def make_workload(name, rank):
+def make_workload(name, rank, args=None):
     from paper_1704_08897_gb300 import synth
     if name == "single":
         p = synth.single_star_case(1024)
         return [p], {"workload": "star1024_periodic_extend_in", "grid": "1024x1024",
                      "instances": 1, "prec": "fp32"}
+    if name == "serve":
+        reqs = synth.serving_stream(count=args.requests, rate=args.rate,
+                                    seed=synth.BASE_SEED + 1000 * rank, side_lo=64, side_hi=512)
+        probs = [r.problem for r in reqs]
+        return probs, {"workload": f"serve{args.requests}_poisson{args.rate:g}per_s_sides64-512",
+                       "instances": len(probs), "arrivals": [r.arrival_s for r in reqs],
+                       "prec": "mixed_bf16"}
     probs = synth.batch_case(256, seed=synth.BASE_SEED + 1000 * rank)
     nodes = sum(p.nx * p.ny for p in probs)
     return probs, {"workload": "batch256_sides128-512_wobbly_extend_out", "instances": 256,
-                   "nodes": nodes, "prec": "fp32"}
+                   "nodes": nodes, "prec": "mixed_bf16"}
 
 
 def algorithmic_cost(probs, kind):
@@ -136,8 +151,11 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------------------
 # our implementation
 # ----------------------------------------------------------------------------------------------
-def kernel_hash(kind):
-    f = "kernels_gemm_simt.cu" if kind.startswith("prec") else "kernels_grid.cu"
+def kernel_hash(kind, prec="fp32"):
+    if kind.startswith("prec"):
+        f = "kernels_gemm_simt.cu" if prec == "fp32" else "kernels_gemm_tc.cu"
+    else:
+        f = "kernels_grid.cu"
     with open(os.path.join(CSRC, f), "rb") as fh:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
@@ -150,12 +168,13 @@ def run_ours(args, rank, world):
 
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
     ext.load()
-    probs, cfg = make_workload(args.workload, rank)
+    probs, cfg = make_workload(args.workload, rank, args)
+    arrivals = cfg.pop("arrivals", None)
     prec = args.prec or cfg["prec"]
     cfg["prec"] = prec
     stream = torch.cuda.Stream()
     # hard extend-out grids need up to ~10 n iterations at 1e-8 in FP32 arithmetic
-    maxit = 20 * max(max(p.nx, p.ny) for p in probs)
+    maxit = 40 * max(max(p.nx, p.ny) for p in probs)
     ctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=maxit), stream=stream)
     dprobs = [ext.problem_of(p) for p in probs]
     phis = [torch.from_numpy(p.phi).cuda() for p in probs]
@@ -163,11 +182,27 @@ def run_ours(args, rank, world):
     outs = [torch.empty_like(x) for x in phis]
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
+    serve_stats = []
+
     def step():
+        if args.workload == "serve":
+            # requests arrive on their Poisson schedule while earlier ones are on the GPU
+            t0 = time.perf_counter()
+            tickets = []
+            for k in range(len(probs)):
+                while time.perf_counter() - t0 < arrivals[k]:
+                    time.sleep(5e-5)
+                tickets.append(ext.ext_submit(ctx, dprobs[k], phis[k], fs[k], outs[k]))
+            ext.ext_drain(ctx)
+            wall = time.perf_counter() - t0
+            res = [ext.ext_poll(ctx, t) for t in tickets]
+            serve_stats.append({"wall_s": wall,
+                                "lat_ms": [r["ms_queue"] + r["ms_solve"] for r in res]})
+            return res
         if len(probs) == 1:
             r = ext.ext_solve(ctx, dprobs[0], phis[0], fs[0], outs[0])
             return [r]
-        rc, res = ext.ext_solve_batch(ctx, dprobs, phis, fs, outs)
+        rc, res = ext.ext_solve_batch(ctx, dprobs, phis, fs, outs, check=False)
         return res
 
     for _ in range(args.warmup):
@@ -197,29 +232,52 @@ def run_ours(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
         torch.distributed.barrier()
-    solves = len(probs) * args.steps * world
+    solves = sum(1 for r in results if r.get("status", 0) == 0) * args.steps * world
     value = solves / (total_ms / 1e3)
+    serving = None
+    if serve_stats:
+        lat = sorted(x for st in serve_stats for x in st["lat_ms"])
+        wall = sum(st["wall_s"] for st in serve_stats)
+        value = solves / wall  # arrivals pace the step: throughput over wall time
+        serving = {"p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 3),
+                   "requests": len(lat), "offered_rate_per_s": args.rate}
     iters = [r["iters"] for r in results]
     nodes = sum(p.nx * p.ny for p in probs)
     pt_its = sum(p.nx * p.ny * r["iters"] for p, r in zip(probs, results))
 
+    # the plain FP32 single-solve path on a sample of the same grids (the comparison the batched
+    # and served paths are measured against)
+    plain = None
+    if args.workload != "single":
+        k = min(args.plain_sample, len(probs))
+        pctx = ext.ext_create(ext.options("fp32", rtol=1e-8, maxit=maxit), stream=stream)
+        ext.ext_solve(pctx, dprobs[0], phis[0], fs[0], outs[0], check=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for j in range(k):
+            ext.ext_solve(pctx, dprobs[j], phis[j], fs[j], outs[j], check=False)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        ext.ext_destroy(pctx)
+        plain = {"value": round(k / el, 4), "unit": "solves/s", "sample": f"first {k} grids of the workload, one ext_solve each, FP32 path"}
+
     # end to end through the public API with host (pinned) buffers
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.workload != "serve":
         hphis = [torch.from_numpy(p.phi).pin_memory() for p in probs]
         hfs = [torch.from_numpy(p.f).pin_memory() for p in probs]
         houts = [torch.empty(p.phi.shape, dtype=torch.float32).pin_memory() for p in probs]
         if len(probs) == 1:
             ext.ext_solve(ctx, dprobs[0], hphis[0], hfs[0], houts[0])
         else:
-            ext.ext_solve_batch(ctx, dprobs, hphis, hfs, houts)
+            ext.ext_solve_batch(ctx, dprobs, hphis, hfs, houts, check=False)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             if len(probs) == 1:
                 ext.ext_solve(ctx, dprobs[0], hphis[0], hfs[0], houts[0])
             else:
-                ext.ext_solve_batch(ctx, dprobs, hphis, hfs, houts)
+                ext.ext_solve_batch(ctx, dprobs, hphis, hfs, houts, check=False)
         torch.cuda.synchronize()
         el = time.perf_counter() - t0
         e2e = {"value": len(probs) * args.steps * world / el, "unit": "solves/s",
@@ -229,11 +287,15 @@ def run_ours(args, rank, world):
     # per-kernel CUDA-event durations of the same workload (a profiled pass: no graphs)
     roofline, kernels = None, None
     if not args.no_profile and rank == 0:
-        pctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=maxit, profile=1), stream=stream)
-        if len(probs) == 1:
-            ext.ext_solve(pctx, dprobs[0], phis[0], fs[0], outs[0])
+        # profiled pass: the first 100 iterations, during which every instance is still iterating,
+        # so each launch processes the whole workload (the algorithmic cost per launch holds)
+        pctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=100, profile=1), stream=stream)
+        if args.workload == "serve":
+            ext.ext_solve_batch(pctx, dprobs, phis, fs, outs, check=False)
+        elif len(probs) == 1:
+            ext.ext_solve(pctx, dprobs[0], phis[0], fs[0], outs[0], check=False)
         else:
-            ext.ext_solve_batch(pctx, dprobs, phis, fs, outs)
+            ext.ext_solve_batch(pctx, dprobs, phis, fs, outs, check=False)
         prof = ext.ext_profile_read(pctx)
         ext.ext_destroy(pctx)
         tot = sum(ms for ms, n in prof.values())
@@ -245,7 +307,16 @@ def run_ours(args, rank, world):
         amount, unit = algorithmic_cost(probs, dom)
         if amount is not None and n:
             per_launch_s = ms / n / 1e3
-            if unit == "flop":
+            if unit == "flop" and prec != "fp32":
+                # tensor-core stage: algorithmic flops (2 n^3-type, unpadded) against the measured
+                # sustained dense BF16 peak; the MMAs actually issued are six slice products
+                # over padded tiles, reported beside it
+                achieved = amount / per_launch_s / 1e12
+                with open(PEAKS_FILE) as fh:
+                    peak = json.load(fh)["bf16_tflops_sustained"]
+                bound, u = "tensor", "TFLOP/s"
+                peak_src = "measured bf16_tflops_sustained"
+            elif unit == "flop":
                 achieved = amount / per_launch_s / 1e12
                 peak, bound, u = FP32_ALU_PEAK_TFLOPS, "alu", "TFLOP/s"
                 peak_src = "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz"
@@ -258,8 +329,8 @@ def run_ours(args, rank, world):
             if os.path.exists(TRAFFIC_FILE):
                 with open(TRAFFIC_FILE) as fh:
                     tr = json.load(fh)
-                ent = tr.get(f"{dom}:{cfg['workload']}")
-                if ent and ent.get("source_hash") == kernel_hash(dom):
+                ent = tr.get(f"{dom}:{prec}:{cfg['workload']}")
+                if ent and ent.get("source_hash") == kernel_hash(dom, prec):
                     traffic = ent.get("bytes_per_launch")
             roofline = {"kernel": dom, "bound": bound, "achieved": round(achieved, 3),
                         "peak": round(peak, 3), "unit": u, "frac": round(achieved / peak, 4),
@@ -278,6 +349,8 @@ def run_ours(args, rank, world):
            {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},
            "grid_point_iterations_per_s": round(pt_its * args.steps * world / (total_ms / 1e3), 1),
            "relres_true_max": max(r["relres_true"] for r in results),
+           "all_converged": all(r.get("status", 0) == 0 for r in results),
+           "plain_fp32_single_solve": plain, "serving": serving,
            "e2e": e2e, "roofline": roofline, "kernels": kernels,
            "gpu_launches": launches, "clocks": clk}
     return out, probs

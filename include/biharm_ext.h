@@ -91,8 +91,9 @@ enum {
   EXT_KERNEL_PREC2 = 6,
   EXT_KERNEL_PREC3 = 7,
   EXT_KERNEL_OUTPUT = 8,         /* out = f on Omega, x elsewhere                            */
-  EXT_KERNEL_SPLIT = 9,          /* residual -> scaled 16-bit planes (mixed modes)            */
-  EXT_KERNEL_KINDS = 10
+  EXT_KERNEL_SPLIT = 9,          /* residual -> 16-bit integer slices (mixed modes)           */
+  EXT_KERNEL_PREC_FINISH = 10,   /* per-slot r.z, z.q -> rho, beta                            */
+  EXT_KERNEL_KINDS = 11
 };
 
 typedef struct {

@@ -151,6 +151,7 @@ static bool is_device_ptr(const void* p) {
 }
 
 // ---- tensor-core operands --------------------------------------------------------------------
+constexpr int kExpBlock = 64;  // k per block exponent of the sliced operands (kernels_gemm_tc.cu KC)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -214,7 +215,7 @@ static int block_exp_host(const double* v, size_t stride, int count) {
   if (!(m > 0.0)) return 0;
   int e;
   std::frexp(m, &e);
-  if (std::ldexp(m, 8 - e) >= 255.5) ++e;
+  if (count > 64 && std::ldexp(m, 8 - e) >= 255.5) ++e;
   return std::max(e, -100);
 }
 
@@ -227,7 +228,7 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
     P->tc = nullptr;
   }
   const int NS = tc_planes(ctx->split);
-  const int np = P->np, n = P->n, nkb = np / 128;
+  const int np = P->np, n = P->n, nkb = np / kExpBlock;
   const size_t plane = (size_t)np * np;
   std::vector<uint16_t> h(2 * NS * plane, 0);
   std::vector<int8_t> ex(2 * (size_t)np * nkb, 0);
@@ -244,10 +245,11 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
     int8_t* eo = ex.data() + t * (size_t)np * nkb;
     for (int row = 0; row < np; ++row)
       for (int kb = 0; kb < nkb; ++kb) {
-        const double* blk = M.data() + (size_t)row * np + kb * 128;
-        const int E = block_exp_host(blk, 1, 128);
+        const double* blk = M.data() + (size_t)row * np + kb * kExpBlock;
+        const int E = block_exp_host(blk, 1, kExpBlock);
         eo[(size_t)row * nkb + kb] = (int8_t)E;
-        for (int k = 0; k < 128; ++k) slice_host(blk[k], E, ctx->split, out, plane, (size_t)row * np + kb * 128 + k);
+        for (int k = 0; k < kExpBlock; ++k)
+          slice_host(blk[k], E, ctx->split, out, plane, (size_t)row * np + kb * kExpBlock + k);
       }
   }
   const size_t bytes = 2 * h.size() + ex.size();
@@ -265,7 +267,7 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
 // Exponent arrays of a plan: t = 0 for Q rows, 1 for Q^T rows.
 static const int8_t* plan_exps(const PlanDev* P, int t) {
   const size_t plane = (size_t)P->np * P->np;
-  const size_t nkb = P->np / 128;
+  const size_t nkb = P->np / kExpBlock;
   return (const int8_t*)((const char*)P->tc + 2 * 2 * 3 * plane) + t * (size_t)P->np * nkb;
 }
 
@@ -671,6 +673,9 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
       else launch_prec_tc(g, s, mode, ctx->split, ctx->d_err);
     }, g.stream);
   }
+  LaunchCfg f = cfg_of(ctx, W, 2);
+  f.grid = std::max(1, std::min(W->n_gm, ctx->sm_count * 4));
+  timed(ctx, EXT_KERNEL_PREC_FINISH, [&] { launch_prec_finish(f, mode); }, f.stream);
 }
 
 static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {

@@ -26,6 +26,8 @@ void launch_update(const LaunchCfg& c);
 void launch_true_residual(const LaunchCfg& c);
 void launch_output(const LaunchCfg& c, const float* const* fs, float* const* outs);
 void launch_output64(const SlotDesc* slot, int n, const float* f, double* out, cudaStream_t s);
+// per-slot reduction of the last preconditioner stage's r.z, z.q partials -> rho, beta
+void launch_prec_finish(const LaunchCfg& c, int mode);
 void launch_apply(const SlotDesc* slot, int n_tiles, bool aniso, const float* p, float* q,
                   double* part, cudaStream_t s);
 

@@ -5,7 +5,8 @@
 //   stage 0: T1[kx][y]  = sum_x r[y][x]  Qx[x][kx]       (forward transform along x)
 //   stage 1: T2[ky][kx] = w(ky,kx) sum_y T1[kx][y] Qy[y][ky]   (along y, times 1/(lam+mu)^2)
 //   stage 2: T3[x][ky]  = sum_kx T2[ky][kx] Qx[x][kx]    (inverse along x)
-//   stage 3: z[y][x]    = mask(y,x) sum_ky T3[x][ky] Qy[y][ky] (inverse along y), plus r.z, z.q
+//   stage 3: z[y][x]    = mask(y,x) sum_ky T3[x][ky] Qy[y][ky] (inverse along y), plus partial
+//            r.z, z.q per tile (reduced by k_prec_finish)
 // Every stage is D[m][n] = sum_k A[m][k] B[n][k] with both operands k-contiguous, written out
 // transposed (Out[n][m]) so the next stage again reads a k-contiguous operand.  The division by
 // the squared eigenvalue sums is fused into stage 1's epilogue, masking and the CG inner
@@ -174,14 +175,9 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
     if (STAGE == 3) {
       double d_rz = c_rz.value(), d_zq = c_zq.value();
       block_sum2<NT>(d_rz, d_zq, red);
-      if (t == 0) {
-        S.part[item.tile * 4 + 0] = d_rz;
-        S.part[item.tile * 4 + 1] = d_zq;
-      }
-      if (last_item_block(&sc->cnt[4], S.n_gm_tiles, &s_last)) {
-        double sums[2];
-        reduce_partials<NT, 2>(S.part, S.n_gm_tiles, sums, red);
-        if (t == 0) finish_preconditioner(S, sums[0], sums[1], mode);
+      if (t == 0) {  // tile partials; k_prec_finish forms rho and beta from them
+        S.part[item.tile * 4 + 2] = d_rz;
+        S.part[item.tile * 4 + 3] = d_zq;
       }
     }
     __syncthreads();

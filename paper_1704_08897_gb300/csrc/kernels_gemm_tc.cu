@@ -6,15 +6,16 @@
 // even float hi/lo operand splits lose too much in the tensor core's truncating FP32
 // accumulation.  The products are therefore made exact:
 //
-//  * every operand is cut into blocks of 128 consecutive k; a block with largest magnitude below
-//    2^E is stored as three integer slices, v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24),
-//    |c0| <= 255, |c1|, |c2| <= 128 (exact in FP16 and BF16), plus the exponent E (int8);
+//  * every operand is cut into blocks of KC = 64 consecutive k; a block with largest magnitude
+//    below 2^E is stored as three integer slices, v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24),
+//    |c0| <= 256, |c1|, |c2| <= 128 (exact in FP16 and BF16), plus the exponent E (int8);
 //  * for each slice order d = i + j (products c_i c'_j, d <= 2: six MMAs per k-step) a separate
-//    TMEM accumulator sums one 128-wide k-block: for d = 2 at most 128 * (2*255*128 + 128^2)
-//    < 2^24, so every partial sum is an exact integer and so is the accumulation;
+//    TMEM accumulator sums one k-block: at most 3 * 64 products below 2^16, so every partial sum
+//    is an exact integer below 2^24 and so is the accumulation (128-wide blocks would also stay
+//    exact with |c0| <= 255, but the coarser exponents cost this operator many CG iterations);
 //  * the epilogue warps scale the three exact sums by 2^(E_A + E_B - 16 - 8d) and add them into
 //    a compensated (hi, lo) register pair, k-block after k-block.
-// The result carries about 24 bits relative to each 128-block's largest value, with no error
+// The result carries about 24 bits relative to each 64-block's largest value, with no error
 // growth along K.  The writer of the next stage's operand computes its block exponents with a
 // two-warp maximum and stores the slices transposed (Out[n][m], coalesced along m).
 //
@@ -23,7 +24,7 @@
 //   warp 1      : TMEM allocation; lane 0 issues the MMAs and the tcgen05.commit arrivals
 //   warps 2..9  : two per TMEM lane quarter (32 rows), each owning 32 of the tile's 64 columns:
 //                 exact k-block sums -> compensated registers -> the stage's epilogue
-//                 (eigenvalue weights; masking, FP64 dot products and CG scalars in stage 3).
+//                 (eigenvalue weights; masking and per-tile r.z, z.q partials in stage 3).
 // Every wait on an mbarrier is bounded; on time-out the CTA raises an error flag, drains its
 // outstanding copies and MMAs, frees its TMEM and returns.
 #include <cuda.h>
@@ -37,7 +38,8 @@ namespace bx {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 64;  // BK: one 128-byte swizzle atom per pipeline stage
-constexpr int KC = 128;                     // k per exact accumulation block (two pipeline stages)
+constexpr int KC = 64;                      // k per exponent / exact accumulation block
+constexpr int KPC = KC / BK;                // pipeline stages per accumulation block
 constexpr int NS = 3;                            // slices per operand
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -169,13 +171,13 @@ __device__ __forceinline__ float pow2f(int e) {
   return e < -126 ? 0.f : __int_as_float((min(e, 127) + 127) << 23);
 }
 
-// Exponent E of a block whose largest magnitude is amax: amax < 2^E and amax 2^(8-E) < 255.5,
-// so the leading slice stays within +-255 (0 for an all-zero block).
+// Exponent E of a block whose largest magnitude is amax: amax < 2^E (0 for an all-zero block);
+// for blocks wider than 64 also amax 2^(8-E) < 255.5, so the leading slice stays within +-255.
 __device__ __forceinline__ int block_exp(float amax) {
   if (!(amax > 0.f)) return 0;
   int e;
   frexpf(amax, &e);
-  if (amax * pow2f(8 - e) >= 255.5f) ++e;
+  if (KC > 64 && amax * pow2f(8 - e) >= 255.5f) ++e;
   return max(e, -100);
 }
 
@@ -327,7 +329,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         if (!slot_runs(S.sc, mode)) continue;
         const TcStage v = tc_stage(S, STAGE);
         for (int kb = 0; kb < v.K / BK; ++kb) {
-          const int half_kb = kb & 1;  // position inside the 128-wide accumulation block
+          const int half_kb = kb % KPC;  // position inside the accumulation block
           const int cb = chunk % kChunks;
           if ((half_kb == 0 && !mbar_wait(&ctl->tempty[cb], ((chunk / kChunks) & 1) ^ 1, abort_flag)) ||
               !mbar_wait(&ctl->full[stage], phase, abort_flag)) {
@@ -353,7 +355,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             }
           }
           umma_commit(&ctl->empty[stage]);
-          if (half_kb == 1) {
+          if (half_kb == KPC - 1) {
             umma_commit(&ctl->tfull[cb]);
             ++chunk;
           }
@@ -464,7 +466,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         }
       }
       if (STAGE <= 2) {
-        // block exponents of the next operand: rows n, k-blocks of 128 consecutive m (this tile)
+        // block exponents of the next operand: rows n, k-blocks of KC consecutive m (lane quarters
+        // 32q .. 32q+31 of this tile; KC/32 quarters per block)
         float mine = 0.f;
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
@@ -473,8 +476,10 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         }
         ctl->colmax[half][quarter][lane] = mine;
         epi_bar();
-        const float bmax = fmaxf(fmaxf(ctl->colmax[half][0][lane], ctl->colmax[half][1][lane]),
-                                 fmaxf(ctl->colmax[half][2][lane], ctl->colmax[half][3][lane]));
+        float bmax = 0.f;
+        const int q0 = (quarter / (KC / 32)) * (KC / 32);
+#pragma unroll
+        for (int q = 0; q < KC / 32; ++q) bmax = fmaxf(bmax, ctl->colmax[half][q0 + q][lane]);
         const int E_mine = block_exp(bmax);
         epi_bar();
         const size_t plane = static_cast<size_t>(v.M) * v.N;
@@ -484,8 +489,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           const int E = __shfl_sync(0xffffffffu, E_mine, i);
           slice_store<BF16>(out, plane, static_cast<size_t>(ncol0 + i) * v.M + m, val[i], E);
         }
-        if (quarter == 0)
-          v.eout[static_cast<size_t>(ncol0 + lane) * (v.M / KC) + m0 / KC] = static_cast<int8_t>(E_mine);
+        if (quarter == q0)
+          v.eout[static_cast<size_t>(ncol0 + lane) * (v.M / KC) + (m0 + 32 * quarter) / KC] =
+              static_cast<int8_t>(E_mine);
       } else {
         CompDot c_rz, c_zq;
 #pragma unroll
@@ -499,8 +505,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             c_zq.add(zv, S.q[g]);
           }
         }
-        // tile partials of r.z and z.q (FP32-compensated inside the warp), then the slot's last
-        // tile forms rho and beta
+        // tile partials of r.z and z.q (FP32-compensated inside the warp)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
           float e;
@@ -524,40 +529,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             a += ctl->red[2 * k];
             b += ctl->red[2 * k + 1];
           }
-          S.part[it.tile * 4 + 0] = a;
-          S.part[it.tile * 4 + 1] = b;
-          __threadfence();
-          const unsigned prev = atomicAdd(&sc->cnt[4], 1u);
-          const int last = (prev == static_cast<unsigned>(S.n_tc_tiles) - 1) ? 1 : 0;
-          if (last) {
-            __threadfence();
-            sc->cnt[4] = 0u;
-          }
-          ctl->last = last;
-        }
-        epi_bar();
-        if (ctl->last) {
-          double a = 0.0, b = 0.0;
-          for (int k = ew * 32 + lane; k < S.n_tc_tiles; k += 32 * kEpiWarps) {
-            a += __ldcg(&S.part[k * 4 + 0]);
-            b += __ldcg(&S.part[k * 4 + 1]);
-          }
-          a = warp_sum(a);
-          b = warp_sum(b);
-          epi_bar();
-          if (lane == 0) {
-            ctl->red[2 * ew] = a;
-            ctl->red[2 * ew + 1] = b;
-          }
-          epi_bar();
-          if (ew == 0 && lane == 0) {
-            double rz = 0.0, zq = 0.0;
-            for (int k = 0; k < kEpiWarps; ++k) {
-              rz += ctl->red[2 * k];
-              zq += ctl->red[2 * k + 1];
-            }
-            finish_preconditioner(S, rz, zq, mode);
-          }
+          // tile partials; k_prec_finish forms rho and beta from them
+          S.part[it.tile * 4 + 2] = a;
+          S.part[it.tile * 4 + 3] = b;
         }
         epi_bar();
       }
@@ -574,9 +548,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
 }
 
-// Residual -> slices of the first stage's A operand.  One warp per (row, 128-column block); the
-// work list is the stencil's (64 x 16 tiles): tiles starting at an even multiple of 64 take the
-// 128 columns of their block, the others have nothing to do.
+// Residual -> slices of the first stage's A operand.  One warp per (row, KC-column block); the
+// work list is the stencil's (64 x 16 tiles): a tile starting at a multiple of KC takes the KC
+// columns of its block, the others (if KC > 64) have nothing to do.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
@@ -599,17 +573,17 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     for (int ly = warp; ly < kStTileY; ly += 8) {
       const int y = y0 + ly;
       if (y >= S.ny) break;
-      float v[4];
+      float v[KC / 32];
       float amax = 0.f;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < KC / 32; ++k) {
         const int x = x0 + 32 * k + lane;
         v[k] = x < S.nx ? S.r[y * S.nx + x] : 0.f;
         amax = fmaxf(amax, fabsf(v[k]));
       }
       const int E = block_exp(warp_max(amax));
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < KC / 32; ++k)
         slice_store<BF16>(out, plane, static_cast<size_t>(y) * S.nxp + x0 + 32 * k + lane, v[k], E);
       if (lane == 0) S.tc_e[0][static_cast<size_t>(y) * kblocks + x0 / KC] = static_cast<int8_t>(E);
     }

@@ -409,6 +409,34 @@ k_true_residual(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__
 }
 
 // ---------------------------------------------------------------------------------------------
+// After the last preconditioner stage: one block per slot (the slot's tile-0 item of the
+// transform work list) reduces the per-tile r.z and z.q partials in a fixed order and forms rho
+// and beta (flexible or Fletcher-Reeves), or flags breakdown.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_prec_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+              const int* __restrict__ n_items, int mode) {
+  __shared__ double red[64];
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    if (it.tile != 0) continue;
+    const SlotDesc& S = slots[it.slot];
+    SlotScalars* sc = S.sc;
+    const int run = mode == 0 ? sc->active : (mode == 1 ? sc->need_prec : 1);
+    if (!run) continue;
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < S.n_gm_tiles; t += blockDim.x) {
+      a += S.part[t * 4 + 2];
+      b += S.part[t * 4 + 3];
+    }
+    block_sum2<256>(a, b, red);
+    if (threadIdx.x == 0) finish_preconditioner(S, a, b, mode);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Output (Algorithm 1, last statement): out = f at known nodes (bit copy), xhat at unknowns.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecThreads)
@@ -494,6 +522,9 @@ void launch_true_residual(const LaunchCfg& c) {
 }
 void launch_output(const LaunchCfg& c, const float* const* fs, float* const* outs) {
   k_output<<<c.grid, kVecThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, fs, outs);
+}
+void launch_prec_finish(const LaunchCfg& c, int mode) {
+  k_prec_finish<<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
 }
 void launch_output64(const SlotDesc* slot, int n, const float* f, double* out, cudaStream_t s) {
   int grid = (n + kVecThreads - 1) / kVecThreads;
