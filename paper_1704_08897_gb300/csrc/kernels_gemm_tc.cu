@@ -401,8 +401,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       bool fail_all = false;
       for (int kb = 0; kb < kblocks; ++kb) {
         const int cb = chunk % kChunks;
-        const int ea = ea_row[kb];
-        const int eb_mine = eb[static_cast<size_t>(ncol0 + lane) * kblocks + kb];
+        // scale of the block sums: 2^(E_A + E_B - 16), as an exact product of two powers of two
+        const float sa = pow2f(static_cast<int>(ea_row[kb]) - 16);
+        const float sb_mine = pow2f(eb[static_cast<size_t>(ncol0 + lane) * kblocks + kb]);
         // all epilogue warps leave together if any of them gave up waiting
         const uint32_t fail = mbar_wait(&ctl->tfull[cb], (chunk / kChunks) & 1, abort_flag) ? 0u : 1u;
         uint32_t any_fail;
@@ -435,15 +436,14 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
             const int c = hc * 16 + i;
-            const int e = ea + __shfl_sync(0xffffffffu, eb_mine, c) - 16;
-            const float t0 = __uint_as_float(s0[i]) * pow2f(e);
-            const float t1 = __uint_as_float(s1[i]) * pow2f(e - 8);
-            const float t2 = __uint_as_float(s2[i]) * pow2f(e - 16);
+            const float sc = sa * __shfl_sync(0xffffffffu, sb_mine, c);
+            // orders 1 and 2 combined first: their rounding is 2^-24 of a term 2^-8 below hi
+            const float u = __fmaf_rn(__uint_as_float(s2[i]), 0.00390625f, __uint_as_float(s1[i]));
+            const float t0 = __uint_as_float(s0[i]) * sc;
+            const float t1 = u * (sc * 0.00390625f);
             float er;
             two_sum(hi[c], t0, hi[c], er);
-            lo[c] = __fadd_rn(lo[c], er);
-            two_sum(hi[c], t1, hi[c], er);
-            lo[c] = __fadd_rn(lo[c], __fadd_rn(er, t2));
+            lo[c] = __fadd_rn(lo[c], __fadd_rn(er, t1));
           }
         }
         ++chunk;
@@ -494,15 +494,29 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               static_cast<int8_t>(E_mine);
       } else {
         CompDot c_rz, c_zq;
+        if (m < S.nx) {
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int n = ncol0 + i;
-          if (n < S.ny && m < S.nx) {
-            const int g = n * S.nx + m;
-            const float zv = S.mask[g] ? val[i] : 0.f;
-            S.z[g] = zv;
-            c_rz.add(S.r[g], zv);
-            c_zq.add(zv, S.q[g]);
+          for (int g8 = 0; g8 < 32; g8 += 8) {
+            float rv[8], qv[8];
+            uint8_t mk[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {  // issue the group's loads together
+              const int n = ncol0 + g8 + i;
+              const int g = (n < S.ny ? n : 0) * S.nx + m;
+              rv[i] = S.r[g];
+              qv[i] = S.q[g];
+              mk[i] = n < S.ny ? S.mask[g] : 0;
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const int n = ncol0 + g8 + i;
+              if (n < S.ny) {
+                const float zv = mk[i] ? val[g8 + i] : 0.f;
+                S.z[n * S.nx + m] = zv;
+                c_rz.add(rv[i], zv);
+                c_zq.add(zv, qv[i]);
+              }
+            }
           }
         }
         // tile partials of r.z and z.q (FP32-compensated inside the warp)
