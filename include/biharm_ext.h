@@ -93,7 +93,8 @@ enum {
   EXT_KERNEL_OUTPUT = 8,         /* out = f on Omega, x elsewhere                            */
   EXT_KERNEL_SPLIT = 9,          /* residual -> 16-bit integer slices (mixed modes)           */
   EXT_KERNEL_PREC_FINISH = 10,   /* per-slot r.z, z.q -> rho, beta                            */
-  EXT_KERNEL_KINDS = 11
+  EXT_KERNEL_PQ_FINISH = 11,     /* per-slot p.q -> alpha                                     */
+  EXT_KERNEL_KINDS = 12
 };
 
 typedef struct {
@@ -206,7 +207,7 @@ int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float*
  * No context is needed.  phi, p and q are device pointers, [ny][nx] float32; the call runs on
  * cuda_stream (NULL = the default stream) and returns after that stream has finished its work.
  * Scratch: one fixed 2 MiB array per device (grids up to 1,048,576 nodes and 32,768 stencil
- * tiles of 64x16; larger grids return EXT_EINVAL, see ext_noalloc_last_error).  The first call on
+ * tiles of 64x32; larger grids return EXT_EINVAL, see ext_noalloc_last_error).  The first call on
  * a device looks up that array's device address; make that first call before any stream capture.
  * All calls on a device share the array: calls whose GPU work overlaps race and must be
  * serialised by the caller.  Nothing in it needs to start at zero. */

@@ -682,6 +682,9 @@ static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
   const LaunchCfg st = cfg_of(ctx, W, 0), vc = cfg_of(ctx, W, 1);
   for (int i = 0; i < iters; ++i) {
     timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(st, W->aniso); }, st.stream);
+    LaunchCfg pf = st;
+    pf.grid = std::max(1, std::min(W->n_st, ctx->sm_count * 4));
+    timed(ctx, EXT_KERNEL_PQ_FINISH, [&] { launch_pq_finish(pf); }, st.stream);
     timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); }, st.stream);
     launch_prec(ctx, W, 0);
   }

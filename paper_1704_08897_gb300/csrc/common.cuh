@@ -13,7 +13,7 @@ namespace bx {
 
 constexpr int kPad = 128;           // transform buffers are padded to multiples of this
 constexpr int kStTileX = 64;        // stencil tile (x contiguous)
-constexpr int kStTileY = 16;
+constexpr int kStTileY = 32;
 constexpr int kStThreads = 256;
 constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels
 constexpr int kVecThreads = 256;

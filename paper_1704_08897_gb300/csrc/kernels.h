@@ -22,6 +22,8 @@ void set_weights(SlotDesc& d, double hx, double hy);
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
                   const int* dirs);
 void launch_stencil(const LaunchCfg& c, bool aniso);
+// per-slot p.q -> alpha (after the stencil)
+void launch_pq_finish(const LaunchCfg& c);
 void launch_update(const LaunchCfg& c);
 void launch_true_residual(const LaunchCfg& c);
 void launch_output(const LaunchCfg& c, const float* const* fs, float* const* outs);

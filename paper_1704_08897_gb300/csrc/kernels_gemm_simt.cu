@@ -57,7 +57,6 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
   __shared__ __align__(16) float As[2][BK][BM + 4];
   __shared__ __align__(16) float Bs[2][BK][BN + 4];
   __shared__ double red[64];
-  __shared__ int s_last;
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
   const int arow = t >> 1, acol = (t & 1) * 8;  // A tile 128 x 16: 8 per thread

@@ -563,7 +563,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
 }
 
 // Residual -> slices of the first stage's A operand.  One warp per (row, KC-column block); the
-// work list is the stencil's (64 x 16 tiles): a tile starting at a multiple of KC takes the KC
+// work list is the stencil's (64 x 32 tiles): a tile starting at a multiple of KC takes the KC
 // columns of its block, the others (if KC > 64) have nothing to do.
 template <bool BF16>
 __global__ void __launch_bounds__(256)

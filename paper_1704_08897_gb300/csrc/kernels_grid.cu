@@ -170,8 +170,8 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
 
 // ---------------------------------------------------------------------------------------------
 // Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo),
-// q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), partial p.q in FP64.
-// The last item of the slot forms alpha = rho / p.q and flags breakdown.
+// q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), per-tile partial p.q;
+// k_pq_finish then forms alpha = rho / p.q for each slot.
 // ---------------------------------------------------------------------------------------------
 template <bool ANISO>
 __global__ void __launch_bounds__(kStThreads)
@@ -179,7 +179,6 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           const int* __restrict__ n_items) {
   __shared__ float sp[kHalo];
   __shared__ double red[64];
-  __shared__ int s_last;
   const int total = *n_items;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem it = items[w];
@@ -230,20 +229,35 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       dot.add(pv, qv);
     }
     const double pq = block_sum_comp<kStThreads>(dot, red);
-    if (threadIdx.x == 0) S.part[it.tile * 4 + 0] = pq;
-    if (last_item_block(&sc->cnt[1], S.n_st_tiles, &s_last)) {
-      double sums[1];
-      reduce_partials<kStThreads, 1>(S.part, S.n_st_tiles, sums, red);
-      if (threadIdx.x == 0) {
-        const double s = sums[0];
-        sc->pq = s;
-        if (!(s > 0.0) || !isfinite(s) || !isfinite(sc->rho)) {
-          sc->status = ST_EBREAKDOWN;
-          sc->active = 0;
-          sc->fold = 1;  // the tail folds and reports the best iterate
-        } else {
-          sc->alpha = sc->rho / s;
-        }
+    if (threadIdx.x == 0) S.part[it.tile * 4 + 1] = pq;  // reduced by k_pq_finish
+    __syncthreads();
+  }
+}
+
+// One block per slot (the slot's tile-0 stencil item): p.q from the stencil's per-tile partials
+// in a fixed order, alpha = rho / p.q, breakdown detection.
+__global__ void __launch_bounds__(256)
+k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+            const int* __restrict__ n_items) {
+  __shared__ double red[64];
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    if (it.tile != 0) continue;
+    const SlotDesc& S = slots[it.slot];
+    SlotScalars* sc = S.sc;
+    if (!sc->active) continue;
+    double a = 0.0, b = 0.0;
+    for (int t = threadIdx.x; t < S.n_st_tiles; t += blockDim.x) a += S.part[t * 4 + 1];
+    block_sum2<256>(a, b, red);
+    if (threadIdx.x == 0) {
+      sc->pq = a;
+      if (!(a > 0.0) || !isfinite(a) || !isfinite(sc->rho)) {
+        sc->status = ST_EBREAKDOWN;
+        sc->active = 0;
+        sc->fold = 1;  // the tail replaces the residual and reports the best iterate
+      } else {
+        sc->alpha = sc->rho / a;
       }
     }
     __syncthreads();
@@ -513,6 +527,9 @@ void launch_setup(const LaunchCfg& c, const float* const* phis, const float* con
 void launch_stencil(const LaunchCfg& c, bool aniso) {
   if (aniso) k_stencil<true><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
   else k_stencil<false><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
+}
+void launch_pq_finish(const LaunchCfg& c) {
+  k_pq_finish<<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items);
 }
 void launch_update(const LaunchCfg& c) {
   k_update<<<c.grid, kVecThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);

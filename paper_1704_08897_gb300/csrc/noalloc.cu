@@ -83,7 +83,7 @@ extern "C" int ext_apply_biharmonic_noalloc(const ext_problem* prob, const float
                         ((prob->ny + kStTileY - 1) / kStTileY);
   if (n > kNoAllocMaxNodes || tiles > kNoAllocMaxTiles) {
     g_noalloc_err = "grid too large for the fixed no-allocation scratch (at most 1048576 nodes "
-                    "and 32768 stencil tiles of 64x16)";
+                    "and 32768 stencil tiles of 64x32)";
     return EXT_EINVAL;
   }
   // Once per device, with that device current: the device address of the scratch array.

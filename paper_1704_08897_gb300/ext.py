@@ -31,7 +31,8 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
             "ext_noalloc_last_error"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
-                "prec_stage2", "prec_stage3", "output", "split", "prec_finish"]
+                "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
+                "pq_finish"]
 
 
 class ExtProblem(C.Structure):
