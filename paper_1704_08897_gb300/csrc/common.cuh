@@ -260,13 +260,20 @@ __device__ __forceinline__ int ghost(int i, int n, int bc, float& sgn) {
   return i < 0 ? -i - 2 : 2 * n - i;
 }
 
+// wnorm / s^2 by the approximate division (at most 2 ulp for s^2 in [2^-126, 2^126]; s^2 of the
+// grids' eigenvalue sums stays far inside that range).  The preconditioner is only an
+// approximation of the inverse, so a 2-ulp change of its weights is immaterial.
+__device__ __forceinline__ float spectral_weight_of(float wnorm, float s) {
+  return __fdividef(wnorm, s * s);
+}
+
 // Spectral weight 1/(lam_y + lam_x)^2, normalised to <= 1; zero for padding and the constant
 // mode when both axes are symmetric/periodic (pseudo-inverse).
 __device__ __forceinline__ float spectral_weight(const SlotDesc& S, int kx, int ky) {
   if (kx >= S.nx || ky >= S.ny) return 0.f;
   const float s = S.lamy[ky] + S.lamx[kx];
   if (!(s > 0.f)) return 0.f;
-  return S.wnorm / (s * s);
+  return spectral_weight_of(S.wnorm, s);
 }
 
 // Last item of stage 3 (thread 0): r.z, z.q -> rho, beta (flexible or Fletcher-Reeves).

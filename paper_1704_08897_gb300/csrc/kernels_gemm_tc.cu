@@ -22,7 +22,7 @@
 // Kernel structure (one CTA per SM, persistent over the (slot, tile) work list):
 //   warp 0      : TMA producer: 128B-swizzled K-major tiles of the three slices of A and B
 //   warp 1      : TMEM allocation; lane 0 issues the MMAs and the tcgen05.commit arrivals
-//   warps 2..9  : two per TMEM lane quarter (32 rows), each owning 32 of the tile's 64 columns:
+//   warps 2..17 : four per TMEM lane quarter (32 rows), each owning 16 of the tile's 64 columns:
 //                 exact k-block sums -> compensated registers -> the stage's epilogue
 //                 (eigenvalue weights; masking and per-tile r.z, z.q partials in stage 3).
 // Every wait on an mbarrier is bounded; on time-out the CTA raises an error flag, drains its
@@ -41,8 +41,15 @@ constexpr int BM = 128, BN = 64, BK = 64;  // BK: one 128-byte swizzle atom per 
 constexpr int KC = 64;                      // k per exponent / exact accumulation block
 constexpr int KPC = KC / BK;                // pipeline stages per accumulation block
 constexpr int NS = 3;                            // slices per operand
-constexpr int kEpiWarps = 8;
+constexpr int kEpiWarps = 16;
+constexpr int kColGroups = kEpiWarps / 4;        // epilogue warps per TMEM lane quarter
+constexpr int kEpiCols = BN / kColGroups;        // tile columns per epilogue warp
+static_assert(kEpiCols % 16 == 0 && kEpiCols <= 32, "epilogue column split");
+constexpr int kLdCols = kEpiWarps == 16 ? 8 : 16;  // TMEM columns per load (register budget)
 constexpr int kThreads = 64 + 32 * kEpiWarps;
+// One CTA per SM.  Each of the SM's four schedulers owns a quarter of the register file and
+// holds up to ceil(warps / 4) of the CTA's warps.
+constexpr int kMaxRegs = (16384 / (32 * ((kThreads / 32 + 3) / 4))) & ~7;
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at 2 GHz
 constexpr int kChunks = 2;                       // TMEM ring of k-block accumulator sets
 constexpr int kSetCols = 3 * BN;                 // one accumulator per slice order
@@ -64,7 +71,7 @@ struct Ctl {
   int last;
   int pad;
   double red[2 * kEpiWarps];
-  float colmax[2][4][32];  // [column half][lane quarter][column]
+  float colmax[kColGroups][4][kEpiCols];  // [column group][lane quarter][column]
 };
 static_assert(sizeof(Ctl) <= 2048, "control block too large");
 
@@ -81,14 +88,17 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// One try: the thread may sleep in the barrier until the phase completes or kSuspendNs pass, so
+// waiting warps take few issue slots from the epilogue.
+constexpr uint32_t kSuspendNs = 20000;
 __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -143,19 +153,7 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-        "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-        "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-        "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+[[maybe_unused]] __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
       "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -163,6 +161,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
         "=r"(v[15])
       : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
+  if constexpr (N == 16) tmem_ld16(taddr, v);
+  else tmem_ld8(taddr, v);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -181,14 +189,16 @@ __device__ __forceinline__ int block_exp(float amax) {
   return max(e, -100);
 }
 
-// Three integer slices of v for block exponent E (exact residuals; last slice rounded).
+// Three integer slices of v for block exponent E, given s = 2^(8-E) and is = 2^(E-8) (both normal
+// for the exponents block_exp returns): every product below is exact, so each residual is v minus
+// the slices so far, rounded once; the last slice is rounded to an integer.
 template <bool BF16>
-__device__ __forceinline__ void slice_store(uint16_t* base, size_t plane, size_t idx, float v, int E) {
-  const float c0 = rintf(v * pow2f(8 - E));
-  const float r1 = v - c0 * pow2f(E - 8);
-  const float c1 = rintf(r1 * pow2f(16 - E));
-  const float r2 = r1 - c1 * pow2f(E - 16);
-  const float c2 = rintf(r2 * pow2f(24 - E));
+__device__ __forceinline__ void slice_store(uint16_t* base, size_t plane, size_t idx, float v, float s, float is) {
+  const float c0 = rintf(v * s);
+  const float r1 = __fmaf_rn(-c0, is, v);
+  const float c1 = rintf(r1 * (s * 256.f));
+  const float r2 = __fmaf_rn(-c1, is * 0.00390625f, r1);
+  const float c2 = rintf(r2 * (s * 65536.f));
   if (BF16) {
     base[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c0));
     base[plane + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c1));
@@ -204,6 +214,29 @@ __device__ __forceinline__ float warp_max(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
+}
+
+// Column maxima of a warp's C x 32 block (v[i]: column i of this lane's row), by a transposing
+// butterfly: at each step a lane keeps the half of its columns selected by its lane bit and takes
+// the partner's copy of that half.  Returns, in lane l, the maximum over all 32 rows of column
+// l mod C.  C - 1 exchanges instead of the C * 5 of one reduction per column.
+template <int C>
+__device__ __forceinline__ float column_max(float (&v)[C], int lane) {
+  if (C == 16) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = fmaxf(v[i], __shfl_xor_sync(0xffffffffu, v[i], 16));
+  }
+#pragma unroll
+  for (int w = C / 2; w >= 1; w /= 2) {
+    const bool up = (lane & w) != 0;
+#pragma unroll
+    for (int i = 0; i < w; ++i) {
+      const float keep = up ? v[i + w] : v[i];
+      const float give = up ? v[i] : v[i + w];
+      v[i] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, give, w));
+    }
+  }
+  return v[0];
 }
 
 __device__ __forceinline__ bool slot_runs(const SlotScalars* sc, int mode) {
@@ -230,7 +263,7 @@ __device__ __forceinline__ TcStage tc_stage(const SlotDesc& S, int stage) {
 }
 
 template <bool BF16, int STAGE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __maxnreg__(kMaxRegs)
 k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int mode, int* __restrict__ err) {
   extern __shared__ unsigned char smem_raw[];
@@ -374,10 +407,11 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     __syncwarp();
   } else {
     // ------------------------------------------------------------------ epilogue
-    const int quarter = warp & 3;        // TMEM lanes 32*quarter .. +31
-    const int half = (warp - 2) >> 2;    // columns 32*half .. +31 of the tile
+    const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+    const int group = (warp - 2) >> 2;       // columns kEpiCols*group .. +kEpiCols-1 of the tile
     const int ew = warp - 2;
     const int row = quarter * 32 + lane;
+    const bool col_lane = lane < kEpiCols;   // lanes that own one of the warp's columns
     int chunk = 0;
     for (int w = blockIdx.x; w < total && !*abort_flag; w += gridDim.x) {
       const WorkItem it = items[w];
@@ -388,13 +422,27 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       const int mt = v.M / BM;
       const int m0 = (it.tile % mt) * BM, n0 = (it.tile / mt) * BN;
       const int m = m0 + row;
-      const int ncol0 = n0 + half * 32;
+      const int ncol0 = n0 + group * kEpiCols;
       const int kblocks = v.K / KC;
+      if (STAGE == 3 && col_lane) {
+        // the r, q and mask entries read after the last k-block: start them towards L2 now
+        const int n = ncol0 + lane;
+        const int mr = min(m0 + 32 * quarter, S.nx - 1);
+        if (n < S.ny && m0 + 32 * quarter < S.nx) {
+          const size_t g = static_cast<size_t>(n) * S.nx + mr;
+          const size_t g1 = static_cast<size_t>(n) * S.nx + min(mr + 31, S.nx - 1);
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(S.r + g));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(S.r + g1));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(S.q + g));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(S.q + g1));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(S.mask + g));
+        }
+      }
       const int8_t* ea_row = S.tc_e[STAGE] + static_cast<size_t>(m) * kblocks;
-      const int8_t* eb = S.tc_eb[STAGE];
-      float hi[32], lo[32];
+      const int8_t* eb_col = S.tc_eb[STAGE] + static_cast<size_t>(ncol0 + (col_lane ? lane : 0)) * kblocks;
+      float hi[kEpiCols], lo[kEpiCols];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < kEpiCols; ++i) {
         hi[i] = 0.f;
         lo[i] = 0.f;
       }
@@ -403,7 +451,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int cb = chunk % kChunks;
         // scale of the block sums: 2^(E_A + E_B - 16), as an exact product of two powers of two
         const float sa = pow2f(static_cast<int>(ea_row[kb]) - 16);
-        const float sb_mine = pow2f(eb[static_cast<size_t>(ncol0 + lane) * kblocks + kb]);
+        const float sb_mine = pow2f(eb_col[kb]);
         // all epilogue warps leave together if any of them gave up waiting
         const uint32_t fail = mbar_wait(&ctl->tfull[cb], (chunk / kChunks) & 1, abort_flag) ? 0u : 1u;
         uint32_t any_fail;
@@ -420,27 +468,28 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           break;
         }
         tc_fence_after();
-        const uint32_t base = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + cb * kSetCols + half * 32;
+        const uint32_t base =
+            tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + cb * kSetCols + group * kEpiCols;
 #pragma unroll
-        for (int hc = 0; hc < 2; ++hc) {
-          uint32_t s0[16], s1[16], s2[16];
-          tmem_ld16(base + hc * 16, s0);
-          tmem_ld16(base + BN + hc * 16, s1);
-          tmem_ld16(base + 2 * BN + hc * 16, s2);
+        for (int hc = 0; hc < kEpiCols / kLdCols; ++hc) {
+          uint32_t s0[kLdCols], s1[kLdCols], s2[kLdCols];
+          tmem_ld<kLdCols>(base + hc * kLdCols, s0);
+          tmem_ld<kLdCols>(base + BN + hc * kLdCols, s1);
+          tmem_ld<kLdCols>(base + 2 * BN + hc * kLdCols, s2);
           tmem_wait_ld();
-          if (hc == 1) {
+          if (hc == kEpiCols / kLdCols - 1) {
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->tempty[cb]);
           }
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = hc * 16 + i;
-            const float sc = sa * __shfl_sync(0xffffffffu, sb_mine, c);
+          for (int i = 0; i < kLdCols; ++i) {
+            const int c = hc * kLdCols + i;
+            const float scl = sa * __shfl_sync(0xffffffffu, sb_mine, c);
             // orders 1 and 2 combined first: their rounding is 2^-24 of a term 2^-8 below hi
             const float u = __fmaf_rn(__uint_as_float(s2[i]), 0.00390625f, __uint_as_float(s1[i]));
-            const float t0 = __uint_as_float(s0[i]) * sc;
-            const float t1 = u * (sc * 0.00390625f);
+            const float t0 = __uint_as_float(s0[i]) * scl;
+            const float t1 = u * (scl * 0.00390625f);
             float er;
             two_sum(hi[c], t0, hi[c], er);
             lo[c] = __fadd_rn(lo[c], __fadd_rn(er, t1));
@@ -449,54 +498,55 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         ++chunk;
       }
       if (fail_all) break;
-      float val[32];
+      float val[kEpiCols];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) val[i] = __fadd_rn(hi[i], lo[i]);
+      for (int i = 0; i < kEpiCols; ++i) val[i] = __fadd_rn(hi[i], lo[i]);
       if (STAGE == 1) {
+        // weight 1/(lam_y + lam_x)^2 (normalised); lam_y of the warp's columns via shuffles
         const float lamx_m = (m < S.nx) ? S.lamx[m] : 0.f;
+        const float lamy_mine = (col_lane && ncol0 + lane < S.ny) ? S.lamy[ncol0 + lane] : 0.f;
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
+        for (int i = 0; i < kEpiCols; ++i) {
           const int n = ncol0 + i;
-          float wgt = 0.f;
-          if (m < S.nx && n < S.ny) {
-            const float s = S.lamy[n] + lamx_m;
-            wgt = (s > 0.f) ? S.wnorm / (s * s) : 0.f;
-          }
-          val[i] *= wgt;
+          const float s = __shfl_sync(0xffffffffu, lamy_mine, i) + lamx_m;
+          const bool ok = (m < S.nx) && (n < S.ny) && (s > 0.f);
+          val[i] = ok ? val[i] * spectral_weight_of(S.wnorm, s) : 0.f;
         }
       }
       if (STAGE <= 2) {
         // block exponents of the next operand: rows n, k-blocks of KC consecutive m (lane quarters
         // 32q .. 32q+31 of this tile; KC/32 quarters per block)
-        float mine = 0.f;
+        float av[kEpiCols];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const float wm = warp_max(fabsf(val[i]));
-          if (lane == i) mine = wm;
-        }
-        ctl->colmax[half][quarter][lane] = mine;
+        for (int i = 0; i < kEpiCols; ++i) av[i] = fabsf(val[i]);
+        const float mine = column_max<kEpiCols>(av, lane);
+        if (col_lane) ctl->colmax[group][quarter][lane] = mine;
         epi_bar();
         float bmax = 0.f;
         const int q0 = (quarter / (KC / 32)) * (KC / 32);
+        if (col_lane) {
 #pragma unroll
-        for (int q = 0; q < KC / 32; ++q) bmax = fmaxf(bmax, ctl->colmax[half][q0 + q][lane]);
+          for (int q = 0; q < KC / 32; ++q) bmax = fmaxf(bmax, ctl->colmax[group][q0 + q][lane]);
+        }
         const int E_mine = block_exp(bmax);
+        const float s_mine = pow2f(8 - E_mine), is_mine = pow2f(E_mine - 8);
         epi_bar();
         const size_t plane = static_cast<size_t>(v.M) * v.N;
         uint16_t* out = static_cast<uint16_t*>(v.out);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int E = __shfl_sync(0xffffffffu, E_mine, i);
-          slice_store<BF16>(out, plane, static_cast<size_t>(ncol0 + i) * v.M + m, val[i], E);
+        for (int i = 0; i < kEpiCols; ++i) {
+          const float s = __shfl_sync(0xffffffffu, s_mine, i);
+          const float is = __shfl_sync(0xffffffffu, is_mine, i);
+          slice_store<BF16>(out, plane, static_cast<size_t>(ncol0 + i) * v.M + m, val[i], s, is);
         }
-        if (quarter == q0)
+        if (quarter == q0 && col_lane)
           v.eout[static_cast<size_t>(ncol0 + lane) * (v.M / KC) + (m0 + 32 * quarter) / KC] =
               static_cast<int8_t>(E_mine);
       } else {
         CompDot c_rz, c_zq;
         if (m < S.nx) {
 #pragma unroll
-          for (int g8 = 0; g8 < 32; g8 += 8) {
+          for (int g8 = 0; g8 < kEpiCols; g8 += 8) {
             float rv[8], qv[8];
             uint8_t mk[8];
 #pragma unroll
@@ -584,21 +634,31 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     const int kblocks = S.nxp / KC;
     const size_t plane = static_cast<size_t>(S.nyp) * S.nxp;
     uint16_t* out = static_cast<uint16_t*>(S.tc_r);
-    for (int ly = warp; ly < kStTileY; ly += 8) {
-      const int y = y0 + ly;
-      if (y >= S.ny) break;
-      float v[KC / 32];
-      float amax = 0.f;
+    // every row of the warp loaded before any is sliced
+    constexpr int kRows = kStTileY / 8;
+    static_assert(kRows * 8 == kStTileY, "rows per warp");
+    float v[kRows][KC / 32];
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      const int y = y0 + warp + 8 * j;
 #pragma unroll
       for (int k = 0; k < KC / 32; ++k) {
         const int x = x0 + 32 * k + lane;
-        v[k] = x < S.nx ? S.r[y * S.nx + x] : 0.f;
-        amax = fmaxf(amax, fabsf(v[k]));
+        v[j][k] = (x < S.nx && y < S.ny) ? S.r[y * S.nx + x] : 0.f;
       }
+    }
+#pragma unroll
+    for (int j = 0; j < kRows; ++j) {
+      const int y = y0 + warp + 8 * j;
+      if (y >= S.ny) break;
+      float amax = 0.f;
+#pragma unroll
+      for (int k = 0; k < KC / 32; ++k) amax = fmaxf(amax, fabsf(v[j][k]));
       const int E = block_exp(warp_max(amax));
+      const float s = pow2f(8 - E), is = pow2f(E - 8);
 #pragma unroll
       for (int k = 0; k < KC / 32; ++k)
-        slice_store<BF16>(out, plane, static_cast<size_t>(y) * S.nxp + x0 + 32 * k + lane, v[k], E);
+        slice_store<BF16>(out, plane, static_cast<size_t>(y) * S.nxp + x0 + 32 * k + lane, v[j][k], s, is);
       if (lane == 0) S.tc_e[0][static_cast<size_t>(y) * kblocks + x0 / KC] = static_cast<int8_t>(E);
     }
   }
@@ -628,7 +688,16 @@ bool tc_supported() {
     cudaGetLastError();
     return false;
   }
-  return p.major == 10 && p.sharedMemPerBlockOptin >= static_cast<size_t>(SMEM_BYTES);
+  if (p.major != 10 || p.sharedMemPerBlockOptin < static_cast<size_t>(SMEM_BYTES)) return false;
+  // one CTA of kThreads threads at kMaxRegs registers each must fit an SM
+  int blocks = 0;
+  if (set_attr<true, 0>() != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_prec_tc<true, 0>, kThreads, SMEM_BYTES) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return blocks >= 1;
 }
 
 int tc_planes(int) { return NS; }

@@ -192,6 +192,9 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     const float* __restrict__ z = S.z;
     int x0, y0;
     tile_origin(S, it.tile, x0, y0);
+    // a tile whose halo lies inside the grid needs no boundary rule
+    const bool interior =
+        x0 >= 2 && y0 >= 2 && x0 + kStTileX + 2 <= S.nx && y0 + kStTileY + 2 <= S.ny;
     // halo of p = z + beta p_old: gather every index first so all loads are in flight together
     constexpr int kPer = (kHalo + kStThreads - 1) / kStThreads;
     int gi[kPer];
@@ -201,13 +204,32 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       const int i = threadIdx.x + j * kStThreads;
       gs[j] = 0.f;
       gi[j] = 0;
-      if (i < kHalo) gi[j] = halo_src(S, x0, y0, i, gs[j]);
+      if (i < kHalo) {
+        if (interior) {
+          const int ly = i / kHX, lx = i - ly * kHX;
+          gi[j] = (y0 - 2 + ly) * S.nx + (x0 - 2 + lx);
+          gs[j] = 1.f;
+        } else {
+          gi[j] = halo_src(S, x0, y0, i, gs[j]);
+        }
+      }
     }
     float zv[kPer], pv[kPer];
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
       zv[j] = gs[j] != 0.f ? __ldg(z + gi[j]) : 0.f;
       pv[j] = gs[j] != 0.f ? __ldg(pold + gi[j]) : 0.f;
+    }
+    // the mask of the thread's own nodes travels with the halo loads (one bit per node)
+    constexpr int kOwn = kStTileX * kStTileY / kStThreads;
+    static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn <= 32, "tile / block size");
+    uint32_t mk = 0;
+#pragma unroll
+    for (int j = 0; j < kOwn; ++j) {
+      const int k = threadIdx.x + j * kStThreads;
+      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx < S.nx && gy < S.ny && S.mask[gy * S.nx + gx]) mk |= 1u << j;
     }
 #pragma unroll
     for (int j = 0; j < kPer; ++j) {
@@ -216,14 +238,16 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     }
     __syncthreads();
     CompDot dot;
-    for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
+#pragma unroll 1
+    for (int j = 0; j < kOwn; ++j) {
+      const int k = threadIdx.x + j * kStThreads;
       const int ly = k / kStTileX, lx = k - ly * kStTileX;
       const int gx = x0 + lx, gy = y0 + ly;
       if (gx >= S.nx || gy >= S.ny) continue;
       const int g = gy * S.nx + gx;
       const float pv = sp[(ly + 2) * kHX + lx + 2];
       float qv = 0.f;
-      if (S.mask[g]) qv = stencil13<ANISO>(S, sp, ly, lx);
+      if ((mk >> j) & 1u) qv = stencil13<ANISO>(S, sp, ly, lx);
       pnew[g] = pv;
       S.q[g] = qv;
       dot.add(pv, qv);
