@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=400, help="serve: requests per step")
     ap.add_argument("--rate", type=float, default=500.0, help="serve: arrivals per second")
     ap.add_argument("--plain-sample", type=int, default=16, help="batch: grids timed on the plain path")
+    ap.add_argument("--instances", type=int, default=256,
+                    help="batch: number of grids (256 = the benchmark workload; fewer for profiling)")
     ap.add_argument("--prec", default=None, help="fp32 | mixed_fp16 | mixed_bf16")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -78,9 +80,10 @@ def make_workload(name, rank, args=None):
         return probs, {"workload": f"serve{args.requests}_poisson{args.rate:g}per_s_sides64-512",
                        "instances": len(probs), "arrivals": [r.arrival_s for r in reqs],
                        "prec": "mixed_bf16"}
-    probs = synth.batch_case(256, seed=synth.BASE_SEED + 1000 * rank)
+    count = args.instances if args is not None else 256
+    probs = synth.batch_case(count, seed=synth.BASE_SEED + 1000 * rank)
     nodes = sum(p.nx * p.ny for p in probs)
-    return probs, {"workload": "batch256_sides128-512_wobbly_extend_out", "instances": 256,
+    return probs, {"workload": f"batch{count}_sides128-512_wobbly_extend_out", "instances": count,
                    "nodes": nodes, "prec": "mixed_bf16"}
 
 
@@ -152,7 +155,7 @@ class ClockSampler:
 # our implementation
 # ----------------------------------------------------------------------------------------------
 def kernel_hash(kind, prec="fp32"):
-    if kind.startswith("prec"):
+    if kind.startswith("prec") or kind == "split":
         f = "kernels_gemm_simt.cu" if prec == "fp32" else "kernels_gemm_tc.cu"
     else:
         f = "kernels_grid.cu"
