@@ -9,8 +9,9 @@
 //  * every operand is cut into blocks of KC = 64 consecutive k; a block with largest magnitude
 //    below 2^E is stored as three integer slices, v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24),
 //    |c0| <= 256, |c1|, |c2| <= 128 (exact in FP16 and BF16), plus the exponent E (int8);
-//  * for each slice order d = i + j (products c_i c'_j, d <= 2: six MMAs per k-step) a separate
-//    TMEM accumulator sums one k-block: at most 3 * 64 products below 2^16, so every partial sum
+//  * for each slice order d = i + j (products c_i c'_j, d <= 2) a separate TMEM accumulator sums
+//    one k-block; the three B slices are stacked along N, so the six products of a k-step take
+//    three MMAs (N = 192, 128, 64): at most 3 * 64 products below 2^16, so every partial sum
 //    is an exact integer below 2^24 and so is the accumulation (128-wide blocks would also stay
 //    exact with |c0| <= 255, but the coarser exponents cost this operator many CG iterations);
 //  * the epilogue warps scale the three exact sums by 2^(E_A + E_B - 16 - 8d) and add them into
@@ -273,7 +274,6 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   volatile int* abort_flag = &ctl->abort_flag;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = *n_items;
-  constexpr uint32_t IDESC = idesc_f16(BF16, BM, BN);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -377,14 +377,14 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           for (int j = 0; j < BK / 16; ++j) {
 #pragma unroll
             for (int pa = 0; pa < NS; ++pa) {
-#pragma unroll
-              for (int pb = 0; pa + pb < NS; ++pb) {
-                const int d = pa + pb;
-                const uint64_t ad = sdesc(sa + pa * A_PLANE) + 2 * j;
-                const uint64_t bd = sdesc(sb + pb * B_PLANE) + 2 * j;
-                // the first product of each order in an accumulation block starts afresh
-                umma(dset + d * BN, ad, bd, IDESC, (half_kb > 0 || j > 0 || pa > 0) ? 1u : 0u);
-              }
+              // slice pa of A against the B slices 0 .. NS-1-pa stacked along N (adjacent in
+              // shared memory): one MMA adds A_pa B_pb to the accumulator of order pa + pb for
+              // every pb, since the order accumulators are adjacent in TMEM the same way
+              const uint64_t ad = sdesc(sa + pa * A_PLANE) + 2 * j;
+              const uint64_t bd = sdesc(sb) + 2 * j;
+              // the first MMA of an accumulation block (pa = 0) starts all three orders afresh
+              umma(dset + pa * BN, ad, bd, idesc_f16(BF16, BM, (NS - pa) * BN),
+                   (half_kb > 0 || j > 0 || pa > 0) ? 1u : 0u);
             }
           }
           umma_commit(&ctl->empty[stage]);
@@ -437,6 +437,12 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           asm volatile("prefetch.global.L2 [%0];" ::"l"(S.q + g1));
           asm volatile("prefetch.global.L2 [%0];" ::"l"(S.mask + g));
         }
+      }
+      // stage 1's eigenvalues, read now so their latency hides behind the k-blocks
+      float lamx_m = 0.f, lamy_mine = 0.f;
+      if (STAGE == 1) {
+        lamx_m = (m < S.nx) ? S.lamx[m] : 0.f;
+        lamy_mine = (col_lane && ncol0 + lane < S.ny) ? S.lamy[ncol0 + lane] : 0.f;
       }
       const int8_t* ea_row = S.tc_e[STAGE] + static_cast<size_t>(m) * kblocks;
       const int8_t* eb_col = S.tc_eb[STAGE] + static_cast<size_t>(ncol0 + (col_lane ? lane : 0)) * kblocks;
@@ -503,8 +509,6 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       for (int i = 0; i < kEpiCols; ++i) val[i] = __fadd_rn(hi[i], lo[i]);
       if (STAGE == 1) {
         // weight 1/(lam_y + lam_x)^2 (normalised); lam_y of the warp's columns via shuffles
-        const float lamx_m = (m < S.nx) ? S.lamx[m] : 0.f;
-        const float lamy_mine = (col_lane && ncol0 + lane < S.ny) ? S.lamy[ncol0 + lane] : 0.f;
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) {
           const int n = ncol0 + i;
@@ -545,12 +549,13 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       } else {
         CompDot c_rz, c_zq;
         if (m < S.nx) {
+          constexpr int kGrp = kEpiCols < 16 ? kEpiCols : 16;
 #pragma unroll
-          for (int g8 = 0; g8 < kEpiCols; g8 += 8) {
-            float rv[8], qv[8];
-            uint8_t mk[8];
+          for (int g8 = 0; g8 < kEpiCols; g8 += kGrp) {
+            float rv[kGrp], qv[kGrp];
+            uint8_t mk[kGrp];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {  // issue the group's loads together
+            for (int i = 0; i < kGrp; ++i) {  // issue the group's loads together
               const int n = ncol0 + g8 + i;
               const int g = (n < S.ny ? n : 0) * S.nx + m;
               rv[i] = S.r[g];
@@ -558,7 +563,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               mk[i] = n < S.ny ? S.mask[g] : 0;
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
+            for (int i = 0; i < kGrp; ++i) {
               const int n = ncol0 + g8 + i;
               if (n < S.ny) {
                 const float zv = mk[i] ? val[g8 + i] : 0.f;
