@@ -151,7 +151,7 @@ static bool is_device_ptr(const void* p) {
 }
 
 // ---- tensor-core operands --------------------------------------------------------------------
-constexpr int kExpBlock = 64;  // k per block exponent of the sliced operands (kernels_gemm_tc.cu KC)
+constexpr int kExpBlock = 128;  // k per block exponent of the sliced operands (kernels_gemm_tc.cu KC)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -195,16 +195,14 @@ static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint
 
 // Three integer slices of v for block exponent E (v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24)),
 // stored as FP16 or BF16 (integers of at most 9 bits are exact in both).
-static void slice_host(double v, int E, int split, uint16_t* out, size_t plane, size_t idx) {
-  const double c0 = std::nearbyint(std::ldexp(v, 8 - E));
-  const double r1 = v - std::ldexp(c0, E - 8);
-  const double c1 = std::nearbyint(std::ldexp(r1, 16 - E));
-  const double r2 = r1 - std::ldexp(c1, E - 16);
-  const double c2 = std::nearbyint(std::ldexp(r2, 24 - E));
-  const double c[3] = {c0, c1, c2};
-  for (int k = 0; k < 3; ++k)
-    out[k * plane + idx] = split == 0 ? __half_as_ushort(__double2half(c[k]))
-                                      : __bfloat16_as_ushort(__double2bfloat16(c[k]));
+static void slice_host(double v, int E, int split, int ns, uint16_t* out, size_t plane, size_t idx) {
+  double r = v;
+  for (int k = 0; k < ns; ++k) {
+    const double c = std::nearbyint(std::ldexp(r, 8 * (k + 1) - E));
+    r -= std::ldexp(c, E - 8 * (k + 1));
+    out[k * plane + idx] = split == 0 ? __half_as_ushort(__double2half(c))
+                                      : __bfloat16_as_ushort(__double2bfloat16(c));
+  }
 }
 
 // Block exponent of `count` values: max |v| < 2^E and max |v| 2^(8-E) < 255.5 (the leading
@@ -216,11 +214,11 @@ static int block_exp_host(const double* v, size_t stride, int count) {
   int e;
   std::frexp(m, &e);
   if (count > 64 && std::ldexp(m, 8 - e) >= 255.5) ++e;
-  return std::max(e, -100);
+  return std::max(e, -90);
 }
 
 // Q and Q^T of one axis as block-scaled slices (zero-padded to np x np) with their exponents:
-// [Q slices (3 planes)][Q^T slices (3 planes)][exponents of Q rows][exponents of Q^T rows].
+// [Q slices (NS planes)][Q^T slices (NS planes)][exponents of Q rows][exponents of Q^T rows].
 static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
   if (P->tc && P->tc_split == ctx->split) return EXT_OK;
   if (P->tc) {
@@ -249,7 +247,7 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
         const int E = block_exp_host(blk, 1, kExpBlock);
         eo[(size_t)row * nkb + kb] = (int8_t)E;
         for (int k = 0; k < kExpBlock; ++k)
-          slice_host(blk[k], E, ctx->split, out, plane, (size_t)row * np + kb * kExpBlock + k);
+          slice_host(blk[k], E, ctx->split, NS, out, plane, (size_t)row * np + kb * kExpBlock + k);
       }
   }
   const size_t bytes = 2 * h.size() + ex.size();
@@ -268,7 +266,8 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
 static const int8_t* plan_exps(const PlanDev* P, int t) {
   const size_t plane = (size_t)P->np * P->np;
   const size_t nkb = P->np / kExpBlock;
-  return (const int8_t*)((const char*)P->tc + 2 * 2 * 3 * plane) + t * (size_t)P->np * nkb;
+  return (const int8_t*)((const char*)P->tc + 2 * 2 * (size_t)tc_planes(P->tc_split) * plane) +
+         t * (size_t)P->np * nkb;
 }
 
 static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {

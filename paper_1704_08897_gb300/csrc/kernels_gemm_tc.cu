@@ -6,22 +6,26 @@
 // even float hi/lo operand splits lose too much in the tensor core's truncating FP32
 // accumulation.  The products are therefore made exact:
 //
-//  * every operand is cut into blocks of KC = 64 consecutive k; a block with largest magnitude
-//    below 2^E is stored as three integer slices, v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24),
-//    |c0| <= 256, |c1|, |c2| <= 128 (exact in FP16 and BF16), plus the exponent E (int8);
-//  * for each slice order d = i + j (products c_i c'_j, d <= 2) a separate TMEM accumulator sums
-//    one k-block; the three B slices are stacked along N, so the six products of a k-step take
-//    three MMAs (N = 192, 128, 64): at most 3 * 64 products below 2^16, so every partial sum
-//    is an exact integer below 2^24 and so is the accumulation (128-wide blocks would also stay
-//    exact with |c0| <= 255, but the coarser exponents cost this operator many CG iterations);
-//  * the epilogue warps scale the three exact sums by 2^(E_A + E_B - 16 - 8d) and add them into
+//  * every operand is cut into blocks of KC = 128 consecutive k; a block with largest magnitude
+//    below 2^E (and 2^(8-E) times it below 255.5) is stored as four integer slices,
+//    v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24) + c3 2^(E-32), |c0| <= 255, |c1..c3| <= 128
+//    (exact in FP16 and BF16), plus the exponent E (int8);
+//  * for each slice order d = i + j <= 3 (products c_i c'_j; higher orders are below 2^-32 of
+//    the block and dropped) a separate TMEM accumulator sums one k-block.  The B slices are
+//    stacked along N, so the ten products of a k-step take four MMAs (N = 256, 192, 128, 64).
+//    Per k, the products of one order add up to less than 2^16.6, so over 128 k every partial
+//    sum is an exact integer below 2^24 and so is the accumulation;
+//  * the epilogue warps scale the four exact sums by 2^(E_A + E_B - 16 - 8d) and add them into
 //    a compensated (hi, lo) register pair, k-block after k-block.
-// The result carries about 24 bits relative to each 64-block's largest value, with no error
-// growth along K.  The writer of the next stage's operand computes its block exponents with a
-// two-warp maximum and stores the slices transposed (Out[n][m], coalesced along m).
+// The operands carry 32 bits relative to each 128-block's largest value and the products add no
+// error along K; only the stage output is rounded (to FP32, then sliced).  Three slices on
+// 64-blocks (24 bits) cost this operator 30-80% more CG iterations than exact transforms; four on
+// 128-blocks come within 5-10% of them.  The writer of the next stage's operand computes its
+// block exponents with a four-warp maximum and stores the slices transposed (Out[n][m],
+// coalesced along m).
 //
 // Kernel structure (one CTA per SM, persistent over the (slot, tile) work list):
-//   warp 0      : TMA producer: 128B-swizzled K-major tiles of the three slices of A and B
+//   warp 0      : TMA producer: 128B-swizzled K-major tiles of the four slices of A and B
 //   warp 1      : TMEM allocation; lane 0 issues the MMAs and the tcgen05.commit arrivals
 //   warps 2..17 : four per TMEM lane quarter (32 rows), each owning 16 of the tile's 64 columns:
 //                 exact k-block sums -> compensated registers -> the stage's epilogue
@@ -39,23 +43,25 @@ namespace bx {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 64;  // BK: one 128-byte swizzle atom per pipeline stage
-constexpr int KC = 64;                      // k per exponent / exact accumulation block
+constexpr int KC = 128;                     // k per exponent / exact accumulation block
 constexpr int KPC = KC / BK;                // pipeline stages per accumulation block
-constexpr int NS = 3;                            // slices per operand
+constexpr int NS = 4;                            // slices per operand
 constexpr int kEpiWarps = 16;
 constexpr int kColGroups = kEpiWarps / 4;        // epilogue warps per TMEM lane quarter
 constexpr int kEpiCols = BN / kColGroups;        // tile columns per epilogue warp
 static_assert(kEpiCols % 16 == 0 && kEpiCols <= 32, "epilogue column split");
-constexpr int kLdCols = kEpiWarps == 16 ? 8 : 16;  // TMEM columns per load (register budget)
+static_assert(KC % BK == 0 && KC <= BM && BM % KC == 0, "exponent blocks within a tile");
+constexpr int kLdCols = kEpiWarps == 16 ? 4 : 8;  // TMEM columns per load (register budget)
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 // One CTA per SM.  Each of the SM's four schedulers owns a quarter of the register file and
 // holds up to ceil(warps / 4) of the CTA's warps.
 constexpr int kMaxRegs = (16384 / (32 * ((kThreads / 32 + 3) / 4))) & ~7;
 constexpr long long kWaitCycles = 4000000000LL;  // about two seconds at 2 GHz
 constexpr int kChunks = 2;                       // TMEM ring of k-block accumulator sets
-constexpr int kSetCols = 3 * BN;                 // one accumulator per slice order
+constexpr int kSetCols = NS * BN;                // one accumulator per slice order
 constexpr int kTmemCols = 512;                   // power of two >= kChunks * kSetCols
-constexpr int STAGES = 3;
+static_assert(kChunks * kSetCols <= kTmemCols, "TMEM columns");
+constexpr int STAGES = 2;
 constexpr int A_PLANE = BM * BK * 2;
 constexpr int B_PLANE = BN * BK * 2;
 constexpr int STAGE_BYTES = NS * (A_PLANE + B_PLANE);
@@ -163,15 +169,21 @@ __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::
         "=r"(v[15])
       : "r"(taddr));
 }
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+[[maybe_unused]] __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
   asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
                : "r"(taddr));
 }
 template <int N>
 __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
   if constexpr (N == 16) tmem_ld16(taddr, v);
-  else tmem_ld8(taddr, v);
+  else if constexpr (N == 8) tmem_ld8(taddr, v);
+  else tmem_ld4(taddr, v);
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
@@ -187,27 +199,23 @@ __device__ __forceinline__ int block_exp(float amax) {
   int e;
   frexpf(amax, &e);
   if (KC > 64 && amax * pow2f(8 - e) >= 255.5f) ++e;
-  return max(e, -100);
+  return max(e, -90);  // keeps 2^(32-E) and 2^(E-16-8d) normal
 }
 
-// Three integer slices of v for block exponent E, given s = 2^(8-E) and is = 2^(E-8) (both normal
-// for the exponents block_exp returns): every product below is exact, so each residual is v minus
-// the slices so far, rounded once; the last slice is rounded to an integer.
+// The NS integer slices of v for block exponent E, given s = 2^(8-E) and is = 2^(E-8) (all the
+// powers of two below are normal for the exponents block_exp returns): every product is exact, so
+// each residual is v minus the slices so far, rounded once; the last slice is rounded to an
+// integer.
 template <bool BF16>
 __device__ __forceinline__ void slice_store(uint16_t* base, size_t plane, size_t idx, float v, float s, float is) {
-  const float c0 = rintf(v * s);
-  const float r1 = __fmaf_rn(-c0, is, v);
-  const float c1 = rintf(r1 * (s * 256.f));
-  const float r2 = __fmaf_rn(-c1, is * 0.00390625f, r1);
-  const float c2 = rintf(r2 * (s * 65536.f));
-  if (BF16) {
-    base[idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c0));
-    base[plane + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c1));
-    base[2 * plane + idx] = __bfloat16_as_ushort(__float2bfloat16_rn(c2));
-  } else {
-    base[idx] = __half_as_ushort(__float2half_rn(c0));
-    base[plane + idx] = __half_as_ushort(__float2half_rn(c1));
-    base[2 * plane + idx] = __half_as_ushort(__float2half_rn(c2));
+  float r = v, up = s, down = is;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    const float c = rintf(r * up);
+    if (k + 1 < NS) r = __fmaf_rn(-c, down, r);
+    up *= 256.f;
+    down *= 0.00390625f;
+    base[k * plane + idx] = BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(c)) : __half_as_ushort(__float2half_rn(c));
   }
 }
 
@@ -478,10 +486,11 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + cb * kSetCols + group * kEpiCols;
 #pragma unroll
         for (int hc = 0; hc < kEpiCols / kLdCols; ++hc) {
-          uint32_t s0[kLdCols], s1[kLdCols], s2[kLdCols];
+          uint32_t s0[kLdCols], s1[kLdCols], s2[kLdCols], s3[kLdCols];
           tmem_ld<kLdCols>(base + hc * kLdCols, s0);
           tmem_ld<kLdCols>(base + BN + hc * kLdCols, s1);
           tmem_ld<kLdCols>(base + 2 * BN + hc * kLdCols, s2);
+          tmem_ld<kLdCols>(base + 3 * BN + hc * kLdCols, s3);
           tmem_wait_ld();
           if (hc == kEpiCols / kLdCols - 1) {
             tc_fence_before();
@@ -492,8 +501,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           for (int i = 0; i < kLdCols; ++i) {
             const int c = hc * kLdCols + i;
             const float scl = sa * __shfl_sync(0xffffffffu, sb_mine, c);
-            // orders 1 and 2 combined first: their rounding is 2^-24 of a term 2^-8 below hi
-            const float u = __fmaf_rn(__uint_as_float(s2[i]), 0.00390625f, __uint_as_float(s1[i]));
+            // orders 1..3 combined first: their roundings are 2^-24 of terms 2^-8 below hi
+            const float w = __fmaf_rn(__uint_as_float(s3[i]), 0.00390625f, __uint_as_float(s2[i]));
+            const float u = __fmaf_rn(w, 0.00390625f, __uint_as_float(s1[i]));
             const float t0 = __uint_as_float(s0[i]) * scl;
             const float t1 = u * (scl * 0.00390625f);
             float er;
@@ -519,7 +529,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       }
       if (STAGE <= 2) {
         // block exponents of the next operand: rows n, k-blocks of KC consecutive m (lane quarters
-        // 32q .. 32q+31 of this tile; KC/32 quarters per block)
+        // 32q .. 32q+31 of this tile; KC/32 quarters per block, KC <= BM)
         float av[kEpiCols];
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) av[i] = fabsf(val[i]);
