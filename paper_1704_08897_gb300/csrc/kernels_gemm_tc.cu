@@ -77,7 +77,7 @@ struct Ctl {
   int abort_flag;
   int last;
   int pad;
-  double red[2 * kEpiWarps];
+  float red[kEpiWarps][4];  // stage 3: per-warp compensated r.z and z.q
   float colmax[kColGroups][4][kEpiCols];  // [column group][lane quarter][column]
 };
 static_assert(sizeof(Ctl) <= 2048, "control block too large");
@@ -544,7 +544,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         }
         const int E_mine = block_exp(bmax);
         const float s_mine = pow2f(8 - E_mine), is_mine = pow2f(E_mine - 8);
-        epi_bar();
+        // no second barrier before colmax is rewritten: that happens after the next tile's first
+        // k-block, whose failure vote every epilogue warp joins only after these reads
         const size_t plane = static_cast<size_t>(v.M) * v.N;
         uint16_t* out = static_cast<uint16_t*>(v.out);
 #pragma unroll
@@ -595,24 +596,39 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           two_sum(c_zq.s, b1, c_zq.s, e);
           c_zq.c = __fadd_rn(c_zq.c, __fadd_rn(b2, e));
         }
-        const double d_rz = c_rz.value();
-        const double d_zq = c_zq.value();
         if (lane == 0) {
-          ctl->red[2 * ew] = d_rz;
-          ctl->red[2 * ew + 1] = d_zq;
+          ctl->red[ew][0] = c_rz.s;
+          ctl->red[ew][1] = c_rz.c;
+          ctl->red[ew][2] = c_zq.s;
+          ctl->red[ew][3] = c_zq.c;
         }
         epi_bar();
-        if (ew == 0 && lane == 0) {
-          double a = 0.0, b = 0.0;
-          for (int k = 0; k < kEpiWarps; ++k) {
-            a += ctl->red[2 * k];
-            b += ctl->red[2 * k + 1];
+        if (ew == 0) {
+          // the warps' compensated pairs, summed the same way across lanes 0 .. kEpiWarps-1
+          CompDot t_rz, t_zq;
+          if (lane < kEpiWarps) {
+            t_rz.s = ctl->red[lane][0];
+            t_rz.c = ctl->red[lane][1];
+            t_zq.s = ctl->red[lane][2];
+            t_zq.c = ctl->red[lane][3];
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            float e;
+            const float a1 = __shfl_xor_sync(0xffffffffu, t_rz.s, o), a2 = __shfl_xor_sync(0xffffffffu, t_rz.c, o);
+            two_sum(t_rz.s, a1, t_rz.s, e);
+            t_rz.c = __fadd_rn(t_rz.c, __fadd_rn(a2, e));
+            const float b1 = __shfl_xor_sync(0xffffffffu, t_zq.s, o), b2 = __shfl_xor_sync(0xffffffffu, t_zq.c, o);
+            two_sum(t_zq.s, b1, t_zq.s, e);
+            t_zq.c = __fadd_rn(t_zq.c, __fadd_rn(b2, e));
           }
           // tile partials; k_prec_finish forms rho and beta from them
-          S.part[it.tile * 4 + 2] = a;
-          S.part[it.tile * 4 + 3] = b;
+          if (lane == 0) {
+            S.part[it.tile * 4 + 2] = t_rz.value();
+            S.part[it.tile * 4 + 3] = t_zq.value();
+          }
         }
-        epi_bar();
+        // ctl->red is rewritten only after the next tile's first k-block (see stages 0..2)
       }
     }
   }
