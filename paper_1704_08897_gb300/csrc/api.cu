@@ -789,6 +789,7 @@ static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const
   int rc = ensure_graph(ctx, W);
   if (rc) return rc;
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(cfg_of(ctx, W, 0), W->d_phis, W->d_fs, W->d_dirs); });
+  timed(ctx, EXT_KERNEL_SETUP, [&] { launch_rhs_scale(cfg_of(ctx, W, 0)); });
   launch_prec(ctx, W, 1);
   BX_CUDA(cudaGetLastError());
   int max_blocks = 0;
@@ -1050,6 +1051,7 @@ static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi,
   W->h_sc[0].pscale = 1.f;
   BX_CUDA(cudaMemcpyAsync(W->d_sc, W->h_sc, sizeof(SlotScalars), cudaMemcpyHostToDevice, s));
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(cfg_of(ctx, W, 0), W->d_phis, W->d_fs, W->d_dirs); });
+  timed(ctx, EXT_KERNEL_SETUP, [&] { launch_rhs_scale(cfg_of(ctx, W, 0)); });
   BX_CUDA(cudaGetLastError());
   *Wout = W;
   return EXT_OK;
@@ -1370,6 +1372,7 @@ static int serve_setup_slots(ext_ctx* ctx, const std::vector<int>& admitted) {
   c.grid = std::max(1, std::min((int)fresh.size(), ctx->sm_count * 8));
   c.stream = s;
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(c, W->d_phis, W->d_fs, W->d_dirs); }, s);
+  timed(ctx, EXT_KERNEL_SETUP, [&] { launch_rhs_scale(c); }, s);
   launch_prec(ctx, W, 1);
   BX_CUDA(cudaGetLastError());
   BX_CUDA(cudaStreamSynchronize(s));  // `fresh` is a pageable source

@@ -46,6 +46,7 @@ struct __align__(16) SlotScalars {
   int flexible;
   unsigned cnt[6];  // completion counters of the last-item reductions, one per kernel kind
   int n_known;      // known nodes, counted by the set-up kernel
+  int bexp;         // the iteration solves A x' = 2^bexp b; the answer is x = 2^-bexp x'
 };
 
 // Static description of one slot (device copy).  Padded transform dims are multiples of kPad.

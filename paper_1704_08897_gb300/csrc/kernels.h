@@ -21,6 +21,7 @@ void set_weights(SlotDesc& d, double hx, double hy);
 // grid kernels (kernels_grid.cu)
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
                   const int* dirs);
+void launch_rhs_scale(const LaunchCfg& c);
 void launch_stencil(const LaunchCfg& c, bool aniso);
 // per-slot p.q -> alpha (after the stencil)
 void launch_pq_finish(const LaunchCfg& c);

@@ -139,10 +139,23 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       if (threadIdx.x == 0) {
         const double sb = sums[0], sk = sums[1], sn = sums[2];
         SlotScalars* sc = S.sc;
-        sc->bb = sb;
-        sc->rr = sb;
-        sc->rr_true = sb;
-        sc->rr_ref = sb;
+        // The extension is linear in f: the iteration runs on 2^e b with e chosen so that the
+        // root mean square of 2^e b over the unknowns is near 1, which keeps the FP32 vectors
+        // and their pairwise products inside FP32's range for any magnitude of f.  A power of
+        // two changes no rounding; k_output scales the answer back.
+        int e = 0;
+        const double n_unk = (double)S.nx * (double)S.ny - sk;
+        if (sb > 0.0 && isfinite(sb) && n_unk > 0.0) {
+          int k;
+          frexp(sb / n_unk, &k);
+          e = max(-1000, min(1000, -(k / 2)));
+        }
+        sc->bexp = e;
+        const double sbs = ldexp(sb, 2 * e);
+        sc->bb = sbs;
+        sc->rr = sbs;
+        sc->rr_true = sbs;
+        sc->rr_ref = sbs;
         sc->rho = 0.0;
         sc->beta = 0.0;
         sc->alpha = 0.0;
@@ -165,6 +178,27 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       }
     }
     __syncthreads();
+  }
+}
+
+// Set-up, second pass: r = 2^e b in FP32, once the slot's scale exponent e is known.
+__global__ void __launch_bounds__(kStThreads)
+k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+            const int* __restrict__ n_items) {
+  const int total = *n_items;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    const int e = S.sc->bexp;
+    int x0, y0;
+    tile_origin(S, it.tile, x0, y0);
+    for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
+      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      const int gx = x0 + lx, gy = y0 + ly;
+      if (gx >= S.nx || gy >= S.ny) continue;
+      const int g = gy * S.nx + gx;
+      S.r[g] = (float)ldexp(S.b[g], e);
+    }
   }
 }
 
@@ -393,6 +427,7 @@ k_true_residual(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
     if (!sc->fold) continue;
+    const int be = sc->bexp;
     int x0, y0;
     tile_origin(S, it.tile, x0, y0);
     for (int i = threadIdx.x; i < kHalo; i += blockDim.x) {
@@ -408,7 +443,7 @@ k_true_residual(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__
       if (gx >= S.nx || gy >= S.ny) continue;
       const int g = gy * S.nx + gx;
       double rv = 0.0;
-      if (S.mask[g]) rv = S.b[g] - stencil13_f64(S, sx, ly, lx);
+      if (S.mask[g]) rv = ldexp(S.b[g], be) - stencil13_f64(S, sx, ly, lx);
       S.r[g] = (float)rv;
       rr += rv * rv;
     }
@@ -490,8 +525,9 @@ k_output(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
     const int n = S.nx * S.ny;
     const int e0 = it.tile * kVecChunk;
     const int e1 = min(n, e0 + kVecChunk);
+    const int be = S.sc->bexp;  // x = 2^-bexp x'
     for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x)
-      out[e] = S.mask[e] ? (float)((double)S.xhi[e] + (double)S.xlo[e]) : f[e];
+      out[e] = S.mask[e] ? (float)ldexp((double)S.xhi[e] + (double)S.xlo[e], -be) : f[e];
   }
 }
 
@@ -500,8 +536,9 @@ __global__ void __launch_bounds__(kVecThreads)
 k_output64(const SlotDesc* __restrict__ slots, const float* __restrict__ f, double* __restrict__ out) {
   const SlotDesc& S = slots[0];
   const int n = S.nx * S.ny;
+  const int be = S.sc->bexp;  // x = 2^-bexp x'
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x)
-    out[e] = S.mask[e] ? (double)S.xhi[e] + (double)S.xlo[e] : (double)f[e];
+    out[e] = S.mask[e] ? ldexp((double)S.xhi[e] + (double)S.xlo[e], -be) : (double)f[e];
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -547,6 +584,9 @@ k_apply(const SlotDesc* __restrict__ slots, const float* __restrict__ p, float* 
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
                   const int* dirs) {
   k_setup<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, phis, fs, dirs);
+}
+void launch_rhs_scale(const LaunchCfg& c) {
+  k_rhs_scale<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
 }
 void launch_stencil(const LaunchCfg& c, bool aniso) {
   if (aniso) k_stencil<true><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);

@@ -401,3 +401,33 @@ def test_fp16_and_bf16_slices_give_identical_results(ext):
         finally:
             ext.ext_destroy(c)
     assert torch.equal(outs[0], outs[1])
+
+
+# ----------------------------------------------------------------------------------------------
+# scale: the extension is linear in f.  The iteration runs on 2^e b with e chosen from ||b||, so a
+# power-of-two scale of f gives the same iterates and an exactly scaled answer, and fields far
+# from unit size (whose FP32 pairwise products would overflow or underflow) still converge.
+# ----------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16"])
+@pytest.mark.parametrize("s", [2.0 ** -70, 2.0 ** 70, 1e-25, 1e25])
+def test_solution_scales_with_the_field(ext, prec, s):
+    p = synth.wobbly(192, 3)
+    c = ext.ext_create(ext.options(prec, rtol=1e-8))
+    try:
+        outs = []
+        for k in (1.0, s):
+            f = (p.f.astype(np.float64) * k).astype(np.float32)
+            assert np.all(np.isfinite(f)) and np.all(f[p.f != 0] != 0)
+            out = torch.empty(p.phi.shape, device="cuda")
+            r = ext.ext_solve(c, ext.problem_of(p), dev(p.phi), dev(f), out)
+            assert r["status"] == 0 and r["relres_true"] <= 1.05e-8, (k, r)
+            outs.append(out.cpu().numpy())
+        if np.log2(s) == np.round(np.log2(s)):
+            # exact power of two: the same iterates, the answer scaled bit for bit
+            assert np.array_equal(outs[1], (outs[0].astype(np.float64) * s).astype(np.float32))
+        else:
+            a = outs[0].astype(np.float64)
+            b = outs[1].astype(np.float64) / s
+            assert np.abs(b - a).max() <= 1e-4 * np.abs(a).max()
+    finally:
+        ext.ext_destroy(c)
