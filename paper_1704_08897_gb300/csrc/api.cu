@@ -150,6 +150,17 @@ static bool is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// Transform tiles in decreasing order of their k extent (a tile's cost is proportional to it), so
+// that the persistent CTAs of a launch end together; tiles of one slot keep their order.  Any
+// order gives the same results: tile partial sums are stored per tile and reduced in tile order.
+static void longest_first(std::vector<WorkItem>& gm, const std::vector<SlotHost>& slots) {
+  std::stable_sort(gm.begin(), gm.end(), [&](const WorkItem& a, const WorkItem& b) {
+    const SlotDesc& da = slots[a.slot].d;
+    const SlotDesc& db = slots[b.slot].d;
+    return std::max(da.nxp, da.nyp) > std::max(db.nxp, db.nyp);
+  });
+}
+
 // ---- tensor-core operands --------------------------------------------------------------------
 constexpr int kExpBlock = 128;  // k per block exponent of the sliced operands (kernels_gemm_tc.cu KC)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -528,6 +539,7 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
     for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
   }
+  longest_first(gm, W->slots);
   W->n_st = (int)st.size();
   W->n_vec = (int)vec.size();
   W->n_gm = (int)gm.size();
@@ -1240,6 +1252,7 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
     for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
   }
+  longest_first(gm, W->slots);
   const int need = (int)std::max(st.size(), std::max(vec.size(), gm.size()));
   if (need > S->cap_items) {
     int cap = S->cap_items;
