@@ -242,6 +242,8 @@ def run_ours(args, rank, world):
         step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     launches = ext.ext_launch_count(ctx) - launches0
+    # answers of the last timed step, for the error against the oracle (later passes reuse outs)
+    answers = [o.cpu().numpy() for o in outs[:32]]
     clk = clocks.stop()
     total_ms = sum(step_ms)
     if world > 1:
@@ -376,7 +378,7 @@ def run_ours(args, rank, world):
            "plain_fp32_single_solve": plain, "serving": serving,
            "e2e": e2e, "roofline": roofline, "kernels": kernels,
            "gpu_launches": launches, "clocks": clk}
-    return out, probs
+    return out, probs, answers
 
 
 def oracle_solve(p):
@@ -388,11 +390,12 @@ def oracle_solve(p):
 
 
 def cpu_baseline(args, probs, budget_s=30.0):
-    """The oracle, as it stands, on a bounded sample of the workload (whole problems only)."""
+    """The oracle, as it stands, on a bounded sample of the workload (whole problems only).
+    Returns the timing record and the oracle's answers."""
     t0 = time.perf_counter()
-    done = 0
+    done, refs = 0, []
     for p in probs:
-        oracle_solve(p)
+        refs.append(oracle_solve(p)[0])
         done += 1
         if time.perf_counter() - t0 > budget_s:
             break
@@ -400,7 +403,23 @@ def cpu_baseline(args, probs, budget_s=30.0):
     return {"value": round(done / el, 5), "unit": "solves/s", "cores": 1, "kind": "oracle",
             "sample": f"{done} of {len(probs)} problem(s) of the workload solved completely by the "
                       f"FP64 oracle (sparse assembly + SuperLU), {el:.1f} s",
-            "host_cores_available": os.cpu_count()}
+            "host_cores_available": os.cpu_count()}, refs
+
+
+def error_vs_oracle(probs, answers, refs, prec):
+    """Max-norm relative error (max over unknowns of |x - x*| / max |out*|) of the GPU answers
+    of the timed run against the oracle's direct solves, over the problems the oracle solved."""
+    import numpy as np
+
+    from oracle import biharmonic as ob
+    errs = []
+    for p, a, r in zip(probs, answers, refs):
+        known = ob.known_mask(p.phi.astype(np.float64), p.direction)
+        errs.append(ob.max_rel_error(a, r, known))
+    bound = 1e-6 if prec == "fp32" else 1e-5
+    return {"max_rel": float(max(errs)), "median_rel": float(np.median(errs)),
+            "problems": len(errs), "bound": bound, "within": bool(max(errs) <= bound),
+            "at": "rel-res 1e-8, answers of the last timed step"}
 
 
 def run_reference(args, rank, world):
@@ -447,10 +466,11 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    out, probs = run_ours(args, rank, world)
+    out, probs, answers = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline(args, probs)
+            out["cpu_baseline"], refs = cpu_baseline(args, probs)
+            out["error_vs_oracle"] = error_vs_oracle(probs, answers, refs, out["config"]["prec"])
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist

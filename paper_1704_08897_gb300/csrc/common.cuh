@@ -196,6 +196,29 @@ struct CompSum {
   __device__ __forceinline__ float result() const { return __fadd_rn(s, c); }
 };
 
+// Packed FP32x2 arithmetic (two independent lanes, each rounded exactly as its scalar
+// counterpart): a - b is fma(b, -1, a), one rounding.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 mul2(float w, float2 a) { return __fmul2_rn(make_float2(w, w), a); }
+__device__ __forceinline__ void two_sum2(float2 a, float2 b, float2& s, float2& e) {
+  s = add2(a, b);
+  const float2 bb = sub2(s, a);
+  e = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// CompSum on two lanes at once (the same operations, in the same order, per lane).
+struct CompSum2 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 x) {
+    float2 e;
+    two_sum2(s, x, s, e);
+    c = add2(c, e);
+  }
+  __device__ __forceinline__ float2 result() const { return add2(s, c); }
+};
+
 // Compensated FP32 dot-product accumulator (TwoProd + TwoSum per term).  GB300 runs FP64 at a
 // small fraction of its FP32 rate, so per-element FP64 arithmetic would dominate the
 // bandwidth-bound kernels; a thread's terms are summed here and only the per-thread totals are

@@ -63,6 +63,27 @@ __device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, in
   return acc.result();
 }
 
+// The isotropic 13-point stencil at two adjacent nodes (x, x+1) of a smem tile; c points at
+// node x, an even index.  Eleven aligned 8-byte loads cover both neighbourhoods, and each lane
+// runs the scalar stencil13's operations in the same order (bit-identical results).
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 stencil13_pair(const float* c) {
+  const float2 Cm = ld2(c - 2), C = ld2(c), Cp = ld2(c + 2);                     // row y
+  const float2 Nm = ld2(c - kHX - 2), N = ld2(c - kHX), Np = ld2(c - kHX + 2);   // row y-1
+  const float2 Sm = ld2(c + kHX - 2), Sv = ld2(c + kHX), Sp = ld2(c + kHX + 2);  // row y+1
+  const float2 NN = ld2(c - 2 * kHX), SS = ld2(c + 2 * kHX);                     // rows y-2, y+2
+  const float2 E0 = make_float2(Cm.y, C.x), E1 = make_float2(C.y, Cp.x);
+  const float2 D0 = make_float2(Nm.y, N.x), D1 = make_float2(N.y, Np.x);
+  const float2 D2 = make_float2(Sm.y, Sv.x), D3 = make_float2(Sv.y, Sp.x);
+  CompSum2 acc;
+  acc.add(mul2(16.f, C));
+  acc.add(mul2(4.f, C));
+  acc.add(mul2(-8.f, E0)); acc.add(mul2(-8.f, E1)); acc.add(mul2(-8.f, N)); acc.add(mul2(-8.f, Sv));
+  acc.add(mul2(2.f, D0)); acc.add(mul2(2.f, D1)); acc.add(mul2(2.f, D2)); acc.add(mul2(2.f, D3));
+  acc.add(Cm); acc.add(Cp); acc.add(NN); acc.add(SS);
+  return acc.result();
+}
+
 __device__ __forceinline__ double stencil13_f64(const SlotDesc& S, const double* t, int ly, int lx) {
   const double* c = t + (ly + 2) * kHX + (lx + 2);
   return S.dwc * c[0] + S.dwex * (c[-1] + c[1]) + S.dwey * (c[-kHX] + c[kHX]) +
@@ -211,7 +232,7 @@ template <bool ANISO>
 __global__ void __launch_bounds__(kStThreads)
 k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items) {
-  __shared__ float sp[kHalo];
+  __shared__ __align__(16) float sp[kHalo];
   __shared__ double red[64];
   const int total = *n_items;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
@@ -254,14 +275,24 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       zv[j] = gs[j] != 0.f ? __ldg(z + gi[j]) : 0.f;
       pv[j] = gs[j] != 0.f ? __ldg(pold + gi[j]) : 0.f;
     }
-    // the mask of the thread's own nodes travels with the halo loads (one bit per node)
+    // the mask of the thread's own nodes travels with the halo loads (one bit per node); the
+    // isotropic path owns node pairs (x, x+1), the anisotropic one single nodes
     constexpr int kOwn = kStTileX * kStTileY / kStThreads;
-    static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn <= 32, "tile / block size");
+    static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn <= 32 && kOwn % 2 == 0,
+                  "tile / block size");
     uint32_t mk = 0;
 #pragma unroll
     for (int j = 0; j < kOwn; ++j) {
-      const int k = threadIdx.x + j * kStThreads;
-      const int ly = k / kStTileX, lx = k - ly * kStTileX;
+      int ly, lx;
+      if (!ANISO) {
+        const int k = threadIdx.x + (j / 2) * kStThreads;  // pair index
+        ly = k / (kStTileX / 2);
+        lx = 2 * (k - ly * (kStTileX / 2)) + (j & 1);
+      } else {
+        const int k = threadIdx.x + j * kStThreads;
+        ly = k / kStTileX;
+        lx = k - ly * kStTileX;
+      }
       const int gx = x0 + lx, gy = y0 + ly;
       if (gx < S.nx && gy < S.ny && S.mask[gy * S.nx + gx]) mk |= 1u << j;
     }
@@ -272,19 +303,43 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     }
     __syncthreads();
     CompDot dot;
+    if (!ANISO) {
 #pragma unroll 1
-    for (int j = 0; j < kOwn; ++j) {
-      const int k = threadIdx.x + j * kStThreads;
-      const int ly = k / kStTileX, lx = k - ly * kStTileX;
-      const int gx = x0 + lx, gy = y0 + ly;
-      if (gx >= S.nx || gy >= S.ny) continue;
-      const int g = gy * S.nx + gx;
-      const float pv = sp[(ly + 2) * kHX + lx + 2];
-      float qv = 0.f;
-      if ((mk >> j) & 1u) qv = stencil13<ANISO>(S, sp, ly, lx);
-      pnew[g] = pv;
-      S.q[g] = qv;
-      dot.add(pv, qv);
+      for (int j = 0; j < kOwn / 2; ++j) {
+        const int k = threadIdx.x + j * kStThreads;
+        const int ly = k / (kStTileX / 2), lx = 2 * (k - ly * (kStTileX / 2));
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= S.nx || gy >= S.ny) continue;
+        const int g = gy * S.nx + gx;
+        const float* c = sp + (ly + 2) * kHX + lx + 2;
+        const float2 pv = ld2(c);
+        const float2 q2 = ((mk >> (2 * j)) & 3u) ? stencil13_pair(c) : make_float2(0.f, 0.f);
+        const float q0 = ((mk >> (2 * j)) & 1u) ? q2.x : 0.f;
+        const float q1 = ((mk >> (2 * j + 1)) & 1u) ? q2.y : 0.f;
+        pnew[g] = pv.x;
+        S.q[g] = q0;
+        dot.add(pv.x, q0);
+        if (gx + 1 < S.nx) {
+          pnew[g + 1] = pv.y;
+          S.q[g + 1] = q1;
+          dot.add(pv.y, q1);
+        }
+      }
+    } else {
+#pragma unroll 1
+      for (int j = 0; j < kOwn; ++j) {
+        const int k = threadIdx.x + j * kStThreads;
+        const int ly = k / kStTileX, lx = k - ly * kStTileX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= S.nx || gy >= S.ny) continue;
+        const int g = gy * S.nx + gx;
+        const float pv = sp[(ly + 2) * kHX + lx + 2];
+        float qv = 0.f;
+        if ((mk >> j) & 1u) qv = stencil13<ANISO>(S, sp, ly, lx);
+        pnew[g] = pv;
+        S.q[g] = qv;
+        dot.add(pv, qv);
+      }
     }
     const double pq = block_sum_comp<kStThreads>(dot, red);
     if (threadIdx.x == 0) S.part[it.tile * 4 + 1] = pq;  // reduced by k_pq_finish
