@@ -454,11 +454,12 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       }
       const int8_t* ea_row = S.tc_e[STAGE] + static_cast<size_t>(m) * kblocks;
       const int8_t* eb_col = S.tc_eb[STAGE] + static_cast<size_t>(ncol0 + (col_lane ? lane : 0)) * kblocks;
-      float hi[kEpiCols], lo[kEpiCols];
+      // compensated (hi, lo) pairs of the warp's columns, two columns per packed register pair
+      float2 hi[kEpiCols / 2], lo[kEpiCols / 2];
 #pragma unroll
-      for (int i = 0; i < kEpiCols; ++i) {
-        hi[i] = 0.f;
-        lo[i] = 0.f;
+      for (int i = 0; i < kEpiCols / 2; ++i) {
+        hi[i] = make_float2(0.f, 0.f);
+        lo[i] = make_float2(0.f, 0.f);
       }
       bool fail_all = false;
       for (int kb = 0; kb < kblocks; ++kb) {
@@ -497,18 +498,26 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             __syncwarp();
             if (lane == 0) mbar_arrive(&ctl->tempty[cb]);
           }
+          // two columns per step on packed FP32x2; per column the operations and their order
+          // are those of the scalar merge
+          const float2 q8 = make_float2(0.00390625f, 0.00390625f);
 #pragma unroll
-          for (int i = 0; i < kLdCols; ++i) {
+          for (int i = 0; i < kLdCols; i += 2) {
             const int c = hc * kLdCols + i;
-            const float scl = sa * __shfl_sync(0xffffffffu, sb_mine, c);
+            const float2 scl = mul2(sa, make_float2(__shfl_sync(0xffffffffu, sb_mine, c),
+                                                    __shfl_sync(0xffffffffu, sb_mine, c + 1)));
+            const float2 v0 = make_float2(__uint_as_float(s0[i]), __uint_as_float(s0[i + 1]));
+            const float2 v1 = make_float2(__uint_as_float(s1[i]), __uint_as_float(s1[i + 1]));
+            const float2 v2 = make_float2(__uint_as_float(s2[i]), __uint_as_float(s2[i + 1]));
+            const float2 v3 = make_float2(__uint_as_float(s3[i]), __uint_as_float(s3[i + 1]));
             // orders 1..3 combined first: their roundings are 2^-24 of terms 2^-8 below hi
-            const float w = __fmaf_rn(__uint_as_float(s3[i]), 0.00390625f, __uint_as_float(s2[i]));
-            const float u = __fmaf_rn(w, 0.00390625f, __uint_as_float(s1[i]));
-            const float t0 = __uint_as_float(s0[i]) * scl;
-            const float t1 = u * (scl * 0.00390625f);
-            float er;
-            two_sum(hi[c], t0, hi[c], er);
-            lo[c] = __fadd_rn(lo[c], __fadd_rn(er, t1));
+            const float2 w = __ffma2_rn(v3, q8, v2);
+            const float2 u = __ffma2_rn(w, q8, v1);
+            const float2 t0 = __fmul2_rn(v0, scl);
+            const float2 t1 = __fmul2_rn(u, __fmul2_rn(scl, q8));
+            float2 er;
+            two_sum2(hi[c / 2], t0, hi[c / 2], er);
+            lo[c / 2] = add2(lo[c / 2], add2(er, t1));
           }
         }
         ++chunk;
@@ -516,7 +525,11 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       if (fail_all) break;
       float val[kEpiCols];
 #pragma unroll
-      for (int i = 0; i < kEpiCols; ++i) val[i] = __fadd_rn(hi[i], lo[i]);
+      for (int i = 0; i < kEpiCols / 2; ++i) {
+        const float2 v = add2(hi[i], lo[i]);
+        val[2 * i] = v.x;
+        val[2 * i + 1] = v.y;
+      }
       if (STAGE == 1) {
         // weight 1/(lam_y + lam_x)^2 (normalised); lam_y of the warp's columns via shuffles
 #pragma unroll
