@@ -202,20 +202,29 @@ __device__ __forceinline__ int block_exp(float amax) {
   return max(e, -90);  // keeps 2^(32-E) and 2^(E-16-8d) normal
 }
 
-// The NS integer slices of v for block exponent E, given s = 2^(8-E) and is = 2^(E-8) (all the
-// powers of two below are normal for the exponents block_exp returns): every product is exact, so
-// each residual is v minus the slices so far, rounded once; the last slice is rounded to an
-// integer.
+// The NS integer slices of a value for block exponent E, given s = 2^(8-E) and is = 2^(E-8)
+// (all the powers of two involved are normal for the exponents block_exp returns): every
+// product is exact, so each residual is the value minus the slices so far, rounded once; the last
+// slice is rounded to an integer.
+// Two values at once on packed FP32x2, each lane with its own block factors; the slices' 16-bit
+// codes are returned as (lane x, lane y) pairs.
 template <bool BF16>
-__device__ __forceinline__ void slice_store(uint16_t* base, size_t plane, size_t idx, float v, float s, float is) {
-  float r = v, up = s, down = is;
+__device__ __forceinline__ void slice_codes2(float2 v, float2 s, float2 is, uint32_t (&code)[NS]) {
+  float2 r = v, up = s, down = make_float2(-is.x, -is.y);
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    const float c = rintf(r * up);
-    if (k + 1 < NS) r = __fmaf_rn(-c, down, r);
-    up *= 256.f;
-    down *= 0.00390625f;
-    base[k * plane + idx] = BF16 ? __bfloat16_as_ushort(__float2bfloat16_rn(c)) : __half_as_ushort(__float2half_rn(c));
+    const float2 t = __fmul2_rn(r, up);
+    const float2 c = make_float2(rintf(t.x), rintf(t.y));
+    if (k + 1 < NS) r = __ffma2_rn(c, down, r);
+    up = mul2(256.f, up);
+    down = mul2(0.00390625f, down);
+    if (BF16) {
+      code[k] = static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(c.x))) |
+                (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(c.y))) << 16);
+    } else {
+      code[k] = static_cast<uint32_t>(__half_as_ushort(__float2half_rn(c.x))) |
+                (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(c.y))) << 16);
+    }
   }
 }
 
@@ -562,10 +571,18 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const size_t plane = static_cast<size_t>(v.M) * v.N;
         uint16_t* out = static_cast<uint16_t*>(v.out);
 #pragma unroll
-        for (int i = 0; i < kEpiCols; ++i) {
-          const float s = __shfl_sync(0xffffffffu, s_mine, i);
-          const float is = __shfl_sync(0xffffffffu, is_mine, i);
-          slice_store<BF16>(out, plane, static_cast<size_t>(ncol0 + i) * v.M + m, val[i], s, is);
+        for (int i = 0; i < kEpiCols; i += 2) {
+          const float2 s2 = make_float2(__shfl_sync(0xffffffffu, s_mine, i), __shfl_sync(0xffffffffu, s_mine, i + 1));
+          const float2 is2 =
+              make_float2(__shfl_sync(0xffffffffu, is_mine, i), __shfl_sync(0xffffffffu, is_mine, i + 1));
+          uint32_t code[NS];
+          slice_codes2<BF16>(make_float2(val[i], val[i + 1]), s2, is2, code);
+          const size_t i0 = static_cast<size_t>(ncol0 + i) * v.M + m, i1 = i0 + v.M;
+#pragma unroll
+          for (int q = 0; q < NS; ++q) {
+            out[q * plane + i0] = static_cast<uint16_t>(code[q] & 0xffffu);
+            out[q * plane + i1] = static_cast<uint16_t>(code[q] >> 16);
+          }
         }
         if (quarter == q0 && col_lane)
           v.eout[static_cast<size_t>(ncol0 + lane) * (v.M / KC) + (m0 + 32 * quarter) / KC] =
@@ -681,28 +698,39 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     // every row of the warp loaded before any is sliced
     constexpr int kRows = kStTileY / 8;
     static_assert(kRows * 8 == kStTileY, "rows per warp");
-    float v[kRows][KC / 32];
+    // each lane takes adjacent pairs (x, x+1) and writes both codes of a slice in one 4-byte
+    // store (x even, rows of nxp even: aligned)
+    constexpr int kPairs = KC / 64;
+    float2 v[kRows][kPairs];
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       const int y = y0 + warp + 8 * j;
 #pragma unroll
-      for (int k = 0; k < KC / 32; ++k) {
-        const int x = x0 + 32 * k + lane;
-        v[j][k] = (x < S.nx && y < S.ny) ? S.r[y * S.nx + x] : 0.f;
+      for (int k = 0; k < kPairs; ++k) {
+        const int x = x0 + 64 * k + 2 * lane;
+        const float* row = S.r + static_cast<size_t>(y) * S.nx;
+        v[j][k].x = (x < S.nx && y < S.ny) ? row[x] : 0.f;
+        v[j][k].y = (x + 1 < S.nx && y < S.ny) ? row[x + 1] : 0.f;
       }
     }
+    uint32_t* out32 = reinterpret_cast<uint32_t*>(out);
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       const int y = y0 + warp + 8 * j;
       if (y >= S.ny) break;
       float amax = 0.f;
 #pragma unroll
-      for (int k = 0; k < KC / 32; ++k) amax = fmaxf(amax, fabsf(v[j][k]));
+      for (int k = 0; k < kPairs; ++k) amax = fmaxf(amax, fmaxf(fabsf(v[j][k].x), fabsf(v[j][k].y)));
       const int E = block_exp(warp_max(amax));
       const float s = pow2f(8 - E), is = pow2f(E - 8);
 #pragma unroll
-      for (int k = 0; k < KC / 32; ++k)
-        slice_store<BF16>(out, plane, static_cast<size_t>(y) * S.nxp + x0 + 32 * k + lane, v[j][k], s, is);
+      for (int k = 0; k < kPairs; ++k) {
+        uint32_t code[NS];
+        slice_codes2<BF16>(v[j][k], make_float2(s, s), make_float2(is, is), code);
+        const size_t idx = (static_cast<size_t>(y) * S.nxp + x0 + 64 * k + 2 * lane) / 2;
+#pragma unroll
+        for (int q = 0; q < NS; ++q) out32[q * (plane / 2) + idx] = code[q];
+      }
       if (lane == 0) S.tc_e[0][static_cast<size_t>(y) * kblocks + x0 / KC] = static_cast<int8_t>(E);
     }
   }
