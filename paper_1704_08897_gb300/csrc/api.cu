@@ -78,8 +78,9 @@ struct Workspace {
   SlotScalars* d_sc = nullptr;
   SlotScalars* h_sc = nullptr;  // pinned
   WorkItem *d_st = nullptr, *d_vec = nullptr, *d_gm = nullptr;
-  int *d_counts = nullptr;      // [0] stencil items, [1] vector items, [2] gemm items
-  int n_st = 0, n_vec = 0, n_gm = 0;
+  WorkItem* d_sl = nullptr;     // one item per slot (tile 0), for the per-slot scalar kernels
+  int *d_counts = nullptr;      // [0] stencil items, [1] vector items, [2] gemm items, [3] slots
+  int n_st = 0, n_vec = 0, n_gm = 0, n_sl = 0;
   const float** d_phis = nullptr;
   const float** d_fs = nullptr;
   float** d_outs = nullptr;
@@ -342,6 +343,7 @@ static void free_workspace(Workspace* W) {
   cudaFree(W->d_st);
   cudaFree(W->d_vec);
   cudaFree(W->d_gm);
+  cudaFree(W->d_sl);
   cudaFree(W->d_counts);
   cudaFree(W->d_phis);
   cudaFree(W->d_fs);
@@ -540,6 +542,9 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
   }
   longest_first(gm, W->slots);
+  std::vector<WorkItem> sl;
+  for (int i = 0; i < count; ++i) sl.push_back({i, 0});
+  W->n_sl = (int)sl.size();
   W->n_st = (int)st.size();
   W->n_vec = (int)vec.size();
   W->n_gm = (int)gm.size();
@@ -557,7 +562,9 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   BX_CUDA(cudaMemcpy(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMemcpy(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMemcpy(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice));
-  int counts[3] = {W->n_st, W->n_vec, W->n_gm};
+  BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * sl.size()));
+  BX_CUDA(cudaMemcpy(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice));
+  int counts[4] = {W->n_st, W->n_vec, W->n_gm, W->n_sl};
   BX_CUDA(cudaMalloc(&W->d_counts, sizeof(counts)));
   BX_CUDA(cudaMemcpy(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * count));
@@ -604,6 +611,10 @@ static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
     c.items = W->d_vec;
     c.n_items = W->d_counts + 1;
     c.grid = std::max(1, std::min(W->n_vec, cap));
+  } else if (which == 3) {
+    c.items = W->d_sl;
+    c.n_items = W->d_counts + 3;
+    c.grid = std::max(1, std::min(W->n_sl, cap));
   } else {
     c.items = W->d_gm;
     c.n_items = W->d_counts + 2;
@@ -684,8 +695,7 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
       else launch_prec_tc(g, s, mode, ctx->split, ctx->d_err);
     }, g.stream);
   }
-  LaunchCfg f = cfg_of(ctx, W, 2);
-  f.grid = std::max(1, std::min(W->n_gm, ctx->sm_count * 4));
+  const LaunchCfg f = cfg_of(ctx, W, 3);  // one block per slot
   timed(ctx, EXT_KERNEL_PREC_FINISH, [&] { launch_prec_finish(f, mode); }, f.stream);
 }
 
@@ -693,8 +703,7 @@ static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
   const LaunchCfg st = cfg_of(ctx, W, 0), vc = cfg_of(ctx, W, 1);
   for (int i = 0; i < iters; ++i) {
     timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(st, W->aniso); }, st.stream);
-    LaunchCfg pf = st;
-    pf.grid = std::max(1, std::min(W->n_st, ctx->sm_count * 4));
+    const LaunchCfg pf = cfg_of(ctx, W, 3);  // one block per slot
     timed(ctx, EXT_KERNEL_PQ_FINISH, [&] { launch_pq_finish(pf); }, st.stream);
     timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); }, st.stream);
     launch_prec(ctx, W, 0);
@@ -1220,8 +1229,10 @@ static int serve_init(ext_ctx* ctx) {
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * cap));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * cap));
   memset(W->h_sc, 0, sizeof(SlotScalars) * cap);
-  BX_CUDA(cudaMalloc(&W->d_counts, 3 * sizeof(int)));
-  BX_CUDA(cudaMemset(W->d_counts, 0, 3 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_counts, 4 * sizeof(int)));
+  BX_CUDA(cudaMemset(W->d_counts, 0, 4 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * cap));
+  W->n_sl = cap;  // the per-slot grid is sized for the slot table
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * cap));
   BX_CUDA(cudaMalloc(&W->d_fs, sizeof(void*) * cap));
   BX_CUDA(cudaMalloc(&W->d_outs, sizeof(void*) * cap));
@@ -1242,7 +1253,7 @@ static int serve_init(ext_ctx* ctx) {
 static int serve_rebuild_lists(ext_ctx* ctx) {
   ext_ctx::Serve* S = ctx->serve;
   Workspace* W = S->W;
-  std::vector<WorkItem> st, vec, gm;
+  std::vector<WorkItem> st, vec, gm, sl;
   bool aniso = false;
   for (int i = 0; i < (int)S->slots.size(); ++i) {
     if (!S->slots[i].used) continue;
@@ -1251,6 +1262,7 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
     for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
+    sl.push_back({i, 0});
   }
   longest_first(gm, W->slots);
   const int need = (int)std::max(st.size(), std::max(vec.size(), gm.size()));
@@ -1270,7 +1282,8 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
   if (!st.empty()) BX_CUDA(cudaMemcpyAsync(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice, s));
   if (!vec.empty()) BX_CUDA(cudaMemcpyAsync(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice, s));
   if (!gm.empty()) BX_CUDA(cudaMemcpyAsync(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice, s));
-  int counts[3] = {(int)st.size(), (int)vec.size(), (int)gm.size()};
+  if (!sl.empty()) BX_CUDA(cudaMemcpyAsync(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice, s));
+  int counts[4] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size()};
   BX_CUDA(cudaMemcpyAsync(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
   // the host vectors die here: the copies above must finish first (pageable sources are staged)
   BX_CUDA(cudaStreamSynchronize(s));
