@@ -187,6 +187,14 @@ __device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&v)[N]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// A global load that stays where it is written (volatile asm is not moved across the other
+// volatile asm of the k-block loop), so its latency overlaps the loop.
+__device__ __forceinline__ float ld_early(const float* p) {
+  float v;
+  asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 // 2^e as a float for e in the normal range, 0 below it.
 __device__ __forceinline__ float pow2f(int e) {
   return e < -126 ? 0.f : __int_as_float((min(e, 127) + 127) << 23);
@@ -458,8 +466,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       // stage 1's eigenvalues, read now so their latency hides behind the k-blocks
       float lamx_m = 0.f, lamy_mine = 0.f;
       if (STAGE == 1) {
-        lamx_m = (m < S.nx) ? S.lamx[m] : 0.f;
-        lamy_mine = (col_lane && ncol0 + lane < S.ny) ? S.lamy[ncol0 + lane] : 0.f;
+        // issued here, not where the compiler would sink them: the MMA waits hide their latency
+        if (m < S.nx) lamx_m = ld_early(S.lamx + m);
+        if (col_lane && ncol0 + lane < S.ny) lamy_mine = ld_early(S.lamy + ncol0 + lane);
       }
       const int8_t* ea_row = S.tc_e[STAGE] + static_cast<size_t>(m) * kblocks;
       const int8_t* eb_col = S.tc_eb[STAGE] + static_cast<size_t>(ncol0 + (col_lane ? lane : 0)) * kblocks;
