@@ -406,7 +406,29 @@ def cpu_baseline(args, probs, budget_s=30.0):
             "host_cores_available": os.cpu_count()}, refs
 
 
-def error_vs_oracle(probs, answers, refs, prec):
+def accuracy_solve(probs, prec, rtol, count=32):
+    """One warm and one timed batched solve of the workload at a tighter tolerance; returns its
+    solves/s and the answers of the first `count` problems."""
+    import torch
+
+    from paper_1704_08897_gb300 import ext
+    maxit = 40 * max(max(p.nx, p.ny) for p in probs)
+    ctx = ext.ext_create(ext.options(prec, rtol=rtol, maxit=maxit))
+    dprobs = [ext.problem_of(p) for p in probs]
+    phis = [torch.from_numpy(p.phi).cuda() for p in probs]
+    fs = [torch.from_numpy(p.f).cuda() for p in probs]
+    outs = [torch.empty_like(x) for x in phis]
+    ext.ext_solve_batch(ctx, dprobs, phis, fs, outs, check=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ext.ext_solve_batch(ctx, dprobs, phis, fs, outs, check=False)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    ext.ext_destroy(ctx)
+    return len(probs) / el, [o.cpu().numpy() for o in outs[:count]]
+
+
+def error_vs_oracle(probs, answers, refs, prec, at="rel-res 1e-8, answers of the last timed step"):
     """Max-norm relative error (max over unknowns of |x - x*| / max |out*|) of the GPU answers
     of the timed run against the oracle's direct solves, over the problems the oracle solved."""
     import numpy as np
@@ -419,7 +441,7 @@ def error_vs_oracle(probs, answers, refs, prec):
     bound = 1e-6 if prec == "fp32" else 1e-5
     return {"max_rel": float(max(errs)), "median_rel": float(np.median(errs)),
             "problems": len(errs), "bound": bound, "within": bool(max(errs) <= bound),
-            "at": "rel-res 1e-8, answers of the last timed step"}
+            "at": at}
 
 
 def run_reference(args, rank, world):
@@ -470,7 +492,16 @@ def main():
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"], refs = cpu_baseline(args, probs)
-            out["error_vs_oracle"] = error_vs_oracle(probs, answers, refs, out["config"]["prec"])
+            prec = out["config"]["prec"]
+            acc = {"rtol_1e-08": error_vs_oracle(probs, answers, refs, prec)}
+            if args.workload == "batch":
+                # the FP32-vector iteration's error at rel-res 1e-8 scatters with the rounding
+                # history; the same batch solved to 5e-9, with its own throughput
+                sps, ans2 = accuracy_solve(probs, prec, 5e-9)
+                acc["rtol_5e-09"] = dict(error_vs_oracle(probs, ans2, refs, prec,
+                                                         at="rel-res 5e-9, one batched solve"),
+                                         solves_per_s=round(sps, 3))
+            out["error_vs_oracle"] = acc
         print(json.dumps(out))
     if world > 1:
         import torch.distributed as dist
