@@ -177,6 +177,15 @@ def kernel_hash(kind, prec="fp32"):
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
+def reduce_over_ranks(value, op, device):
+    """Max or sum of a per-rank number over all ranks (torch.distributed initialised)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -246,12 +255,13 @@ def run_ours(args, rank, world):
     answers = [o.cpu().numpy() for o in outs[:32]]
     clk = clocks.stop()
     total_ms = sum(step_ms)
+    converged = sum(1 for r in results if r.get("status", 0) == 0)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+        # the job's time is the slowest rank's; its work is every rank's converged solves
+        total_ms = reduce_over_ranks(total_ms, "max", "cuda")
+        converged = reduce_over_ranks(converged, "sum", "cuda")
         torch.distributed.barrier()
-    solves = sum(1 for r in results if r.get("status", 0) == 0) * args.steps * world
+    solves = converged * args.steps
     value = solves / (total_ms / 1e3)
     serving = None
     if serve_stats:
