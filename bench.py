@@ -114,6 +114,8 @@ def algorithmic_cost(probs, kind):
         return sum(17 * p.nx * p.ny for p in probs), "byte"
     if kind == "update":    # read xhat(8), p, q, r; write xhat(8), r
         return sum(32 * p.nx * p.ny for p in probs), "byte"
+    if kind == "split":     # read r; write four 16-bit slices
+        return sum(12 * p.nx * p.ny for p in probs), "byte"
     return None, None
 
 
@@ -314,7 +316,7 @@ def run_ours(args, rank, world):
                "d2h_bytes_per_step": sum(4 * p.nx * p.ny for p in probs)}
 
     # per-kernel CUDA-event durations of the same workload (a profiled pass: no graphs)
-    roofline, kernels = None, None
+    roofline, kernels, kernels_hbm = None, None, None
     if not args.no_profile and rank == 0:
         # profiled pass: the first 100 iterations, during which every instance is still iterating,
         # so each launch processes the whole workload (the algorithmic cost per launch holds)
@@ -338,8 +340,8 @@ def run_ours(args, rank, world):
             per_launch_s = ms / n / 1e3
             if unit == "flop" and prec != "fp32":
                 # tensor-core stage: algorithmic flops (2 n^3-type, unpadded) against the measured
-                # sustained dense BF16 peak; the MMAs actually issued are six slice products
-                # over padded tiles, reported beside it
+                # sustained dense BF16 peak; the MMAs actually issued (ten slice products over
+                # padded tiles) are reported beside it
                 achieved = amount / per_launch_s / 1e12
                 with open(PEAKS_FILE) as fh:
                     peak = json.load(fh)["bf16_tflops_sustained"]
@@ -365,6 +367,17 @@ def run_ours(args, rank, world):
                         "peak": round(peak, 3), "unit": u, "frac": round(achieved / peak, 4),
                         "traffic": traffic, "peak_source": peak_src,
                         "algorithmic_per_launch": amount, "algorithmic_unit": unit}
+            # the memory-bound kernels against the measured copy bandwidth, from the same pass
+            with open(PEAKS_FILE) as fh:
+                hbm_peak = json.load(fh)["hbm_gbs"]
+            hbm = {}
+            for kd in ("stencil", "update", "split"):
+                amt, un = algorithmic_cost(probs, kd)
+                if kd in prof and prof[kd][1] and un == "byte":
+                    gbs = amt / (prof[kd][0] / prof[kd][1] / 1e3) / 1e9
+                    hbm[kd] = {"achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),
+                               "bytes_per_launch": amt}
+            kernels_hbm = hbm
             if bound == "tensor":
                 # what the tensor pipe actually executes: the exact slice products on padded tiles
                 issued = issued_tensor_flop(probs, dom) / per_launch_s / 1e12
@@ -386,7 +399,7 @@ def run_ours(args, rank, world):
            "relres_true_max": max(r["relres_true"] for r in results),
            "all_converged": all(r.get("status", 0) == 0 for r in results),
            "plain_fp32_single_solve": plain, "serving": serving,
-           "e2e": e2e, "roofline": roofline, "kernels": kernels,
+           "e2e": e2e, "roofline": roofline, "hbm_kernels": kernels_hbm, "kernels": kernels,
            "gpu_launches": launches, "clocks": clk}
     return out, probs, answers
 
