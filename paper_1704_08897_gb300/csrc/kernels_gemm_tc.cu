@@ -16,7 +16,8 @@
 //    Per k, the products of one order add up to less than 2^16.6, so over 128 k every partial
 //    sum is an exact integer below 2^24 and so is the accumulation;
 //  * the epilogue warps scale the four exact sums by 2^(E_A + E_B - 16 - 8d) and add them into
-//    a compensated (hi, lo) register pair, k-block after k-block.
+//    a compensated (hi, lo) register pair, k-block after k-block, two columns per packed FP32x2
+//    operation.
 // The operands carry 32 bits relative to each 128-block's largest value and the products add no
 // error along K; only the stage output is rounded (to FP32, then sliced).  Three slices on
 // 64-blocks (24 bits) cost this operator 30-80% more CG iterations than exact transforms; four on
