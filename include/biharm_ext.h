@@ -47,9 +47,11 @@ typedef enum { EXT_EXTEND_OUT = 0, EXT_EXTEND_IN = 1 } ext_dir;
  * residual b - A x whenever it has fallen by replace_factor since the last replacement, at
  * least every true_res_every iterations, and before convergence is declared.
  *   FP32        : FP32 vectors, compensated FP32 stencil, FP32 CUDA-core transform products.
- *   MIXED_FP16  : as FP32, transforms on the tcgen05 tensor cores from FP16 hi/lo operand splits
- *                 with FP32 accumulation (flexible CG).
- *   MIXED_BF16  : as MIXED_FP16 with BF16 hi/mid/lo operand splits.                          */
+ *   MIXED_FP16  : as FP32, transforms on the tcgen05 tensor cores: every operand as four exact
+ *                 8-bit integer slices per 128-wide exponent block, stored as FP16, products
+ *                 summed exactly per slice order in FP32 accumulators.
+ *   MIXED_BF16  : the same slices stored as BF16 (results identical to MIXED_FP16).
+ * The iteration runs on 2^e b with e chosen from ||b||; the answer is scaled back exactly.    */
 typedef enum {
   EXT_PREC_FP32 = 1,
   EXT_PREC_MIXED_BF16 = 2,
@@ -74,7 +76,8 @@ typedef struct {
   size_t hbm_budget;       /* bytes the serving queue may hold for admitted requests; 0 = 50%
                               of free device memory at ext_create                             */
   int32_t flexible;        /* 1 = flexible (Polak-Ribiere) beta, 0 = Fletcher-Reeves beta;
-                              default 1 (required for the mixed modes)                        */
+                              default 0: on the benchmark grids it takes fewer iterations and
+                              ends nearer the exact solution at the same residual              */
   int32_t max_slots;       /* serving: most requests in flight at once; default 256            */
   int32_t profile;         /* 1: launch every kernel directly (no CUDA graphs) and time each one
                               with CUDA events on the context stream (ext_profile_read); 0    */

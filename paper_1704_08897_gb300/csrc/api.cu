@@ -895,7 +895,7 @@ void ext_options_default(ext_options* o) {
   o->replace_factor = 1e-2;
   o->iters_per_launch = 10;
   o->hbm_budget = 0;
-  o->flexible = 1;
+  o->flexible = 0;
   o->max_slots = 256;
 }
 

@@ -47,6 +47,7 @@ struct __align__(16) SlotScalars {
   unsigned cnt[6];  // completion counters of the last-item reductions, one per kernel kind
   int n_known;      // known nodes, counted by the set-up kernel
   int bexp;         // the iteration solves A x' = 2^bexp b; the answer is x = 2^-bexp x'
+  double rho_prev;  // r.z of the previous iteration (Fletcher-Reeves beta)
 };
 
 // Static description of one slot (device copy).  Padded transform dims are multiples of kPad.
@@ -309,8 +310,11 @@ __device__ __forceinline__ void finish_preconditioner(const SlotDesc& S, double 
     sc->zq = zq;
     return;
   }
+  // Mode 1 recomputes, after a residual replacement, the beta of the iteration whose mode-0
+  // pass already ran: its Fletcher-Reeves denominator is the r.z from before that pass.
+  if (mode == 0) sc->rho_prev = sc->rho;
   double beta = 0.0;
-  if (sc->it > 0) beta = sc->flexible ? -zq / sc->pq : rz / sc->rho;
+  if (sc->it > 0) beta = sc->flexible ? -zq / sc->pq : rz / sc->rho_prev;
   sc->rho = rz;
   sc->zq = zq;
   sc->beta = beta;

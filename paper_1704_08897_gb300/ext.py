@@ -157,7 +157,7 @@ def problem_of(p):
 
 
 def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launch=10,
-            hbm_budget=0, flexible=1, max_slots=256, replace_factor=1e-2, profile=0):
+            hbm_budget=0, flexible=0, max_slots=256, replace_factor=1e-2, profile=0):
     o = ExtOptions()
     load().ext_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)

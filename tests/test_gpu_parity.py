@@ -431,3 +431,24 @@ def test_solution_scales_with_the_field(ext, prec, s):
             assert np.abs(b - a).max() <= 1e-4 * np.abs(a).max()
     finally:
         ext.ext_destroy(c)
+
+
+# ----------------------------------------------------------------------------------------------
+# Fletcher-Reeves beta (flexible=0) over many residual replacements: after a replacement the
+# beta of the current iteration is recomputed with the previous iteration's r.z.
+# ----------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp32", "mixed_bf16"])
+def test_fletcher_reeves_converges_through_residual_replacements(ext, prec):
+    p = synth.wobbly(128, 2)
+    its = {}
+    for flex in (1, 0):
+        c = ext.ext_create(ext.options(prec, rtol=1e-8, flexible=flex, true_res_every=20))
+        try:
+            out = torch.empty(p.phi.shape, device="cuda")
+            r = ext.ext_solve(c, ext.problem_of(p), dev(p.phi), dev(p.f), out, check=False)
+        finally:
+            ext.ext_destroy(c)
+        assert r["status"] == 0 and r["relres_true"] <= 1.05e-8, (flex, r)
+        its[flex] = r["iters"]
+    # both betas are exact CG for a fixed symmetric preconditioner: comparable counts
+    assert its[0] <= 2 * its[1], its
