@@ -163,7 +163,6 @@ static void longest_first(std::vector<WorkItem>& gm, const std::vector<SlotHost>
 }
 
 // ---- tensor-core operands --------------------------------------------------------------------
-constexpr int kExpBlock = 128;  // k per block exponent of the sliced operands (kernels_gemm_tc.cu KC)
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
                                   CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -238,7 +237,8 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
     P->tc = nullptr;
   }
   const int NS = tc_planes(ctx->split);
-  const int np = P->np, n = P->n, nkb = np / kExpBlock;
+  const int KB = tc_block();  // k per block exponent of the sliced operands
+  const int np = P->np, n = P->n, nkb = np / KB;
   const size_t plane = (size_t)np * np;
   std::vector<uint16_t> h(2 * NS * plane, 0);
   std::vector<int8_t> ex(2 * (size_t)np * nkb, 0);
@@ -255,11 +255,11 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
     int8_t* eo = ex.data() + t * (size_t)np * nkb;
     for (int row = 0; row < np; ++row)
       for (int kb = 0; kb < nkb; ++kb) {
-        const double* blk = M.data() + (size_t)row * np + kb * kExpBlock;
-        const int E = block_exp_host(blk, 1, kExpBlock);
+        const double* blk = M.data() + (size_t)row * np + kb * KB;
+        const int E = block_exp_host(blk, 1, KB);
         eo[(size_t)row * nkb + kb] = (int8_t)E;
-        for (int k = 0; k < kExpBlock; ++k)
-          slice_host(blk[k], E, ctx->split, NS, out, plane, (size_t)row * np + kb * kExpBlock + k);
+        for (int k = 0; k < KB; ++k)
+          slice_host(blk[k], E, ctx->split, NS, out, plane, (size_t)row * np + kb * KB + k);
       }
   }
   const size_t bytes = 2 * h.size() + ex.size();
@@ -277,7 +277,7 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
 // Exponent arrays of a plan: t = 0 for Q rows, 1 for Q^T rows.
 static const int8_t* plan_exps(const PlanDev* P, int t) {
   const size_t plane = (size_t)P->np * P->np;
-  const size_t nkb = P->np / kExpBlock;
+  const size_t nkb = P->np / tc_block();
   return (const int8_t*)((const char*)P->tc + 2 * 2 * (size_t)tc_planes(P->tc_split) * plane) +
          t * (size_t)P->np * nkb;
 }
@@ -803,7 +803,6 @@ static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const
     sc.fold_every = ctx->opt.true_res_every;
     sc.delta2 = ctx->opt.replace_factor * ctx->opt.replace_factor;
     sc.flexible = ctx->opt.flexible;
-    sc.pscale = 1.f;
     sc.status = ST_RUNNING;
   }
   BX_CUDA(cudaMemcpyAsync(W->d_sc, W->h_sc, sizeof(SlotScalars) * count, cudaMemcpyHostToDevice, s));
@@ -1069,7 +1068,6 @@ static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi,
   W->h_sc[0].maxit = 1;
   W->h_sc[0].fold_every = ctx->opt.true_res_every;
   W->h_sc[0].delta2 = 1e-4;
-  W->h_sc[0].pscale = 1.f;
   BX_CUDA(cudaMemcpyAsync(W->d_sc, W->h_sc, sizeof(SlotScalars), cudaMemcpyHostToDevice, s));
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(cfg_of(ctx, W, 0), W->d_phis, W->d_fs, W->d_dirs); });
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_rhs_scale(cfg_of(ctx, W, 0)); });
@@ -1380,7 +1378,6 @@ static int serve_setup_slots(ext_ctx* ctx, const std::vector<int>& admitted) {
     sc.fold_every = ctx->opt.true_res_every;
     sc.delta2 = ctx->opt.replace_factor * ctx->opt.replace_factor;
     sc.flexible = ctx->opt.flexible;
-    sc.pscale = 1.f;
     sc.status = ST_RUNNING;
     BX_CUDA(cudaMemcpyAsync(W->d_sc + i, &sc, sizeof(SlotScalars), cudaMemcpyHostToDevice, s));
     for (int t = 0; t < sl.d.n_st_tiles; ++t) fresh.push_back({i, t});

@@ -35,7 +35,6 @@ struct __align__(16) SlotScalars {
   double rtol2;     // rtol^2
   double rr_ref;    // ||r||^2 at the last residual replacement
   double delta2;    // replace the residual once ||r||^2 < delta2 * rr_ref
-  float pscale;     // power-of-two scale applied to r before the preconditioner
   int it;           // completed iterations
   int maxit;
   int fold_every;   // longest stretch of iterations between residual replacements

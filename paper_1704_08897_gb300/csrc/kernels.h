@@ -46,6 +46,7 @@ void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int
 // residual -> scaled planes of the first stage's A operand (vector work list)
 void launch_prec_tc_prepare(const LaunchCfg& c, int mode, int split_kind);
 int tc_planes(int split_kind);
+int tc_block();
 bool tc_supported();
 // opt the tensor-core kernels into their dynamic shared memory (once per process and device)
 cudaError_t tc_init();

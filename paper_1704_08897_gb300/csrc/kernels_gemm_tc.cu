@@ -697,7 +697,6 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
     if (!slot_runs(sc, mode)) continue;
-    if (it.tile == 0 && threadIdx.x == 0) sc->pscale = 1.f;
     const int tx = (S.nx + kStTileX - 1) / kStTileX;
     const int x0 = (it.tile % tx) * kStTileX;
     const int y0 = (it.tile / tx) * kStTileY;
@@ -783,6 +782,8 @@ bool tc_supported() {
 }
 
 int tc_planes(int) { return NS; }
+
+int tc_block() { return KC; }
 
 cudaError_t tc_init() {
   cudaError_t e = cudaSuccess;
