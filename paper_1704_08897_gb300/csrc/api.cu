@@ -183,25 +183,49 @@ static EncodeTiledFn get_encoder() {
   return fn;
 }
 
-// 2-D map over `rows` rows of `inner` 2-byte elements; boxes of 64 x box_rows, 128-byte swizzle.
-static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+// 2-D map over `rows` rows of `inner` elements of `elem` bytes, boxes of box_inner x box_rows.
+// Cells outside the array read as zeros.
+static int make_tmap_2d(CUtensorMap* m, void* base, CUtensorMapDataType type, uint64_t elem, uint64_t inner,
+                        uint64_t rows, uint32_t box_inner, uint32_t box_rows, CUtensorMapSwizzle swz) {
   EncodeTiledFn enc = get_encoder();
   if (!enc) {
     g_last_error = "cuTensorMapEncodeTiled not available";
     return EXT_ENOTSUP;
   }
   const cuuint64_t dims[2] = {inner, rows};
-  const cuuint64_t strides[1] = {inner * 2};
-  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint64_t strides[1] = {inner * elem};
+  const cuuint32_t box[2] = {box_inner, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  const CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, base,
-                         dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+  const CUresult r = enc(m, type, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     g_last_error = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
     return EXT_ECUDA;
   }
   return EXT_OK;
+}
+
+// Tensor-core operand planes: `rows` rows of `inner` 16-bit slices; boxes of 64 x box_rows,
+// 128-byte swizzle.
+static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint64_t rows, uint32_t box_rows) {
+  return make_tmap_2d(m, base, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                      inner, rows, 64, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
+// Stencil windows: z, p[0], p[1] as FP32 boxes of the tile plus its halo (two extra columns on
+// the left keep each copy's start on a 16-byte boundary) and the mask as 8-bit boxes of the
+// tile.  The mask rows must span a multiple of 16 bytes (nx % 16 == 0).
+static bool stencil_copies_fit(int nx) { return nx % 16 == 0; }
+static int make_stencil_maps(CUtensorMap (&m)[4], const SlotDesc& d) {
+  const uint32_t wx = kStTileX + 8, wy = kStTileY + 4;
+  float* const vec[3] = {d.z, d.p[0], d.p[1]};
+  for (int k = 0; k < 3; ++k) {
+    const int rc = make_tmap_2d(&m[k], vec[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.nx, d.ny, wx, wy,
+                                CU_TENSOR_MAP_SWIZZLE_NONE);
+    if (rc) return rc;
+  }
+  return make_tmap_2d(&m[3], d.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.nx, d.ny, kStTileX, kStTileY,
+                      CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
 // Three integer slices of v for block exponent E (v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24)),
@@ -406,6 +430,8 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
   size_t o_io = 0;
   if (host_io) o_io = take(12 * N);
+  const bool st_copy = stencil_copies_fit(nx);
+  const size_t o_smaps = st_copy ? take(4 * sizeof(CUtensorMap)) : 0;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
   size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0;
   const size_t nex = Np / 64;  // block exponents of one operand
@@ -443,6 +469,14 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.t3 = (float*)(A + o_t3);
   d.rin = nullptr;
   d.n_tc_tiles = n_gm;
+  d.st_maps = nullptr;
+  if (st_copy) {
+    CUtensorMap smaps[4];
+    const int rc1 = make_stencil_maps(smaps, d);
+    if (rc1) return rc1;
+    BX_CUDA(cudaMemcpy(A + o_smaps, smaps, sizeof(smaps), cudaMemcpyHostToDevice));
+    d.st_maps = A + o_smaps;
+  }
   if (ctx->tc) {
     int rc2 = ensure_tc_plan(ctx, px);
     if (!rc2) rc2 = ensure_tc_plan(ctx, py);
@@ -701,8 +735,10 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
 
 static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
   const LaunchCfg st = cfg_of(ctx, W, 0), vc = cfg_of(ctx, W, 1);
+  LaunchCfg sc = st;  // persistent: the resident blocks, each double-buffering its tiles
+  sc.grid = std::max(1, std::min(W->n_st, ctx->sm_count * stencil_blocks_per_sm()));
   for (int i = 0; i < iters; ++i) {
-    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(st, W->aniso); }, st.stream);
+    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, ctx->d_err); }, st.stream);
     const LaunchCfg pf = cfg_of(ctx, W, 3);  // one block per slot
     timed(ctx, EXT_KERNEL_PQ_FINISH, [&] { launch_pq_finish(pf); }, st.stream);
     timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); }, st.stream);
@@ -830,7 +866,7 @@ static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const
     if (*ctx->h_err) {
       BX_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
       BX_CUDA(cudaStreamSynchronize(s));
-      g_last_error = "a bounded device wait in the tensor-core preconditioner ran out";
+      g_last_error = "a bounded device wait (tensor copy or tensor-core pipeline) ran out";
       return EXT_ETIMEOUT;
     }
     bool running = false;
@@ -945,6 +981,7 @@ int ext_create(const ext_options* opt, void* cuda_stream, ext_ctx** out) {
   ctx->tc = o.prec != EXT_PREC_FP32;
   ctx->split = o.prec == EXT_PREC_MIXED_BF16 ? 1 : 0;
   if (ctx->tc) BX_CUDA(tc_init());
+  BX_CUDA(stencil_init());
   BX_CUDA(cudaMalloc(&ctx->d_err, sizeof(int)));
   BX_CUDA(cudaMemset(ctx->d_err, 0, sizeof(int)));
   BX_CUDA(cudaMallocHost(&ctx->h_err, sizeof(int)));

@@ -53,7 +53,7 @@ struct __align__(16) SlotScalars {
 struct SlotDesc {
   int nx, ny, nxp, nyp;
   int bcx, bcy;
-  int n_st_tiles;    // stencil tiles: ceil(nx/64) * ceil(ny/16)
+  int n_st_tiles;    // stencil tiles: ceil(nx/64) * ceil(ny/32)
   int n_vec_items;   // vector chunks: ceil(nx*ny / kVecChunk)
   int n_gm_tiles;    // output tiles of one transform stage
   float wc, wex, wey, wd, wfx, wfy;  // stencil weights (hi), scaled so that max(a, c) = 1
@@ -82,14 +82,16 @@ struct SlotDesc {
   const float* lamy;
   float wnorm;       // 1 / w_max, so that the scaled weights are <= 1
   int zero_mode;     // 1: drop the (0,0) mode (both axes symmetric/periodic)
-  // tensor-core path: block-scaled integer slices (three 16-bit planes) and their TMA descriptors
-  void* tc_r;        // [3][nyp][nxp]  residual
-  void* tc_t1;       // [3][nxp][nyp]
-  void* tc_t2;       // [3][nyp][nxp]
-  void* tc_t3;       // [3][nxp][nyp]
-  int8_t* tc_e[4];   // block exponents of the A operand of stage s: [rows][K/64]
+  // tensor-core path: block-scaled integer slices (NS 16-bit planes) and their TMA descriptors
+  void* tc_r;        // [NS][nyp][nxp]  residual
+  void* tc_t1;       // [NS][nxp][nyp]
+  void* tc_t2;       // [NS][nyp][nxp]
+  void* tc_t3;       // [NS][nxp][nyp]
+  int8_t* tc_e[4];   // block exponents of the A operand of stage s: [rows][K/128]
   const int8_t* tc_eb[4];  // block exponents of the B operand of stage s (transform matrices)
   const void* tmaps; // 8 CUtensorMap (64-byte aligned): A operand of stages 0..3, B of 0..3
+  const void* st_maps;  // 4 CUtensorMap for the stencil's tensor copies (z, p[0], p[1], mask);
+                        // null when a mask row is not a multiple of 16 bytes
   int n_tc_tiles;    // output tiles of one tensor-core transform stage
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing

@@ -22,7 +22,11 @@ void set_weights(SlotDesc& d, double hx, double hy);
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
                   const int* dirs);
 void launch_rhs_scale(const LaunchCfg& c);
-void launch_stencil(const LaunchCfg& c, bool aniso);
+// err receives 1 if a bounded wait for a tensor copy ran out
+void launch_stencil(const LaunchCfg& c, bool aniso, int* err);
+int stencil_blocks_per_sm();
+// shared-memory carveout of the stencil kernels (once per process and device)
+cudaError_t stencil_init();
 // per-slot p.q -> alpha (after the stencil)
 void launch_pq_finish(const LaunchCfg& c);
 void launch_update(const LaunchCfg& c);

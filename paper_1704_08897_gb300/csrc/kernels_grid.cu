@@ -5,13 +5,14 @@
 // The operator is eq. (discrete_biharmonic) of Sec. 2.1 with the boundary rules of Algorithm 1
 // (Dirichlet padding), half-sample reflection (symmetric) or wrap-around (periodic), evaluated
 // matrix-free ("no need to form the 13-banded matrix", Sec. 2.2).
+#include "async.cuh"
 #include "common.cuh"
 #include "kernels.h"
 
 namespace bx {
 
 constexpr int kHX = kStTileX + 4;  // 68
-constexpr int kHY = kStTileY + 4;  // 20
+constexpr int kHY = kStTileY + 4;  // 36
 constexpr int kHalo = kHX * kHY;
 
 __device__ __forceinline__ void tile_origin(const SlotDesc& S, int tile, int& x0, int& y0) {
@@ -32,14 +33,15 @@ __device__ __forceinline__ int halo_src(const SlotDesc& S, int x0, int y0, int i
   return my * S.nx + mx;
 }
 
-// 13-point masked biharmonic of a smem tile at local (ly+2, lx+2), compensated FP32.
-template <bool ANISO>
+// 13-point masked biharmonic of a smem tile (row stride RS) at local (ly+2, lx+2), compensated
+// FP32.
+template <bool ANISO, int RS = kHX>
 __device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, int ly, int lx) {
-  const float* c = t + (ly + 2) * kHX + (lx + 2);
+  const float* c = t + (ly + 2) * RS + (lx + 2);
   const float C = c[0];
-  const float E0 = c[-1], E1 = c[1], N0 = c[-kHX], N1 = c[kHX];
-  const float D0 = c[-kHX - 1], D1 = c[-kHX + 1], D2 = c[kHX - 1], D3 = c[kHX + 1];
-  const float F0 = c[-2], F1 = c[2], G0 = c[-2 * kHX], G1 = c[2 * kHX];
+  const float E0 = c[-1], E1 = c[1], N0 = c[-RS], N1 = c[RS];
+  const float D0 = c[-RS - 1], D1 = c[-RS + 1], D2 = c[RS - 1], D3 = c[RS + 1];
+  const float F0 = c[-2], F1 = c[2], G0 = c[-2 * RS], G1 = c[2 * RS];
   CompSum acc;
   if (!ANISO) {
     // 20 C - 8 (edges) + 2 (diagonals) + (distance 2); every term is an exact FP32 value
@@ -63,15 +65,18 @@ __device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, in
   return acc.result();
 }
 
-// The isotropic 13-point stencil at two adjacent nodes (x, x+1) of a smem tile; c points at
-// node x, an even index.  Eleven aligned 8-byte loads cover both neighbourhoods, and each lane
-// runs the scalar stencil13's operations in the same order (bit-identical results).
+// The isotropic 13-point stencil at two adjacent nodes (x, x+1) of a smem tile with an even row
+// stride RS; c points at node x, an even index.  Eleven aligned 8-byte loads cover both
+// neighbourhoods, and each lane runs the scalar stencil13's operations in the same order
+// (bit-identical results).
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+template <int RS>
 __device__ __forceinline__ float2 stencil13_pair(const float* c) {
-  const float2 Cm = ld2(c - 2), C = ld2(c), Cp = ld2(c + 2);                     // row y
-  const float2 Nm = ld2(c - kHX - 2), N = ld2(c - kHX), Np = ld2(c - kHX + 2);   // row y-1
-  const float2 Sm = ld2(c + kHX - 2), Sv = ld2(c + kHX), Sp = ld2(c + kHX + 2);  // row y+1
-  const float2 NN = ld2(c - 2 * kHX), SS = ld2(c + 2 * kHX);                     // rows y-2, y+2
+  static_assert(RS % 2 == 0, "pairs of nodes start on 8-byte boundaries");
+  const float2 Cm = ld2(c - 2), C = ld2(c), Cp = ld2(c + 2);                  // row y
+  const float2 Nm = ld2(c - RS - 2), N = ld2(c - RS), Np = ld2(c - RS + 2);   // row y-1
+  const float2 Sm = ld2(c + RS - 2), Sv = ld2(c + RS), Sp = ld2(c + RS + 2);  // row y+1
+  const float2 NN = ld2(c - 2 * RS), SS = ld2(c + 2 * RS);                    // rows y-2, y+2
   const float2 E0 = make_float2(Cm.y, C.x), E1 = make_float2(C.y, Cp.x);
   const float2 D0 = make_float2(Nm.y, N.x), D1 = make_float2(N.y, Np.x);
   const float2 D2 = make_float2(Sm.y, Sv.x), D3 = make_float2(Sv.y, Sp.x);
@@ -227,14 +232,100 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
 // Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo),
 // q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), per-tile partial p.q;
 // k_pq_finish then forms alpha = rho / p.q for each slot.
+//
+// Each block walks its share of the (slot, tile) list with two shared-memory windows.  For a slot
+// whose rows span a multiple of 16 bytes in the mask (nx % 16 == 0), the window of the block's
+// next tile arrives by tensor copies while it computes the current one: z and p_old over rows
+// y0-2 .. y0+33 and columns x0-4 .. x0+67 (two columns wider on the left than the halo, so that
+// each copy starts on a 16-byte boundary) and the tile's mask bytes.  Cells outside the grid
+// arrive as zeros; the ghost cells of a boundary tile (reflected, wrapped or negated copies of
+// grid nodes under the boundary rule) are gathered by plain loads.  Tiles of other slots fill the
+// free window with plain loads.
 // ---------------------------------------------------------------------------------------------
+constexpr int kWX = kStTileX + 8;                      // 72: window row, floats
+constexpr int kWinBytes = kWX * kHY * 4;               // one float window (z, then p; p_old)
+constexpr int kMaskBytes = kStTileX * kStTileY;        // the tile's mask
+constexpr int kBufBytes = 2 * kWinBytes + kMaskBytes;  // one window set
+static_assert(kWinBytes % 128 == 0 && kBufBytes % 128 == 0, "tensor copy destinations");
+constexpr int kGhostSlots = 4 * kHY + 4 * kHX;         // candidate ghost cells of one halo
+static_assert(kGhostSlots <= 2 * kStThreads, "two ghost candidates per thread");
+constexpr int kStBlocksPerSm = 4;
+
+// Candidate k of a tile's ghost cells: the four ghost columns (x = -2, -1, nx, nx+1) over the
+// halo's rows, then the four ghost rows over the halo's in-grid columns.  Returns false when the
+// candidate lies outside the halo or beyond the second ghost line; (wy, wx) is its window cell.
+__device__ __forceinline__ bool ghost_cell(const SlotDesc& S, int x0, int y0, int k, int& wy,
+                                           int& wx) {
+  if (k < 4 * kHY) {
+    const int j = k / kHY;
+    wy = k - j * kHY;
+    const int gx = j < 2 ? j - 2 : S.nx + (j - 2);
+    const int lx = gx - (x0 - 2);
+    wx = lx + 2;
+    return lx >= 0 && lx < kHX && y0 - 2 + wy <= S.ny + 1;
+  }
+  const int kk = k - 4 * kHY;
+  const int j = kk / kHX, lx = kk - j * kHX;
+  const int gy = j < 2 ? j - 2 : S.ny + (j - 2);
+  const int gx = x0 - 2 + lx;
+  wy = gy - (y0 - 2);
+  wx = lx + 2;
+  return wy >= 0 && wy < kHY && gx >= 0 && gx < S.nx;
+}
+
+// Thread 0: start the tensor copies of the block's next copied tile (the next item at or after
+// w_issue whose slot iterates and has stencil maps) into window set n_issued % 2.
+__device__ __forceinline__ void stencil_issue_next(const SlotDesc* __restrict__ slots,
+                                                   const WorkItem* __restrict__ items, int total,
+                                                   unsigned char (*sbuf)[kBufBytes],
+                                                   uint64_t* full, int& w_issue, int& n_issued) {
+  while (w_issue < total) {
+    const WorkItem it = items[w_issue];
+    w_issue += gridDim.x;
+    const SlotDesc& S = slots[it.slot];
+    if (S.st_maps == nullptr || !S.sc->active) continue;
+    int x0, y0;
+    tile_origin(S, it.tile, x0, y0);
+    const unsigned char* maps = static_cast<const unsigned char*>(S.st_maps);
+    const void* mz = maps;
+    const void* mp = maps + 128 * (1 + (S.sc->it & 1));
+    const void* mm = maps + 128 * 3;
+    tmap_acquire(mz);
+    tmap_acquire(mp);
+    tmap_acquire(mm);
+    const int b = n_issued & 1;
+    unsigned char* dst = sbuf[b];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&full[b], kBufBytes);
+    tma_load_2d(dst, mz, &full[b], x0 - 4, y0 - 2);
+    tma_load_2d(dst + kWinBytes, mp, &full[b], x0 - 4, y0 - 2);
+    tma_load_2d(dst + 2 * kWinBytes, mm, &full[b], x0, y0);
+    ++n_issued;
+    return;
+  }
+}
+
 template <bool ANISO>
-__global__ void __launch_bounds__(kStThreads)
+__global__ void __launch_bounds__(kStThreads, kStBlocksPerSm)
 k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
-          const int* __restrict__ n_items) {
-  __shared__ __align__(16) float sp[kHalo];
+          const int* __restrict__ n_items, int* __restrict__ err) {
+  __shared__ __align__(128) unsigned char sbuf[2][kBufBytes];
+  __shared__ __align__(8) uint64_t full[2];
   __shared__ double red[64];
+  __shared__ int s_abort;
   const int total = *n_items;
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  volatile int* abort_flag = &s_abort;
+  int w_issue = blockIdx.x, n_issued = 0;  // thread 0: the tensor-copy cursor
+  int n_used = 0;                          // copied windows consumed (uniform over the block)
+  if (threadIdx.x == 0) stencil_issue_next(slots, items, total, sbuf, full, w_issue, n_issued);
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem it = items[w];
     const SlotDesc& S = slots[it.slot];
@@ -247,63 +338,100 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     const float* __restrict__ z = S.z;
     int x0, y0;
     tile_origin(S, it.tile, x0, y0);
-    // a tile whose halo lies inside the grid needs no boundary rule
+    // a tile whose halo lies inside the grid has no ghost cell
     const bool interior =
         x0 >= 2 && y0 >= 2 && x0 + kStTileX + 2 <= S.nx && y0 + kStTileY + 2 <= S.ny;
-    // halo of p = z + beta p_old: gather every index first so all loads are in flight together
-    constexpr int kPer = (kHalo + kStThreads - 1) / kStThreads;
-    int gi[kPer];
-    float gs[kPer];
+    unsigned char* buf;
+    if (S.st_maps != nullptr) {
+      const int b = n_used & 1;
+      buf = sbuf[b];
+      // the other window set finished with the previous tile: start the next tile's copies
+      if (threadIdx.x == 0 && n_issued == n_used + 1)
+        stencil_issue_next(slots, items, total, sbuf, full, w_issue, n_issued);
+      // ghost cells by plain loads, issued before the wait so that both latencies overlap
+      int gcell[2] = {-1, -1};
+      float gz[2] = {0.f, 0.f}, gp[2] = {0.f, 0.f}, gs[2] = {0.f, 0.f};
+      if (!interior) {
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int i = threadIdx.x + j * kStThreads;
-      gs[j] = 0.f;
-      gi[j] = 0;
-      if (i < kHalo) {
-        if (interior) {
-          const int ly = i / kHX, lx = i - ly * kHX;
-          gi[j] = (y0 - 2 + ly) * S.nx + (x0 - 2 + lx);
-          gs[j] = 1.f;
-        } else {
-          gi[j] = halo_src(S, x0, y0, i, gs[j]);
+        for (int h = 0; h < 2; ++h) {
+          const int k = threadIdx.x + h * kStThreads;
+          int wy, wx;
+          if (k < kGhostSlots && ghost_cell(S, x0, y0, k, wy, wx)) {
+            float s;
+            const int g = halo_src(S, x0, y0, wy * kHX + (wx - 2), s);
+            if (s != 0.f) {  // zero-sign ghosts stay the zeros the copy filled in
+              gcell[h] = wy * kWX + wx;
+              gs[h] = s;
+              gz[h] = __ldg(z + g);
+              gp[h] = __ldg(pold + g);
+            }
+          }
         }
       }
-    }
-    float zv[kPer], pv[kPer];
-#pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      zv[j] = gs[j] != 0.f ? __ldg(z + gi[j]) : 0.f;
-      pv[j] = gs[j] != 0.f ? __ldg(pold + gi[j]) : 0.f;
-    }
-    // the mask of the thread's own nodes travels with the halo loads (one bit per node); the
-    // isotropic path owns node pairs (x, x+1), the anisotropic one single nodes
-    constexpr int kOwn = kStTileX * kStTileY / kStThreads;
-    static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn <= 32 && kOwn % 2 == 0,
-                  "tile / block size");
-    uint32_t mk = 0;
-#pragma unroll
-    for (int j = 0; j < kOwn; ++j) {
-      int ly, lx;
-      if (!ANISO) {
-        const int k = threadIdx.x + (j / 2) * kStThreads;  // pair index
-        ly = k / (kStTileX / 2);
-        lx = 2 * (k - ly * (kStTileX / 2)) + (j & 1);
-      } else {
-        const int k = threadIdx.x + j * kStThreads;
-        ly = k / kStTileX;
-        lx = k - ly * kStTileX;
+      mbar_wait(&full[b], (n_used >> 1) & 1, abort_flag);
+      // p = z + beta p_old over the whole window, in place of z
+      float4* zw = reinterpret_cast<float4*>(buf);
+      const float4* pw = reinterpret_cast<const float4*>(buf + kWinBytes);
+      for (int v = threadIdx.x; v < kWX * kHY / 4; v += kStThreads) {
+        const float4 a = zw[v], c = pw[v];
+        zw[v] = make_float4(__fmaf_rn(beta, c.x, a.x), __fmaf_rn(beta, c.y, a.y),
+                            __fmaf_rn(beta, c.z, a.z), __fmaf_rn(beta, c.w, a.w));
       }
-      const int gx = x0 + lx, gy = y0 + ly;
-      if (gx < S.nx && gy < S.ny && S.mask[gy * S.nx + gx]) mk |= 1u << j;
-    }
+      __syncthreads();
+      if (*abort_flag) break;  // every thread reads the flag after the barrier: uniform
+      ++n_used;
+      if (!interior) {
+        float* wf = reinterpret_cast<float*>(buf);
 #pragma unroll
-    for (int j = 0; j < kPer; ++j) {
-      const int i = threadIdx.x + j * kStThreads;
-      if (i < kHalo) sp[i] = gs[j] * __fmaf_rn(beta, pv[j], zv[j]);
+        for (int h = 0; h < 2; ++h)
+          if (gcell[h] >= 0) wf[gcell[h]] = gs[h] * __fmaf_rn(beta, gp[h], gz[h]);
+        __syncthreads();
+      }
+    } else {
+      // plain loads into the free window set, kChunk cells per thread in flight at a time
+      buf = sbuf[(n_used + 1) & 1];
+      float* wf = reinterpret_cast<float*>(buf);
+      uint8_t* mt = buf + 2 * kWinBytes;
+      for (int e = threadIdx.x; e < kMaskBytes; e += kStThreads) {
+        const int ly = e / kStTileX, lx = e - ly * kStTileX;
+        const int gx = x0 + lx, gy = y0 + ly;
+        mt[e] = (gx < S.nx && gy < S.ny) ? S.mask[gy * S.nx + gx] : 0;
+      }
+      constexpr int kChunk = 4;
+#pragma unroll 1
+      for (int i0 = 0; i0 < kHalo; i0 += kChunk * kStThreads) {
+        int gi[kChunk];
+        float gsg[kChunk], zv[kChunk], pv[kChunk];
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const int i = i0 + threadIdx.x + j * kStThreads;
+          gsg[j] = 0.f;
+          gi[j] = 0;
+          if (i < kHalo) gi[j] = halo_src(S, x0, y0, i, gsg[j]);
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          zv[j] = gsg[j] != 0.f ? __ldg(z + gi[j]) : 0.f;
+          pv[j] = gsg[j] != 0.f ? __ldg(pold + gi[j]) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+          const int i = i0 + threadIdx.x + j * kStThreads;
+          if (i < kHalo) {
+            const int ly = i / kHX, lx = i - ly * kHX;
+            wf[ly * kWX + lx + 2] = gsg[j] * __fmaf_rn(beta, pv[j], zv[j]);
+          }
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
+    const float* wf = reinterpret_cast<const float*>(buf);
+    const uint8_t* mt = buf + 2 * kWinBytes;
+    constexpr int kOwn = kStTileX * kStTileY / kStThreads;
+    static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn % 2 == 0, "tile / block size");
     CompDot dot;
     if (!ANISO) {
+      // node pairs (x, x+1): the window's row stride is even and x - x0 is even
 #pragma unroll 1
       for (int j = 0; j < kOwn / 2; ++j) {
         const int k = threadIdx.x + j * kStThreads;
@@ -311,18 +439,27 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= S.nx || gy >= S.ny) continue;
         const int g = gy * S.nx + gx;
-        const float* c = sp + (ly + 2) * kHX + lx + 2;
+        const float* c = wf + (ly + 2) * kWX + lx + 4;
         const float2 pv = ld2(c);
-        const float2 q2 = ((mk >> (2 * j)) & 3u) ? stencil13_pair(c) : make_float2(0.f, 0.f);
-        const float q0 = ((mk >> (2 * j)) & 1u) ? q2.x : 0.f;
-        const float q1 = ((mk >> (2 * j + 1)) & 1u) ? q2.y : 0.f;
-        pnew[g] = pv.x;
-        S.q[g] = q0;
+        const unsigned m2 = *reinterpret_cast<const uint16_t*>(mt + ly * kStTileX + lx);
+        const float2 q2 = m2 ? stencil13_pair<kWX>(c) : make_float2(0.f, 0.f);
+        const float q0 = (m2 & 0xffu) ? q2.x : 0.f;
+        const float q1 = (m2 >> 8) ? q2.y : 0.f;
         dot.add(pv.x, q0);
         if (gx + 1 < S.nx) {
-          pnew[g + 1] = pv.y;
-          S.q[g + 1] = q1;
           dot.add(pv.y, q1);
+          if ((g & 1) == 0) {
+            *reinterpret_cast<float2*>(pnew + g) = pv;
+            *reinterpret_cast<float2*>(S.q + g) = make_float2(q0, q1);
+          } else {
+            pnew[g] = pv.x;
+            pnew[g + 1] = pv.y;
+            S.q[g] = q0;
+            S.q[g + 1] = q1;
+          }
+        } else {
+          pnew[g] = pv.x;
+          S.q[g] = q0;
         }
       }
     } else {
@@ -333,9 +470,9 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= S.nx || gy >= S.ny) continue;
         const int g = gy * S.nx + gx;
-        const float pv = sp[(ly + 2) * kHX + lx + 2];
+        const float pv = wf[(ly + 2) * kWX + lx + 4];
         float qv = 0.f;
-        if ((mk >> j) & 1u) qv = stencil13<ANISO>(S, sp, ly, lx);
+        if (mt[ly * kStTileX + lx]) qv = stencil13<ANISO, kWX>(S, wf + 2, ly, lx);
         pnew[g] = pv;
         S.q[g] = qv;
         dot.add(pv, qv);
@@ -343,7 +480,16 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     }
     const double pq = block_sum_comp<kStThreads>(dot, red);
     if (threadIdx.x == 0) S.part[it.tile * 4 + 1] = pq;  // reduced by k_pq_finish
-    __syncthreads();
+    __syncthreads();  // the window set is free for the copies started at the next copied tile
+  }
+  if (threadIdx.x == 0) {
+    // copies still in flight (only after an abort) land before the block's memory is released
+    for (int o = n_used; o < n_issued; ++o) {
+      const long long t0 = clock64();
+      while (!mbar_try(&full[o & 1], (o >> 1) & 1) && clock64() - t0 < kWaitCycles / 4) {
+      }
+    }
+    if (s_abort) atomicExch(err, 1);
   }
 }
 
@@ -643,9 +789,18 @@ void launch_setup(const LaunchCfg& c, const float* const* phis, const float* con
 void launch_rhs_scale(const LaunchCfg& c) {
   k_rhs_scale<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
 }
-void launch_stencil(const LaunchCfg& c, bool aniso) {
-  if (aniso) k_stencil<true><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
-  else k_stencil<false><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
+void launch_stencil(const LaunchCfg& c, bool aniso, int* err) {
+  if (aniso) k_stencil<true><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, err);
+  else k_stencil<false><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, err);
+}
+int stencil_blocks_per_sm() { return kStBlocksPerSm; }
+cudaError_t stencil_init() {
+  // all of the SM's shared memory to the carveout, so that kStBlocksPerSm window pairs fit
+  cudaError_t e = cudaFuncSetAttribute(k_stencil<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  const cudaError_t e2 = cudaFuncSetAttribute(k_stencil<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                              cudaSharedmemCarveoutMaxShared);
+  return e != cudaSuccess ? e : e2;
 }
 void launch_pq_finish(const LaunchCfg& c) {
   k_pq_finish<<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items);
