@@ -172,7 +172,7 @@ def test_solve_small_all_boundaries(ext, ctx, ctx_tight, bc_x, bc_y, direction):
     _check_solution(ext, ctx, ctx_tight, p)
 
 
-@pytest.mark.parametrize("n", [64, 97, 130, 256])
+@pytest.mark.parametrize("n", [64, 97, 130, 256])  # 64, 256: tensor-copy stencil windows
 def test_solve_circle_symmetric(ext, ctx, ctx_tight, n):
     _check_solution(ext, ctx, ctx_tight, synth.circle(n))
 
@@ -186,8 +186,9 @@ def test_solve_wobbly_batch_member(ext, ctx, ctx_tight):
     _check_solution(ext, ctx, ctx_tight, synth.wobbly(192, 3))
 
 
-def test_solve_anisotropic(ext, ctx, ctx_tight):
-    X, Y, hx, hy = synth.grid(60, 90, "symmetric", "periodic")
+@pytest.mark.parametrize("nx", [60, 64])  # plain-load and tensor-copy stencil windows
+def test_solve_anisotropic(ext, ctx, ctx_tight, nx):
+    X, Y, hx, hy = synth.grid(nx, 90, "symmetric", "periodic")
     hy = hy * 0.7
     phi = (np.sqrt(X ** 2 + Y ** 2) - 0.5).astype(np.float32)
     f = (np.sin(2 * X + Y)).astype(np.float32)
