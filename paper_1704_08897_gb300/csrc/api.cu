@@ -112,7 +112,7 @@ struct ext_ctx {
   std::map<std::string, Workspace*> ws;
   std::mutex api_mu;  // serialises ext_solve* and the serving worker on the stream
   bool tc = false;    // mixed modes: tensor-core preconditioner
-  int split = 0;      // 0 = FP16 hi/lo, 1 = BF16 hi/mid/lo
+  int split = 0;      // type of the exact integer operand slices: 0 = FP16, 1 = BF16
   int* d_err = nullptr;   // device flag raised by a bounded wait that ran out
   int* h_err = nullptr;   // pinned copy
   // launch accounting and optional per-kernel timing (ext_options.profile)
@@ -228,8 +228,8 @@ static int make_stencil_maps(CUtensorMap (&m)[4], const SlotDesc& d) {
                       CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
-// Three integer slices of v for block exponent E (v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24)),
-// stored as FP16 or BF16 (integers of at most 9 bits are exact in both).
+// ns integer slices of v for block exponent E (v = c0 2^(E-8) + c1 2^(E-16) + ... +
+// c_{ns-1} 2^(E-8 ns)), stored as FP16 or BF16 (integers of at most 9 bits are exact in both).
 static void slice_host(double v, int E, int split, int ns, uint16_t* out, size_t plane, size_t idx) {
   double r = v;
   for (int k = 0; k < ns; ++k) {

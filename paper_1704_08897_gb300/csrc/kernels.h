@@ -44,10 +44,10 @@ void launch_apply(const SlotDesc* slot, int n_tiles, bool aniso, const float* p,
 // mode 2: every slot (verification entry point).
 void launch_prec_simt(const LaunchCfg& c, int stage, int mode);
 
-// tensor-core variant (kernels_gemm_tc.cu): FP16 hi/lo (split_kind 0) or BF16 hi/mid/lo
-// (split_kind 1) operand planes; err receives 1 if a bounded wait ran out.
+// tensor-core variant (kernels_gemm_tc.cu): exact block-scaled integer slice planes stored as
+// FP16 (split_kind 0) or BF16 (split_kind 1); err receives 1 if a bounded wait ran out.
 void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int* err);
-// residual -> scaled planes of the first stage's A operand (vector work list)
+// residual -> integer slice planes of the first stage's A operand (stencil tile work list)
 void launch_prec_tc_prepare(const LaunchCfg& c, int mode, int split_kind);
 int tc_planes(int split_kind);
 int tc_block();

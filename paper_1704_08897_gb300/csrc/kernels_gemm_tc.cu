@@ -359,7 +359,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               // every pb, since the order accumulators are adjacent in TMEM the same way
               const uint64_t ad = sdesc(sa + pa * A_PLANE) + 2 * j;
               const uint64_t bd = sdesc(sb) + 2 * j;
-              // the first MMA of an accumulation block (pa = 0) starts all three orders afresh
+              // the first MMA of an accumulation block (pa = 0) starts all NS orders afresh
               umma(dset + pa * BN, ad, bd, idesc_f16(BF16, BM, (NS - pa) * BN),
                    (half_kb > 0 || j > 0 || pa > 0) ? 1u : 0u);
             }
