@@ -217,7 +217,7 @@ static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint
 // tile.  The mask rows must span a multiple of 16 bytes (nx % 16 == 0).
 static bool stencil_copies_fit(int nx) { return nx % 16 == 0; }
 static int make_stencil_maps(CUtensorMap (&m)[4], const SlotDesc& d) {
-  const uint32_t wx = kStTileX + 8, wy = kStTileY + 4;
+  const uint32_t wx = kStWinX, wy = kStWinY;
   float* const vec[3] = {d.z, d.p[0], d.p[1]};
   for (int k = 0; k < 3; ++k) {
     const int rc = make_tmap_2d(&m[k], vec[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.nx, d.ny, wx, wy,

@@ -15,6 +15,11 @@ constexpr int kPad = 128;           // transform buffers are padded to multiples
 constexpr int kStTileX = 64;        // stencil tile (x contiguous)
 constexpr int kStTileY = 32;
 constexpr int kStThreads = 256;
+// The stencil's shared-memory window of one tile (also the box of its tensor copies): the halo
+// rows y0-2 .. y0+kStTileY+1 and the columns x0-4 .. x0+kStTileX+3, two columns wider on the
+// left than the halo so that a copy starts on a 16-byte boundary.
+constexpr int kStWinX = kStTileX + 8;
+constexpr int kStWinY = kStTileY + 4;
 constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels
 constexpr int kVecThreads = 256;
 

@@ -242,7 +242,8 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
 // grid nodes under the boundary rule) are gathered by plain loads.  Tiles of other slots fill the
 // free window with plain loads.
 // ---------------------------------------------------------------------------------------------
-constexpr int kWX = kStTileX + 8;                      // 72: window row, floats
+constexpr int kWX = kStWinX;                           // 72: window row, floats
+static_assert(kStWinY == kHY, "the window spans the halo rows");
 constexpr int kWinBytes = kWX * kHY * 4;               // one float window (z, then p; p_old)
 constexpr int kMaskBytes = kStTileX * kStTileY;        // the tile's mask
 constexpr int kBufBytes = 2 * kWinBytes + kMaskBytes;  // one window set
