@@ -200,6 +200,15 @@ int ext_rhs(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float
 int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float* phi,
                              const float* r, float* z, double* scale);
 
+/* Transform basis of one axis, computed on the host (no GPU, no context): the dense orthonormal
+ * eigenvector matrix of the axis's 1-D negative second difference T (h = 1) that the fast Poisson
+ * preconditioner applies (Algorithm 1: sine transform for Dirichlet edges; Example 1: cosine
+ * transform, DCT-II, for symmetric edges; Example 2: real Fourier basis for periodic edges), and
+ * its eigenvalues.  Q (n*n doubles, row-major: Q[i*n + k] is the k-th eigenvector at node i) and
+ * lam (n doubles, lam[k] its eigenvalue) are caller-owned host arrays; T = Q diag(lam) Q^T.
+ * Returns EXT_OK, or EXT_EINVAL for n < 4, n > 32768, an unknown bc or a NULL array. */
+int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam);
+
 /* ---- operator apply that allocates nothing ----
  *
  * Same result as ext_apply_biharmonic (q = M L^2 p, and the FP64 sum p.q into *sum_pq, which may

@@ -954,6 +954,14 @@ const char* ext_strerror(int code) {
 
 const char* ext_last_error(void) { return g_last_error.c_str(); }
 
+int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam) {
+  if (n < 4 || n > 32768 || bc < 0 || bc > 2 || !Q || !lam) return EXT_EINVAL;
+  const AxisBasis B = make_axis_basis(n, bc);
+  std::copy(B.Q.begin(), B.Q.end(), Q);
+  std::copy(B.lam.begin(), B.lam.end(), lam);
+  return EXT_OK;
+}
+
 int ext_create(const ext_options* opt, void* cuda_stream, ext_ctx** out) {
   if (!out) return EXT_EINVAL;
   *out = nullptr;

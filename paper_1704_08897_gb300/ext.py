@@ -29,7 +29,7 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_poll", "ext_drain", "ext_destroy", "ext_strerror", "ext_last_error",
             "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
             "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
-            "ext_noalloc_last_error"]
+            "ext_noalloc_last_error", "ext_axis_basis"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
                 "pq_finish"]
@@ -113,6 +113,8 @@ def load():
     lib.ext_apply_biharmonic_noalloc.restype = I
     lib.ext_noalloc_last_error.argtypes = []
     lib.ext_noalloc_last_error.restype = C.c_char_p
+    lib.ext_axis_basis.argtypes = [C.c_int32, I, P, P]
+    lib.ext_axis_basis.restype = I
     _lib = lib
     return lib
 
@@ -274,6 +276,17 @@ def ext_apply_biharmonic_noalloc(prob, phi, p, q, stream=None, check=True):
     if check and rc != EXT_OK:
         raise ExtError(rc, "ext_apply_biharmonic_noalloc: " + load().ext_noalloc_last_error().decode())
     return rc, s.value
+
+
+def ext_axis_basis(n, bc):
+    """(Q, lam) of one axis's transform basis, computed by the library on the host (no GPU):
+    Q[i, k] is the k-th orthonormal eigenvector of the axis's negative second difference at node i,
+    lam[k] its eigenvalue (h = 1)."""
+    Q = np.empty((int(n), int(n)), np.float64)
+    lam = np.empty(int(n), np.float64)
+    _check(load().ext_axis_basis(int(n), BC[bc] if isinstance(bc, str) else int(bc), _ptr(Q),
+                                 _ptr(lam)), "ext_axis_basis")
+    return Q, lam
 
 
 def ext_profile_read(ctx, reset=True):
