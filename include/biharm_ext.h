@@ -209,6 +209,16 @@ int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float*
  * Returns EXT_OK, or EXT_EINVAL for n < 4, n > 32768, an unknown bc or a NULL array. */
 int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam);
 
+/* The tensor-core operand form of the same basis, computed on the host (no GPU, no context): Q
+ * and Q^T, zero-padded to np x np (np = n rounded up to a multiple of 128), each row cut into
+ * blocks of 128 columns and each block with exponent E into four exact integer slices,
+ * v = c0 2^(E-8) + c1 2^(E-16) + c2 2^(E-24) + c3 2^(E-32) + (rest below 2^(E-33)), |c0| <= 255,
+ * |c1|, |c2|, |c3| <= 128.  codes (caller-owned, 8 np^2 words): [Q slices 0..3][Q^T slices 0..3],
+ * each slice an [np][np] row-major plane of the integers c_k as FP16 (type 0) or BF16 (type 1)
+ * bit patterns; exps (caller-owned, 2 np^2/128 bytes): [Q rows][Q^T rows], each [np][np/128].
+ * Returns EXT_OK, or EXT_EINVAL for n < 4, n > 32768, an unknown bc or type, or a NULL array. */
+int ext_axis_slices(int32_t n, ext_bc bc, int32_t type, uint16_t* codes, int8_t* exps);
+
 /* ---- operator apply that allocates nothing ----
  *
  * Same result as ext_apply_biharmonic (q = M L^2 p, and the FP64 sum p.q into *sum_pq, which may

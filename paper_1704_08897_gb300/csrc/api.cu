@@ -252,21 +252,18 @@ static int block_exp_host(const double* v, size_t stride, int count) {
   return std::max(e, -90);
 }
 
-// Q and Q^T of one axis as block-scaled slices (zero-padded to np x np) with their exponents:
-// [Q slices (NS planes)][Q^T slices (NS planes)][exponents of Q rows][exponents of Q^T rows].
-static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
-  if (P->tc && P->tc_split == ctx->split) return EXT_OK;
-  if (P->tc) {
-    cudaFree(P->tc);
-    P->tc = nullptr;
-  }
-  const int NS = tc_planes(ctx->split);
+// Q and Q^T of one axis (n nodes, rule bc) as block-scaled slices, zero-padded to np x np, with
+// their exponents: h = [Q slices (NS planes)][Q^T slices (NS planes)], each plane [np][np];
+// ex = [exponents of Q rows][exponents of Q^T rows], each [np][np / KB].
+static void slice_plan_host(int n, int bc, int np, int split, std::vector<uint16_t>& h,
+                            std::vector<int8_t>& ex) {
+  const int NS = tc_planes(split);
   const int KB = tc_block();  // k per block exponent of the sliced operands
-  const int np = P->np, n = P->n, nkb = np / KB;
+  const int nkb = np / KB;
   const size_t plane = (size_t)np * np;
-  std::vector<uint16_t> h(2 * NS * plane, 0);
-  std::vector<int8_t> ex(2 * (size_t)np * nkb, 0);
-  AxisBasis B = make_axis_basis(n, P->bc);
+  h.assign(2 * NS * plane, 0);
+  ex.assign(2 * (size_t)np * nkb, 0);
+  AxisBasis B = make_axis_basis(n, bc);
   std::vector<double> Qp((size_t)np * np, 0.0), QTp((size_t)np * np, 0.0);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
@@ -283,9 +280,20 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
         const int E = block_exp_host(blk, 1, KB);
         eo[(size_t)row * nkb + kb] = (int8_t)E;
         for (int k = 0; k < KB; ++k)
-          slice_host(blk[k], E, ctx->split, NS, out, plane, (size_t)row * np + kb * KB + k);
+          slice_host(blk[k], E, split, NS, out, plane, (size_t)row * np + kb * KB + k);
       }
   }
+}
+
+static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
+  if (P->tc && P->tc_split == ctx->split) return EXT_OK;
+  if (P->tc) {
+    cudaFree(P->tc);
+    P->tc = nullptr;
+  }
+  std::vector<uint16_t> h;
+  std::vector<int8_t> ex;
+  slice_plan_host(P->n, P->bc, P->np, ctx->split, h, ex);
   const size_t bytes = 2 * h.size() + ex.size();
   if (cudaMalloc(&P->tc, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -953,6 +961,17 @@ const char* ext_strerror(int code) {
 }
 
 const char* ext_last_error(void) { return g_last_error.c_str(); }
+
+int ext_axis_slices(int32_t n, ext_bc bc, int32_t type, uint16_t* codes, int8_t* exps) {
+  if (n < 4 || n > 32768 || bc < 0 || bc > 2 || (type != 0 && type != 1) || !codes || !exps)
+    return EXT_EINVAL;
+  std::vector<uint16_t> h;
+  std::vector<int8_t> ex;
+  slice_plan_host(n, bc, pad_to(n, kPad), type, h, ex);
+  std::copy(h.begin(), h.end(), codes);
+  std::copy(ex.begin(), ex.end(), exps);
+  return EXT_OK;
+}
 
 int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam) {
   if (n < 4 || n > 32768 || bc < 0 || bc > 2 || !Q || !lam) return EXT_EINVAL;

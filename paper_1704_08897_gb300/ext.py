@@ -29,7 +29,7 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_poll", "ext_drain", "ext_destroy", "ext_strerror", "ext_last_error",
             "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
             "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
-            "ext_noalloc_last_error", "ext_axis_basis"]
+            "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
                 "pq_finish"]
@@ -115,6 +115,8 @@ def load():
     lib.ext_noalloc_last_error.restype = C.c_char_p
     lib.ext_axis_basis.argtypes = [C.c_int32, I, P, P]
     lib.ext_axis_basis.restype = I
+    lib.ext_axis_slices.argtypes = [C.c_int32, I, C.c_int32, P, P]
+    lib.ext_axis_slices.restype = I
     _lib = lib
     return lib
 
@@ -287,6 +289,19 @@ def ext_axis_basis(n, bc):
     _check(load().ext_axis_basis(int(n), BC[bc] if isinstance(bc, str) else int(bc), _ptr(Q),
                                  _ptr(lam)), "ext_axis_basis")
     return Q, lam
+
+
+def ext_axis_slices(n, bc, type_="bf16"):
+    """(codes, exps) of one axis's basis in tensor-core operand form, computed by the library on
+    the host (no GPU): codes [2, 4, np, np] uint16 (Q then Q^T; four slices; FP16 or BF16 bit
+    patterns of integers), exps [2, np, np // 128] int8 block exponents; np = n rounded up to 128."""
+    np_ = (int(n) + 127) // 128 * 128
+    codes = np.empty((2, 4, np_, np_), np.uint16)
+    exps = np.empty((2, np_, np_ // 128), np.int8)
+    t = {"fp16": 0, "bf16": 1}[type_] if isinstance(type_, str) else int(type_)
+    _check(load().ext_axis_slices(int(n), BC[bc] if isinstance(bc, str) else int(bc), t,
+                                  codes.ctypes.data, exps.ctypes.data), "ext_axis_slices")
+    return codes, exps
 
 
 def ext_profile_read(ctx, reset=True):

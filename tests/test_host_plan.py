@@ -55,3 +55,47 @@ def test_axis_basis_rejects_bad_arguments(ext):
         rc = ext.load().ext_axis_basis(n, bc, Q.ctypes.data, lam.ctypes.data)
         assert rc == ext.EXT_EINVAL, (n, bc)
     assert ext.load().ext_axis_basis(8, 0, None, None) == ext.EXT_EINVAL
+
+
+def _decode(codes, type_):
+    if type_ == "fp16":
+        return codes.view(np.float16).astype(np.float64)
+    return (codes.astype(np.uint32) << 16).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("type_", ["fp16", "bf16"])
+@pytest.mark.parametrize("bc", ob.BCS)
+@pytest.mark.parametrize("n", [4, 100, 128, 200])
+def test_axis_slices_are_exact_block_scaled_integers(ext, type_, bc, n):
+    """The tensor-core operand form of Q and Q^T: four integer slices per 128-wide block of a
+    row, |c0| <= 255 and |c1..c3| <= 128 (exact in FP16 and BF16), reproduce every entry to
+    2^(E-33) of its block's scale, and the padding is zero."""
+    codes, exps = ext.ext_axis_slices(n, bc, type_)
+    Q, _ = ext.ext_axis_basis(n, bc)
+    npad = codes.shape[-1]
+    assert npad % 128 == 0 and npad - 128 < n <= npad
+    c = _decode(codes, type_)                       # [2, 4, np, np]
+    assert np.array_equal(c, np.round(c))           # integers
+    assert np.abs(c[:, 0]).max() <= 255 and np.abs(c[:, 1:]).max() <= 128
+    E = np.repeat(exps.astype(np.float64), 128, axis=2)  # [2, np, np] exponent of each entry
+    recon = sum(c[:, k] * np.exp2(E - 8 * (k + 1)) for k in range(4))
+    for t, M in enumerate((Q, Q.T)):
+        ref = np.zeros((npad, npad))
+        ref[:n, :n] = M
+        err = np.abs(recon[t] - ref)
+        assert np.all(err <= np.exp2(E[t] - 33)), (t, err.max())
+        # each block's largest entry sits in [2^(E-1), 2^E): the scale is the block's own
+        blk = np.abs(ref).reshape(npad, npad // 128, 128).max(axis=2)
+        e = exps[t].astype(np.float64)
+        nz = blk > 0
+        assert np.all(blk[nz] < np.exp2(e[nz])) and np.all(blk[nz] >= np.exp2(e[nz] - 2))
+    assert np.all(recon[:, n:, :] == 0) and np.all(recon[:, :, n:] == 0)
+
+
+def test_axis_slices_rejects_bad_arguments(ext):
+    codes = np.empty(8, np.uint16)
+    exps = np.empty(8, np.int8)
+    lib = ext.load()
+    for n, bc, t in ((3, 0, 1), (32769, 0, 1), (8, 3, 1), (8, 0, 2)):
+        assert lib.ext_axis_slices(n, bc, t, codes.ctypes.data, exps.ctypes.data) == ext.EXT_EINVAL
+    assert lib.ext_axis_slices(8, 0, 1, None, None) == ext.EXT_EINVAL
