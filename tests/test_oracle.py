@@ -302,3 +302,70 @@ def test_example1_errors_and_iterations_match_table1(bc):
         errs.append(err)
     order = np.log2(errs[0] / errs[1])
     assert 1.7 < order < 2.2
+
+
+# -------------------------------------------------------------------------------------------
+# Right-hand side on the full grid (Algorithm 1, first statement) and the residual measure
+# -------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("bc_x,bc_y", BC_PAIRS)
+@pytest.mark.parametrize("direction", ["out", "in"])
+def test_rhs_padded_equals_system_rhs_on_integers(bc_x, bc_y, direction):
+    """rhs_padded (Algorithm 1's padded two-pass stencil on the grid) scattered against b of the
+    assembled system (Kronecker construction, restricted to the unknowns): two independent routes
+    to -R L^2 E_K f.  With h = 1 and integer f both are exact integers, so they agree bit for bit;
+    known nodes hold zero."""
+    nx, ny = 13, 11
+    phi, _ = _random_problem(nx, ny, 17)
+    if direction == "in":
+        phi = -phi
+    f = np.random.default_rng(5).integers(-300, 301, (ny, nx)).astype(np.float64)
+    A, b, unk, known = ob.system(phi, f, direction, bc_x, bc_y)
+    B = ob.rhs_padded(phi, f, direction, bc_x, bc_y)
+    full = np.zeros(nx * ny)
+    full[unk] = b
+    assert np.array_equal(B.ravel(), full)
+    assert np.all(B[known] == 0)
+    # the sign: for one known node of value 1 in the interior, b at its edge neighbour is +8
+    # (minus the -8 coefficient of eq. discrete_biharmonic)
+    phi1 = np.ones((9, 9)) * (1.0 if direction == "out" else -1.0)
+    phi1[4, 4] = -phi1[4, 4]
+    f1 = np.zeros((9, 9))
+    f1[4, 4] = 1.0
+    B1 = ob.rhs_padded(phi1, f1, direction, bc_x, bc_y)
+    assert B1[4, 5] == 8.0 and B1[5, 5] == -2.0 and B1[4, 6] == -1.0 and B1[4, 4] == 0.0
+
+
+def test_rhs_padded_anisotropic_matches_system():
+    phi, f = _random_problem(10, 7, 23)
+    hx, hy = 0.4, 0.9
+    A, b, unk, known = ob.system(phi, f, "out", "periodic", "dirichlet", hx, hy)
+    B = ob.rhs_padded(phi, f, "out", "periodic", "dirichlet", hx, hy)
+    np.testing.assert_allclose(B.ravel()[unk], b, rtol=1e-13, atol=1e-12 * np.abs(b).max())
+
+
+@pytest.mark.parametrize("bc_x,bc_y", BC_PAIRS)
+def test_true_relative_residual_against_dense_brute_force(bc_x, bc_y):
+    """true_relative_residual is ||b - A x|| / ||b|| on the unknowns.  The reference builds A and
+    b densely from the 13-point tap table (a construction the function does not use), and a
+    planted residual pins the value: x = x* + A^-1 v has residual exactly -v."""
+    nx, ny = 12, 10
+    phi, f = _random_problem(nx, ny, 41, frac=0.5)
+    known = ob.known_mask(phi, "out")
+    L2 = ob.squared_laplacian_stencil(nx, ny, bc_x, bc_y).toarray()
+    unk = np.flatnonzero(~known.ravel())
+    Ad = L2[np.ix_(unk, unk)]
+    bd = -(L2 @ np.where(known, f, 0.0).ravel())[unk]
+    xs = np.linalg.solve(Ad, bd)
+    rng = np.random.default_rng(7)
+    v = rng.standard_normal(unk.size) * 1e-3 * np.linalg.norm(bd) / np.sqrt(unk.size)
+    x = xs + np.linalg.solve(Ad, v)
+    out = ob.assemble(x, f, unk, known)
+    got = ob.true_relative_residual(out, phi, f, "out", bc_x, bc_y)
+    want = np.linalg.norm(v) / np.linalg.norm(bd)
+    assert abs(got - want) <= 1e-9 * want
+    # values at known nodes of `out` are not part of the measure
+    out2 = out.copy()
+    out2[known] += 123.0
+    assert ob.true_relative_residual(out2, phi, f, "out", bc_x, bc_y) == got
+    # the exact solution has a residual at round-off level
+    assert ob.true_relative_residual(ob.assemble(xs, f, unk, known), phi, f, "out", bc_x, bc_y) < 1e-12
