@@ -185,8 +185,10 @@ int ext_solve_f64(ext_ctx* ctx, const ext_problem* prob, const float* phi, const
 
 /* q = M L^2 p on the full grid (eq. discrete_biharmonic with the boundary rules), M zeroing the
  * known nodes picked by phi; p must be zero at known nodes for this to be A p (Algorithm 1,
- * matvec).  Uses the same compensated kernel as the solver.  sum_pq (host, may be NULL)
- * receives the FP64 dot p.q. */
+ * matvec).  Runs the solver's own stencil kernel as at iteration 0 with beta = 0 and z = p, so q
+ * is bit for bit what a solve computes for that direction.  phi, p and q are device pointers
+ * (host pointers return EXT_EINVAL).  sum_pq (host, may be NULL) receives the dot p.q (FP64 sum
+ * of the kernel's compensated per-tile partials). */
 int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi,
                          const float* p, float* q, double* sum_pq);
 
@@ -222,17 +224,19 @@ int ext_axis_slices(int32_t n, ext_bc bc, int32_t type, uint16_t* codes, int8_t*
 /* ---- operator apply that allocates nothing ----
  *
  * Same result as ext_apply_biharmonic (q = M L^2 p, and the FP64 sum p.q into *sum_pq, which may
- * be NULL), for callers that cannot allocate device memory when they need it: code running inside
- * a stream capture in global mode (cudaMalloc is refused there), latency-critical loops where
- * cudaMalloc/cudaFree would synchronise the device, and hosts that own the whole device-memory
- * budget.  The paper has no counterpart; this is a property of the library, not of the method.
- * No context is needed.  phi, p and q are device pointers, [ny][nx] float32; the call runs on
- * cuda_stream (NULL = the default stream) and returns after that stream has finished its work.
+ * be NULL), for callers that cannot allocate device memory when they need it: host applications
+ * that reserve the whole device-memory budget up front and forbid libraries from taking more, and
+ * latency-critical loops in which cudaMalloc/cudaFree would synchronise the device.  The paper has
+ * no counterpart; this is a property of the library, not of the method.
+ * No context is needed.  phi, p and q are device pointers, [ny][nx] float32 (host pointers return
+ * EXT_EINVAL); the call runs on cuda_stream (NULL = the legacy default stream) and returns after
+ * that stream has finished its work.
  * Scratch: one fixed 2 MiB array per device (grids up to 1,048,576 nodes and 32,768 stencil
  * tiles of 64x32; larger grids return EXT_EINVAL, see ext_noalloc_last_error).  The first call on
- * a device looks up that array's device address; make that first call before any stream capture.
- * All calls on a device share the array: calls whose GPU work overlaps race and must be
- * serialised by the caller.  Nothing in it needs to start at zero. */
+ * a device looks up that array's device address (a lookup that allocates nothing); make that first
+ * call before any stream capture.  The looked-up address is kept for the life of the process and
+ * does not survive cudaDeviceReset.  All calls on a device share the array: calls whose GPU work
+ * overlaps race and must be serialised by the caller.  Nothing in it needs to start at zero. */
 int ext_apply_biharmonic_noalloc(const ext_problem* prob, const float* phi, const float* p,
                                  float* q, double* sum_pq, void* cuda_stream);
 

@@ -14,6 +14,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -131,7 +132,7 @@ struct ext_ctx {
 // ---------------------------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------------------------
-static int validate(const ext_problem* p) {
+int bx::validate_problem(const ext_problem* p) {
   if (!p) return EXT_EINVAL;
   if (p->nx < 4 || p->ny < 4) return EXT_EINVAL;
   if ((int64_t)p->nx * p->ny > (int64_t)1 << 30) return EXT_EINVAL;
@@ -142,7 +143,8 @@ static int validate(const ext_problem* p) {
   return EXT_OK;
 }
 
-static bool is_device_ptr(const void* p) {
+bool bx::is_device_ptr(const void* p) {
+  if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -1050,7 +1052,7 @@ int ext_solve_batch(ext_ctx* ctx, int count, const ext_problem* probs, const flo
   bool any_host = false, any_dev = false;
   std::vector<int> dirs(count);
   for (int i = 0; i < count; ++i) {
-    int rc = validate(&probs[i]);
+    int rc = validate_problem(&probs[i]);
     if (rc) return rc;
     if (!phi[i] || !f[i] || !out[i]) return EXT_EINVAL;
     const bool d = is_device_ptr(phi[i]) && is_device_ptr(f[i]) && is_device_ptr(out[i]);
@@ -1076,7 +1078,7 @@ int ext_solve_f64(ext_ctx* ctx, const ext_problem* prob, const float* phi, const
                   double* out64, ext_result* res) {
   if (!ctx || !prob || !phi || !f || !out64) return EXT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->api_mu);
-  int rc = validate(prob);
+  int rc = validate_problem(prob);
   if (rc) return rc;
   if (!is_device_ptr(phi) || !is_device_ptr(f) || !is_device_ptr(out64)) return EXT_EINVAL;
   Workspace* W = nullptr;
@@ -1111,9 +1113,9 @@ int64_t ext_launch_count(ext_ctx* ctx) { return ctx ? ctx->launches.load() : 0; 
 
 static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
                         Workspace** Wout) {
-  int rc = validate(prob);
+  int rc = validate_problem(prob);
   if (rc) return rc;
-  if (!phi || !f) return EXT_EINVAL;
+  if (!is_device_ptr(phi) || !is_device_ptr(f)) return EXT_EINVAL;
   Workspace* W = nullptr;
   rc = get_workspace(ctx, 1, prob, false, &W);
   if (rc) return rc;
@@ -1142,23 +1144,43 @@ static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi,
 
 int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* p,
                          float* q, double* sum_pq) {
-  if (!ctx || !p || !q) return EXT_EINVAL;
+  if (!ctx || !is_device_ptr(p) || !is_device_ptr(q)) return EXT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->api_mu);
   Workspace* W = nullptr;
   int rc = single_setup(ctx, prob, phi, p, &W);
   if (rc) return rc;
   SlotHost& sl = W->slots[0];
-  timed(ctx, EXT_KERNEL_STENCIL, [&] {
-    launch_apply(W->d_slots, sl.d.n_st_tiles, W->aniso, p, q, sl.d.part, ctx->stream);
-  });
+  cudaStream_t s = ctx->stream;
+  const size_t N = (size_t)prob->nx * prob->ny;
+  // The solver's own stencil kernel at iteration 0 with beta = 0 and z = p: it forms
+  // p_new = z + 0 * p_old = p in its window (the set-up zeroed p_old), q = M L^2 p_new and the
+  // per-tile p.q partials, through the same tensor-copy or plain-load window path as in a solve.
+  BX_CUDA(cudaMemcpyAsync(sl.d.z, p, 4 * N, cudaMemcpyDeviceToDevice, s));
+  const int it0 = 0, on = 1;
+  const double zero = 0.0;
+  char* dsc = reinterpret_cast<char*>(W->d_sc);
+  BX_CUDA(cudaMemcpyAsync(dsc + offsetof(SlotScalars, it), &it0, sizeof(int), cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(dsc + offsetof(SlotScalars, active), &on, sizeof(int), cudaMemcpyHostToDevice, s));
+  BX_CUDA(cudaMemcpyAsync(dsc + offsetof(SlotScalars, beta), &zero, sizeof(double), cudaMemcpyHostToDevice, s));
+  LaunchCfg sc = cfg_of(ctx, W, 0);
+  sc.grid = std::max(1, std::min(W->n_st, ctx->sm_count * stencil_blocks_per_sm()));
+  timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, ctx->d_err); });
   BX_CUDA(cudaGetLastError());
-  std::vector<double> part(sl.d.n_st_tiles);
-  BX_CUDA(cudaMemcpyAsync(part.data(), sl.d.part, 8 * part.size(), cudaMemcpyDeviceToHost, ctx->stream));
-  BX_CUDA(cudaStreamSynchronize(ctx->stream));
+  BX_CUDA(cudaMemcpyAsync(q, sl.d.q, 4 * N, cudaMemcpyDeviceToDevice, s));
+  std::vector<double> part(4 * (size_t)sl.d.n_st_tiles);
+  BX_CUDA(cudaMemcpyAsync(part.data(), sl.d.part, 8 * part.size(), cudaMemcpyDeviceToHost, s));
+  BX_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BX_CUDA(cudaStreamSynchronize(s));
+  if (*ctx->h_err) {
+    BX_CUDA(cudaMemsetAsync(ctx->d_err, 0, sizeof(int), s));
+    BX_CUDA(cudaStreamSynchronize(s));
+    g_last_error = "a bounded device wait (stencil tensor copy) ran out";
+    return EXT_ETIMEOUT;
+  }
   if (sum_pq) {
-    double s = 0.0;
-    for (double v : part) s += v;
-    *sum_pq = s;
+    double acc = 0.0;
+    for (int t = 0; t < sl.d.n_st_tiles; ++t) acc += part[4 * (size_t)t + 1];
+    *sum_pq = acc;
   }
   return EXT_OK;
 }
@@ -1585,7 +1607,7 @@ extern "C" {
 int ext_submit(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f, float* out,
                uint64_t* ticket) {
   if (!ctx || !prob || !phi || !f || !out || !ticket) return EXT_EINVAL;
-  int rc = validate(prob);
+  int rc = validate_problem(prob);
   if (rc) return rc;
   const bool dev = is_device_ptr(phi) && is_device_ptr(f) && is_device_ptr(out);
   const bool host = !is_device_ptr(phi) && !is_device_ptr(f) && !is_device_ptr(out);

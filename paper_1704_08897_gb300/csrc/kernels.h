@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include "../../include/biharm_ext.h"
 #include "common.cuh"
 
 namespace bx {
@@ -15,8 +16,12 @@ struct LaunchCfg {
   cudaStream_t stream;
 };
 
-// host helper (api.cu): stencil weights of (L_y (+) L_x)^2 for spacings hx, hy
+// host helpers (api.cu): stencil weights of (L_y (+) L_x)^2 for spacings hx, hy; the problem
+// checks every entry point applies (EXT_OK or EXT_EINVAL); whether a pointer is device (or
+// managed) memory that kernels may dereference
 void set_weights(SlotDesc& d, double hx, double hy);
+int validate_problem(const ext_problem* p);
+bool is_device_ptr(const void* p);
 
 // grid kernels (kernels_grid.cu)
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,

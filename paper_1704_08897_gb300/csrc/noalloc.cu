@@ -1,19 +1,22 @@
 // Operator apply without any device allocation.
 //
-// Some callers cannot allocate device memory at the moment they need the operator: code that runs
-// while a stream is being captured in global capture mode (where cudaMalloc is refused), hot loops
-// in which cudaMalloc/cudaFree would synchronise the device and stall other streams, and host
-// applications that own the whole device-memory budget and forbid libraries from taking more.
-// For them, ext_apply_biharmonic_noalloc computes the same q = M L^2 p as ext_apply_biharmonic
-// with every byte of scratch (slot descriptor, known-node mask, per-tile partial sums) taken from
-// one file-scope device array of fixed size, and without creating a context.
+// Some callers cannot allocate device memory at the moment they need the operator: host
+// applications that reserve the whole device-memory budget up front and forbid libraries from
+// taking more (a simulation code that owns its memory pool, or a process sharing the GPU under a
+// fixed quota), and hot loops in which a cudaMalloc/cudaFree pair would synchronise the device and
+// stall every other stream.  For them, ext_apply_biharmonic_noalloc computes the same
+// q = M L^2 p as ext_apply_biharmonic with every byte of scratch (slot descriptor, known-node
+// mask, per-tile partial sums) taken from one file-scope device array of fixed size, and without
+// creating a context.
 //
 // Limits and sharing: grids of at most kNoAllocMaxNodes nodes and kNoAllocMaxTiles stencil tiles.
 // The array exists once per device that loads the library and lives until the process exits.
 // All calls on a device share it and it keeps the previous call's contents; every byte a call
 // reads is written earlier in that same call, so nothing has to start at zero.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on the array and must
-// be serialised by the caller.
+// be serialised by the caller.  The array's device address is looked up once per device, by the
+// first call made with that device current; that first call should come before any stream
+// capture, and the cached address does not survive cudaDeviceReset (the module is loaded anew).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -74,16 +77,22 @@ extern "C" int ext_apply_biharmonic_noalloc(const ext_problem* prob, const float
                                             const float* p, float* q, double* sum_pq,
                                             void* cuda_stream) {
   if (!prob || !phi || !p || !q) return EXT_EINVAL;
-  if (prob->nx < 4 || prob->ny < 4 || !(prob->hx > 0.0) || !(prob->hy > 0.0) ||
-      prob->bc_x < 0 || prob->bc_x > 2 || prob->bc_y < 0 || prob->bc_y > 2 ||
-      (prob->dir != 0 && prob->dir != 1))
+  if (validate_problem(prob) != EXT_OK) {
+    g_noalloc_err = "invalid problem (sizes below 4 or above 2^30 nodes, spacing not finite and "
+                    "positive, unknown boundary rule or direction)";
     return EXT_EINVAL;
+  }
   const int64_t n = (int64_t)prob->nx * prob->ny;
-  const int64_t tiles = (int64_t)((prob->nx + kStTileX - 1) / kStTileX) *
-                        ((prob->ny + kStTileY - 1) / kStTileY);
+  const int64_t tiles = ((int64_t)prob->nx + kStTileX - 1) / kStTileX *
+                        (((int64_t)prob->ny + kStTileY - 1) / kStTileY);
   if (n > kNoAllocMaxNodes || tiles > kNoAllocMaxTiles) {
     g_noalloc_err = "grid too large for the fixed no-allocation scratch (at most 1048576 nodes "
                     "and 32768 stencil tiles of 64x32)";
+    return EXT_EINVAL;
+  }
+  // the kernels dereference phi, p and q: device (or managed) memory only
+  if (!is_device_ptr(phi) || !is_device_ptr(p) || !is_device_ptr(q)) {
+    g_noalloc_err = "phi, p and q must be device pointers";
     return EXT_EINVAL;
   }
   // Once per device, with that device current: the device address of the scratch array.

@@ -269,11 +269,23 @@ def ext_apply_preconditioner(ctx, prob, phi, r, z):
     return s.value
 
 
+def _stream_of(stream, *arrays):
+    """Raw stream handle: the given torch stream or handle; by default torch's current stream on
+    the arrays' device (so the call is ordered after work the caller queued there), else NULL."""
+    if stream is not None:
+        return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    for a in arrays:
+        if getattr(a, "is_cuda", False):
+            import torch
+            return torch.cuda.current_stream(a.device).cuda_stream
+    return None
+
+
 def ext_apply_biharmonic_noalloc(prob, phi, p, q, stream=None, check=True):
     """q = M L^2 p without any device allocation (fixed per-device scratch; see the header).
-    Returns (rc, sum p.q)."""
+    Returns (rc, sum p.q).  Runs on ``stream`` (default: torch's current stream)."""
     s = C.c_double()
-    st = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    st = _stream_of(stream, phi, p, q)
     rc = load().ext_apply_biharmonic_noalloc(C.byref(prob), _ptr(phi), _ptr(p), _ptr(q), C.byref(s), st)
     if check and rc != EXT_OK:
         raise ExtError(rc, "ext_apply_biharmonic_noalloc: " + load().ext_noalloc_last_error().decode())

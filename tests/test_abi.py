@@ -60,3 +60,24 @@ def test_library_loads_and_binding_resolves(lib_path):
     assert ext.strerror(ext.EXT_ENOKNOWN).startswith("no known node")
     o = ext.options()
     assert o.rtol == 1e-8 and o.true_res_every == 200 and o.replace_factor == 1e-2 and o.prec == ext.PREC["fp32"]
+
+
+def test_host_arrays_are_rejected_where_kernels_read_them(lib_path):
+    """Entry points whose kernels dereference the caller's arrays accept device memory only: host
+    (numpy) arrays return EXT_EINVAL before any launch, so a host pointer never reaches a kernel.
+    Runs without a GPU (the pointer query fails, which also reads as not-device)."""
+    import numpy as np
+
+    from paper_1704_08897_gb300 import ext
+    ext.load()
+    phi = np.ones((16, 16), np.float32)
+    p = np.zeros((16, 16), np.float32)
+    q = np.zeros((16, 16), np.float32)
+    rc, _ = ext.ext_apply_biharmonic_noalloc(ext.problem(16, 16), phi, p, q, check=False)
+    assert rc == ext.EXT_EINVAL
+    assert "device" in ext.load().ext_noalloc_last_error().decode()
+    # invalid problems are refused by the same checks the context entry points apply
+    for bad in (ext.problem(16, 16, hx=float("inf")), ext.problem(3, 16),
+                ext.problem(16, 16, hx=float("nan"))):
+        rc, _ = ext.ext_apply_biharmonic_noalloc(bad, phi, p, q, check=False)
+        assert rc == ext.EXT_EINVAL

@@ -1,12 +1,12 @@
 """The operator apply that allocates nothing gives what the context-based entry point gives.
 
 ext_apply_biharmonic_noalloc exists for callers that may not allocate device memory when they
-need the operator (inside a stream capture in global mode, in loops where cudaMalloc/cudaFree
-would synchronise the device, or under a host that owns the whole memory budget).  Its scratch is
+need the operator: a host application that owns the whole device-memory budget, or a loop in
+which cudaMalloc/cudaFree would synchronise the device.  Its scratch is
 one fixed array per device, shared by every call, so the test makes two calls in a row with
-different grids and checks each against ext_apply_biharmonic: q bit for bit (same kernel on the
-same inputs) and the FP64 sum p.q to 1e-12 relative (the two sum the per-tile partials in a
-different order).  This file is collected last; it also passes when run alone.
+different grids and checks each against ext_apply_biharmonic: q bit for bit (both evaluate the
+same compensated 13-point sum, term by term in the same order) and the sum p.q to 1e-10 relative
+(one sums FP64 per-tile partials, the other the solver stencil's compensated FP32 partials).  This file is collected last; it also passes when run alone.
 """
 
 import numpy as np
@@ -45,7 +45,7 @@ def test_noalloc_apply_matches_context_apply_on_two_calls():
             rc, s = ext.ext_apply_biharmonic_noalloc(prob, phi_d, p_d, q)
             assert rc == ext.EXT_OK
             assert torch.equal(q, q_ref)
-            assert abs(s - s_ref) <= 1e-12 * abs(s_ref)
+            assert abs(s - s_ref) <= 1e-10 * abs(s_ref)
     finally:
         ext.ext_destroy(ctx)
 
