@@ -110,12 +110,13 @@ def algorithmic_cost(probs, kind):
         for p in probs:
             fl += 2 * p.nx * p.ny * (p.nx if s in (0, 2) else p.ny)
         return fl, "flop"
-    if kind == "stencil":   # read z, p_old, mask; write p, q
-        return sum(17 * p.nx * p.ny for p in probs), "byte"
-    if kind == "update":    # read xhat(8), p, q, r; write xhat(8), r
-        return sum(32 * p.nx * p.ny for p in probs), "byte"
-    if kind == "split":     # read r; write four 16-bit slices
-        return sum(12 * p.nx * p.ny for p in probs), "byte"
+    # CG vectors are double-float pairs of FP32 planes: 8 bytes per node each
+    if kind == "stencil":   # read z, p_old (8 + 8), mask (1); write p, q (8 + 8)
+        return sum(33 * p.nx * p.ny for p in probs), "byte"
+    if kind == "update":    # read x, p, q, r; write x, r (8 bytes each)
+        return sum(48 * p.nx * p.ny for p in probs), "byte"
+    if kind == "split":     # read r (8); write four 16-bit slices (8)
+        return sum(16 * p.nx * p.ny for p in probs), "byte"
     return None, None
 
 
@@ -276,21 +277,46 @@ def run_ours(args, rank, world):
     nodes = sum(p.nx * p.ny for p in probs)
     pt_its = sum(p.nx * p.ny * r["iters"] for p, r in zip(probs, results))
 
-    # the plain FP32 single-solve path on a sample of the same grids (the comparison the batched
-    # and served paths are measured against)
-    plain = None
-    if args.workload != "single":
+    # the same sample of the workload's grids through the four combinations of path and launch
+    # (FP32 / mixed, one ext_solve per grid / one ext_solve_batch), so that the gain of batching
+    # and the gain of the tensor-core preconditioner are reported separately; the plain FP32
+    # single-solve path is the comparison the batched and served paths are measured against
+    plain, same_grids, sample_answers, sample_iters = None, None, {}, {}
+    if args.workload != "single" and args.plain_sample > 0:
         k = min(args.plain_sample, len(probs))
-        pctx = ext.ext_create(ext.options("fp32", rtol=1e-8, maxit=maxit), stream=stream)
-        ext.ext_solve(pctx, dprobs[0], phis[0], fs[0], outs[0], check=False)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for j in range(k):
-            ext.ext_solve(pctx, dprobs[j], phis[j], fs[j], outs[j], check=False)
-        torch.cuda.synchronize()
-        el = time.perf_counter() - t0
-        ext.ext_destroy(pctx)
-        plain = {"value": round(k / el, 4), "unit": "solves/s", "sample": f"first {k} grids of the workload, one ext_solve each, FP32 path"}
+        same_grids = {"sample": f"first {k} grids of the workload", "grids": k}
+        for pname in ("fp32", "mixed_bf16"):
+            cctx = ext.ext_create(ext.options(pname, rtol=1e-8, maxit=maxit), stream=stream)
+            for mode in ("single", "batched"):
+                # warm: plans and workspaces of these shapes
+                if mode == "single":
+                    for j in range(k):
+                        ext.ext_solve(cctx, dprobs[j], phis[j], fs[j], outs[j], check=False)
+                else:
+                    ext.ext_solve_batch(cctx, dprobs[:k], phis[:k], fs[:k], outs[:k], check=False)
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if mode == "single":
+                    rr = [ext.ext_solve(cctx, dprobs[j], phis[j], fs[j], outs[j], check=False)
+                          for j in range(k)]
+                else:
+                    _, rr = ext.ext_solve_batch(cctx, dprobs[:k], phis[:k], fs[:k], outs[:k],
+                                                check=False)
+                e1.record(stream)
+                e1.synchronize()
+                el = e0.elapsed_time(e1) / 1e3
+                its = [r["iters"] for r in rr]
+                same_grids[f"{pname}_{mode}"] = {
+                    "value": round(k / el, 4), "unit": "solves/s",
+                    "iterations_median": statistics.median(its),
+                    "all_converged": all(r["rc"] == 0 if "rc" in r else r["status"] == 0 for r in rr)}
+                sample_answers[f"{pname}_{mode}"] = [o.cpu().numpy() for o in outs[:k]]
+                sample_iters[f"{pname}_{mode}"] = its
+            ext.ext_destroy(cctx)
+        plain = dict(same_grids["fp32_single"],
+                     sample=f"first {k} grids of the workload, one ext_solve each, FP32 path")
 
     # end to end through the public API with host (pinned) buffers
     e2e = None
@@ -395,13 +421,14 @@ def run_ours(args, rank, world):
                           parallelism="replicas" if world > 1 else "single"),
            "iterations": iters if len(iters) <= 4 else
            {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},
+           "iterations_per_grid": iters[:32],
            "grid_point_iterations_per_s": round(pt_its * args.steps * world / (total_ms / 1e3), 1),
            "relres_true_max": max(r["relres_true"] for r in results),
            "all_converged": all(r.get("status", 0) == 0 for r in results),
-           "plain_fp32_single_solve": plain, "serving": serving,
+           "plain_fp32_single_solve": plain, "same_grids": same_grids, "serving": serving,
            "e2e": e2e, "roofline": roofline, "hbm_kernels": kernels_hbm, "kernels": kernels,
            "gpu_launches": launches, "clocks": clk}
-    return out, probs, answers
+    return out, probs, answers, (sample_answers, sample_iters)
 
 
 def oracle_solve(p):
@@ -429,28 +456,6 @@ def cpu_baseline(args, probs, budget_s=30.0):
             "host_cores_available": os.cpu_count()}, refs
 
 
-def accuracy_solve(probs, prec, rtol, count=32):
-    """One warm and one timed batched solve of the workload at a tighter tolerance; returns its
-    solves/s and the answers of the first `count` problems."""
-    import torch
-
-    from paper_1704_08897_gb300 import ext
-    maxit = 40 * max(max(p.nx, p.ny) for p in probs)
-    ctx = ext.ext_create(ext.options(prec, rtol=rtol, maxit=maxit))
-    dprobs = [ext.problem_of(p) for p in probs]
-    phis = [torch.from_numpy(p.phi).cuda() for p in probs]
-    fs = [torch.from_numpy(p.f).cuda() for p in probs]
-    outs = [torch.empty_like(x) for x in phis]
-    ext.ext_solve_batch(ctx, dprobs, phis, fs, outs, check=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ext.ext_solve_batch(ctx, dprobs, phis, fs, outs, check=False)
-    torch.cuda.synchronize()
-    el = time.perf_counter() - t0
-    ext.ext_destroy(ctx)
-    return len(probs) / el, [o.cpu().numpy() for o in outs[:count]]
-
-
 def error_vs_oracle(probs, answers, refs, prec, at="rel-res 1e-8, answers of the last timed step"):
     """Max-norm relative error (max over unknowns of |x - x*| / max |out*|) of the GPU answers
     of the timed run against the oracle's direct solves, over the problems the oracle solved."""
@@ -465,6 +470,28 @@ def error_vs_oracle(probs, answers, refs, prec, at="rel-res 1e-8, answers of the
     return {"max_rel": float(max(errs)), "median_rel": float(np.median(errs)),
             "problems": len(errs), "bound": bound, "within": bool(max(errs) <= bound),
             "at": at}
+
+
+def oracle_pcg_iterations(probs, batched_iters, sample_iters, count=3, budget_s=20.0):
+    """Iterations of the oracle's FP64 PCG (the same fast Poisson preconditioner and
+    Fletcher-Reeves beta, rel-res 1e-8) beside the GPU's on the first grids of the workload."""
+    import numpy as np
+
+    from oracle import biharmonic as ob
+    rows, t0 = [], time.perf_counter()
+    for j, p in enumerate(probs[:count]):
+        _, info = ob.extend(p.phi.astype(np.float64), p.f.astype(np.float64), p.direction, p.bc_x,
+                            p.bc_y, p.hx, p.hy, method="pcg", rtol=1e-8)
+        row = {"grid": f"{p.nx}x{p.ny}", "oracle_fp64_pcg": info["iters"]}
+        if batched_iters is not None and j < len(batched_iters):
+            row["timed_run"] = batched_iters[j]
+        for key, its in sample_iters.items():
+            if j < len(its):
+                row[key] = its[j]
+        rows.append(row)
+        if time.perf_counter() - t0 > budget_s:
+            break
+    return rows
 
 
 def run_reference(args, rank, world):
@@ -511,19 +538,19 @@ def main():
         import torch.distributed as dist
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
-    out, probs, answers = run_ours(args, rank, world)
+    out, probs, answers, (sample_answers, sample_iters) = run_ours(args, rank, world)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"], refs = cpu_baseline(args, probs)
             prec = out["config"]["prec"]
             acc = {"rtol_1e-08": error_vs_oracle(probs, answers, refs, prec)}
-            if args.workload == "batch":
-                # the FP32-vector iteration's error at rel-res 1e-8 scatters with the rounding
-                # history; the same batch solved to 5e-9, with its own throughput
-                sps, ans2 = accuracy_solve(probs, prec, 5e-9)
-                acc["rtol_5e-09"] = dict(error_vs_oracle(probs, ans2, refs, prec,
-                                                         at="rel-res 5e-9, one batched solve"),
-                                         solves_per_s=round(sps, 3))
+            # every path and launch of the same-grid comparison, against the same direct solves
+            for key, ans in sample_answers.items():
+                acc[f"rtol_1e-08_{key}"] = error_vs_oracle(
+                    probs, ans, refs, "fp32" if key.startswith("fp32") else "mixed",
+                    at=f"rel-res 1e-8, {key.replace('_', ' ')} answers of the same-grid sample")
+            out["iterations_vs_oracle_pcg"] = oracle_pcg_iterations(
+                probs, out.get("iterations_per_grid"), sample_iters)
             out["error_vs_oracle"] = acc
         print(json.dumps(out))
     if world > 1:

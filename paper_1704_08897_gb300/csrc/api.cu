@@ -54,8 +54,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct PlanDev {
   int n = 0, np = 0, bc = 0;
-  float* q = nullptr;   // [np][np]
-  float* qt = nullptr;  // [np][np]
+  float* q = nullptr;   // [2][np][np]: hi plane, lo plane
+  float* qt = nullptr;  // [2][np][np]
   std::vector<double> lam;
   void* tc = nullptr;   // tensor-core operand planes: [Q planes][Q^T planes], 2-byte elements
   int tc_split = -1;
@@ -214,19 +214,19 @@ static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint
                       inner, rows, 64, box_rows, CU_TENSOR_MAP_SWIZZLE_128B);
 }
 
-// Stencil windows: z, p[0], p[1] as FP32 boxes of the tile plus its halo (two extra columns on
-// the left keep each copy's start on a 16-byte boundary) and the mask as 8-bit boxes of the
-// tile.  The mask rows must span a multiple of 16 bytes (nx % 16 == 0).
+// Stencil windows: the hi and lo planes of z, p[0], p[1] as FP32 boxes of the tile plus its halo
+// (two extra columns on the left keep each copy's start on a 16-byte boundary) and the mask as
+// 8-bit boxes of the tile.  The mask rows must span a multiple of 16 bytes (nx % 16 == 0).
 static bool stencil_copies_fit(int nx) { return nx % 16 == 0; }
-static int make_stencil_maps(CUtensorMap (&m)[4], const SlotDesc& d) {
+static int make_stencil_maps(CUtensorMap (&m)[kStMaps], const SlotDesc& d) {
   const uint32_t wx = kStWinX, wy = kStWinY;
-  float* const vec[3] = {d.z, d.p[0], d.p[1]};
-  for (int k = 0; k < 3; ++k) {
+  float* const vec[6] = {d.z, d.z_lo, d.p[0], d.p_lo[0], d.p[1], d.p_lo[1]};
+  for (int k = 0; k < 6; ++k) {
     const int rc = make_tmap_2d(&m[k], vec[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.nx, d.ny, wx, wy,
                                 CU_TENSOR_MAP_SWIZZLE_NONE);
     if (rc) return rc;
   }
-  return make_tmap_2d(&m[3], d.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.nx, d.ny, kStTileX, kStTileY,
+  return make_tmap_2d(&m[6], d.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.nx, d.ny, kStTileX, kStTileY,
                       CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
@@ -330,8 +330,8 @@ static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {
   P.np = pad_to(n, kPad);
   P.lam = B.lam;
   std::vector<float> q, qt;
-  padded_f32(B, P.np, q, qt);
-  const size_t bytes = (size_t)P.np * P.np * sizeof(float);
+  padded_df(B, P.np, q, qt);
+  const size_t bytes = 2 * (size_t)P.np * P.np * sizeof(float);
   if (cudaMalloc(&P.q, bytes) != cudaSuccess || cudaMalloc(&P.qt, bytes) != cudaSuccess) {
     cudaGetLastError();
     g_last_error = "cudaMalloc of transform plan failed";
@@ -435,13 +435,16 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   const size_t o_part = take(8 * 4 * (size_t)n_part);
   const size_t o_r = take(4 * N), o_p0 = take(4 * N), o_p1 = take(4 * N);
   const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
-  const size_t fp = ctx->tc ? 0 : 4 * Np;  // SIMT transform intermediates
+  const size_t o_rl = take(4 * N), o_p0l = take(4 * N), o_p1l = take(4 * N);
+  const size_t o_ql = take(4 * N), o_zl = take(4 * N);
+  const size_t fp = ctx->tc ? 0 : 4 * Np;  // SIMT transform intermediates (hi, lo planes)
   const size_t o_t1 = take(fp), o_t2 = take(fp), o_t3 = take(fp);
+  const size_t o_t1l = take(fp), o_t2l = take(fp), o_t3l = take(fp);
   const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
   size_t o_io = 0;
   if (host_io) o_io = take(12 * N);
   const bool st_copy = stencil_copies_fit(nx);
-  const size_t o_smaps = st_copy ? take(4 * sizeof(CUtensorMap)) : 0;
+  const size_t o_smaps = st_copy ? take(kStMaps * sizeof(CUtensorMap)) : 0;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
   size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0;
   const size_t nex = Np / 64;  // block exponents of one operand
@@ -473,15 +476,22 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.p[1] = (float*)(A + o_p1);
   d.q = (float*)(A + o_q);
   d.z = (float*)(A + o_z);
+  d.r_lo = (float*)(A + o_rl);
+  d.p_lo[0] = (float*)(A + o_p0l);
+  d.p_lo[1] = (float*)(A + o_p1l);
+  d.q_lo = (float*)(A + o_ql);
+  d.z_lo = (float*)(A + o_zl);
   d.mask = (uint8_t*)(A + o_mask);
   d.t1 = (float*)(A + o_t1);
   d.t2 = (float*)(A + o_t2);
   d.t3 = (float*)(A + o_t3);
-  d.rin = nullptr;
+  d.t1_lo = (float*)(A + o_t1l);
+  d.t2_lo = (float*)(A + o_t2l);
+  d.t3_lo = (float*)(A + o_t3l);
   d.n_tc_tiles = n_gm;
   d.st_maps = nullptr;
   if (st_copy) {
-    CUtensorMap smaps[4];
+    CUtensorMap smaps[kStMaps];
     const int rc1 = make_stencil_maps(smaps, d);
     if (rc1) return rc1;
     BX_CUDA(cudaMemcpy(A + o_smaps, smaps, sizeof(smaps), cudaMemcpyHostToDevice));
@@ -1156,6 +1166,7 @@ int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi
   // p_new = z + 0 * p_old = p in its window (the set-up zeroed p_old), q = M L^2 p_new and the
   // per-tile p.q partials, through the same tensor-copy or plain-load window path as in a solve.
   BX_CUDA(cudaMemcpyAsync(sl.d.z, p, 4 * N, cudaMemcpyDeviceToDevice, s));
+  BX_CUDA(cudaMemsetAsync(sl.d.z_lo, 0, 4 * N, s));
   const int it0 = 0, on = 1;
   const double zero = 0.0;
   char* dsc = reinterpret_cast<char*>(W->d_sc);
@@ -1207,7 +1218,9 @@ int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float*
   SlotHost& sl = W->slots[0];
   const size_t N = (size_t)prob->nx * prob->ny;
   BX_CUDA(cudaMemcpyAsync(sl.d.r, r, 4 * N, cudaMemcpyDefault, ctx->stream));
+  BX_CUDA(cudaMemsetAsync(sl.d.r_lo, 0, 4 * N, ctx->stream));
   BX_CUDA(cudaMemsetAsync(sl.d.q, 0, 4 * N, ctx->stream));
+  BX_CUDA(cudaMemsetAsync(sl.d.q_lo, 0, 4 * N, ctx->stream));
   launch_prec(ctx, W, 2);
   BX_CUDA(cudaGetLastError());
   BX_CUDA(cudaMemcpyAsync(z, sl.d.z, 4 * N, cudaMemcpyDefault, ctx->stream));

@@ -20,6 +20,7 @@ constexpr int kStThreads = 256;
 // left than the halo so that a copy starts on a 16-byte boundary.
 constexpr int kStWinX = kStTileX + 8;
 constexpr int kStWinY = kStTileY + 4;
+constexpr int kStMaps = 7;          // stencil tensor maps per slot
 constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels
 constexpr int kVecThreads = 256;
 
@@ -65,21 +66,29 @@ struct SlotDesc {
   float wc_l, wex_l, wey_l, wd_l, wfx_l, wfy_l;  // low parts (anisotropic grids only)
   double dwc, dwex, dwey, dwd, dwfx, dwfy;       // FP64 weights for the true residual
   int aniso;
-  // grid vectors [ny][nx]
+  // grid vectors [ny][nx].  Every CG vector is a double-float pair v = hi + lo of FP32 planes
+  // (about 48 bits), updated with error-free FP32 transformations: with FP32 storage alone the
+  // rounding of any one of r, p, q, z costs this operator 60-100% more iterations.
   uint8_t* mask;     // 1 = unknown node
   double* b;
-  float* xhi;        // the iterate as a double-float pair x = xhi + xlo (about 48 bits),
-  float* xlo;        // updated every iteration with error-free FP32 transformations
-  float* r;
+  float* xhi;        // the iterate x = xhi + xlo
+  float* xlo;
+  float* r;          // hi planes ...
   float* p[2];
   float* q;
   float* z;
-  // transform operands and intermediates, padded [.][.] row-major, float32 (SIMT path)
-  float* rin;        // r scaled, padded [nyp][nxp]
+  float* r_lo;       // ... and their lo planes
+  float* p_lo[2];
+  float* q_lo;
+  float* z_lo;
+  // transform intermediates of the CUDA-core path, padded [.][.] row-major, double-float planes
   float* t1;         // [nxp][nyp]
   float* t2;         // [nyp][nxp]
   float* t3;         // [nxp][nyp]
-  const float* qx;   // [nxp][nxp]  Qx[x][k]
+  float* t1_lo;
+  float* t2_lo;
+  float* t3_lo;
+  const float* qx;   // [nxp][nxp]  Qx[x][k] (hi); the lo plane follows at + nxp * nxp
   const float* qxt;  // [nxp][nxp]  Qx^T
   const float* qy;
   const float* qyt;
@@ -95,8 +104,9 @@ struct SlotDesc {
   int8_t* tc_e[4];   // block exponents of the A operand of stage s: [rows][K/128]
   const int8_t* tc_eb[4];  // block exponents of the B operand of stage s (transform matrices)
   const void* tmaps; // 8 CUtensorMap (64-byte aligned): A operand of stages 0..3, B of 0..3
-  const void* st_maps;  // 4 CUtensorMap for the stencil's tensor copies (z, p[0], p[1], mask);
-                        // null when a mask row is not a multiple of 16 bytes
+  const void* st_maps;  // kStMaps CUtensorMap for the stencil's tensor copies (z, z_lo, p[0],
+                        // p_lo[0], p[1], p_lo[1], mask); null when a mask row is not a multiple
+                        // of 16 bytes
   int n_tc_tiles;    // output tiles of one tensor-core transform stage
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
@@ -264,16 +274,102 @@ __device__ __forceinline__ double block_sum_comp(CompDot d, double* sh) {
   return t;
 }
 
-// x (hi, lo) += a * p with error-free transformations; |lo| stays below half an ulp of hi.
-__device__ __forceinline__ void df_axpy(float& hi, float& lo, float a, float p) {
-  const float prod = __fmul_rn(a, p);
-  const float perr = __fmaf_rn(a, p, -prod);
-  float s, e;
-  two_sum(hi, prod, s, e);
-  const float t = __fadd_rn(__fadd_rn(lo, e), perr);
-  hi = __fadd_rn(s, t);
-  lo = __fsub_rn(t, __fsub_rn(hi, s));
+// ------------------------------------------------------------------------------------------
+// Double-float arithmetic (Dekker, Knuth): a value is an unevaluated FP32 pair hi + lo with
+// |lo| <= ulp(hi) / 2.  Sums use TwoSum, products the FMA-based TwoProd; cross terms of size
+// 2^-24 relative are added in plain FP32, so results carry about 48 bits.
+// ------------------------------------------------------------------------------------------
+// (s, e) -> normalised pair, valid when |e| is at most about ulp(s) (Fast2Sum)
+__device__ __forceinline__ f2 df_norm(float s, float e) {
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
 }
+__device__ __forceinline__ f2 df_add(f2 a, f2 b) {
+  float s, e;
+  two_sum(a.hi, b.hi, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  return df_norm(s, e);
+}
+// a * b for a double-float a and an FP32 b
+__device__ __forceinline__ f2 df_mul(f2 a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  float e = __fmaf_rn(a.hi, b, -p);
+  e = __fmaf_rn(a.lo, b, e);
+  return df_norm(p, e);
+}
+// a * b for double-float a and b
+__device__ __forceinline__ f2 df_mul(f2 a, f2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return df_norm(p, e);
+}
+// c + a * b, all double-float (one TwoProd, one TwoSum)
+__device__ __forceinline__ f2 df_fma(f2 a, f2 b, f2 c) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float pe = __fmaf_rn(a.hi, b.hi, -p);
+  pe = __fmaf_rn(a.hi, b.lo, pe);
+  pe = __fmaf_rn(a.lo, b.hi, pe);
+  float s, e;
+  two_sum(c.hi, p, s, e);
+  e = __fadd_rn(e, __fadd_rn(c.lo, pe));
+  return df_norm(s, e);
+}
+// an FP64 value as a double-float pair (host and device)
+__host__ __device__ __forceinline__ f2 df_of(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+// Packed FP32x2 forms of the same operations (two independent lanes, each rounded exactly as its
+// scalar counterpart).
+struct f2x2 { float2 hi, lo; };
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 neg2(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ f2x2 df_norm2(float2 s, float2 e) {
+  const float2 h = add2(s, e);
+  return {h, sub2(e, sub2(h, s))};
+}
+// z + beta * p for double-float z, p (two lanes) and a double-float scalar beta
+__device__ __forceinline__ f2x2 df_axpy2(f2 beta, f2x2 p, f2x2 z) {
+  const float2 bh = make_float2(beta.hi, beta.hi), bl = make_float2(beta.lo, beta.lo);
+  const float2 t = __fmul2_rn(bh, p.hi);
+  float2 te = fma2(bh, p.hi, neg2(t));
+  te = fma2(bh, p.lo, te);
+  te = fma2(bl, p.hi, te);
+  float2 s, e;
+  two_sum2(z.hi, t, s, e);
+  e = add2(e, add2(z.lo, te));
+  return df_norm2(s, e);
+}
+
+// x += a * p with double-float x, p and scalar a (TwoProd + TwoSum)
+__device__ __forceinline__ void df_axpy(float& xh, float& xl, f2 a, float ph, float pl) {
+  const f2 r = df_fma(a, f2{ph, pl}, f2{xh, xl});
+  xh = r.hi;
+  xl = r.lo;
+}
+
+// Compensated dot product of double-float vectors: hi * hi by TwoProd into a Sum2 accumulator,
+// the two cross terms (2^-24 relative) in plain FP32.
+struct CompDotDF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float ah, float al, float bh, float bl) {
+    const float p = __fmul_rn(ah, bh);
+    const float pe = __fmaf_rn(ah, bh, -p);
+    float e;
+    two_sum(s, p, s, e);
+    c = __fadd_rn(c, __fadd_rn(e, __fmaf_rn(ah, bl, __fmaf_rn(al, bh, pe))));
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+  __device__ __forceinline__ CompDot as_comp() const {
+    CompDot d;
+    d.s = s;
+    d.c = c;
+    return d;
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // Ghost-node maps of one axis (Algorithm 1 padding; symmetric = half-sample reflection;

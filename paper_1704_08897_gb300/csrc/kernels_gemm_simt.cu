@@ -1,5 +1,5 @@
-// Fast Poisson preconditioner of Sec. 2.2 / Algorithm 1 as four dense transform products, FP32
-// on the CUDA cores (the plain path).
+// Fast Poisson preconditioner of Sec. 2.2 / Algorithm 1 as four dense transform products on the
+// CUDA cores in FP32 arithmetic (the plain path).
 //
 // z = M Q_y W Q_y^T (M r) Q_x W... written separably on the padded rectangle:
 //   stage 0: T1[kx][y]  = sum_x r[y][x]  Qx[x][kx]       (forward transform along x)
@@ -11,6 +11,14 @@
 // transposed (Out[n][m]) so the next stage again reads a k-contiguous operand.  The division by
 // the squared eigenvalue sums is fused into stage 1's epilogue, masking and the CG inner
 // products into stage 3's.
+//
+// Precision.  The weights span (64 / lambda_min)^2, so any rounding noise of the preconditioner
+// relative to |r| reappears amplified in the smooth modes of z, and CG pays for it in iterations;
+// FP32 products alone cost this operator about 3x the iterations of exact transforms.  Operands
+// and stage outputs are therefore double-float (hi, lo) planes, and each product is accumulated
+// by the compensated dot product of Ogita, Rump and Oishi (Dot2): TwoProd of the hi parts, a
+// TwoSum into the running sum, the error terms and the two hi x lo cross terms into a plain FP32
+// compensation.  The result carries about 48 bits.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -18,14 +26,16 @@ namespace bx {
 
 namespace {
 
-constexpr int BM = 128, BN = 64, BK = 16, NT = 256;
+constexpr int BM = 128, BN = 64, BK = 8, NT = 256;
 
 struct StageView {
-  const float* A;
+  const float* A;      // hi plane; the lo plane is A_lo
+  const float* A_lo;
   int lda, arows, acols;
-  const float* B;
+  const float* B;      // hi plane; the lo plane follows at B + ldb * ldb
   int ldb;
   float* out;
+  float* out_lo;
   int M, N, K;
 };
 
@@ -33,16 +43,16 @@ __device__ __forceinline__ StageView stage_view(const SlotDesc& S, int stage) {
   StageView v;
   switch (stage) {
     case 0:
-      v = {S.r, S.nx, S.ny, S.nx, S.qxt, S.nxp, S.t1, S.nyp, S.nxp, S.nxp};
+      v = {S.r, S.r_lo, S.nx, S.ny, S.nx, S.qxt, S.nxp, S.t1, S.t1_lo, S.nyp, S.nxp, S.nxp};
       break;
     case 1:
-      v = {S.t1, S.nyp, S.nxp, S.nyp, S.qyt, S.nyp, S.t2, S.nxp, S.nyp, S.nyp};
+      v = {S.t1, S.t1_lo, S.nyp, S.nxp, S.nyp, S.qyt, S.nyp, S.t2, S.t2_lo, S.nxp, S.nyp, S.nyp};
       break;
     case 2:
-      v = {S.t2, S.nxp, S.nyp, S.nxp, S.qx, S.nxp, S.t3, S.nyp, S.nxp, S.nxp};
+      v = {S.t2, S.t2_lo, S.nxp, S.nyp, S.nxp, S.qx, S.nxp, S.t3, S.t3_lo, S.nyp, S.nxp, S.nxp};
       break;
     default:
-      v = {S.t3, S.nyp, S.nxp, S.nyp, S.qy, S.nyp, nullptr, S.nxp, S.nyp, S.nyp};
+      v = {S.t3, S.t3_lo, S.nyp, S.nxp, S.nyp, S.qy, S.nyp, nullptr, nullptr, S.nxp, S.nyp, S.nyp};
       break;
   }
   return v;
@@ -54,13 +64,13 @@ template <int STAGE>
 __global__ void __launch_bounds__(NT)
 k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
             const int* __restrict__ n_items, int mode) {
-  __shared__ __align__(16) float As[2][BK][BM + 4];
-  __shared__ __align__(16) float Bs[2][BK][BN + 4];
+  __shared__ __align__(16) float As[2][2][BK][BM + 4];  // [buffer][hi, lo][k][m]
+  __shared__ __align__(16) float Bs[2][2][BK][BN + 4];
   __shared__ double red[64];
   const int t = threadIdx.x;
   const int tx = t & 15, ty = t >> 4;
-  const int arow = t >> 1, acol = (t & 1) * 8;  // A tile 128 x 16: 8 per thread
-  const int brow = t >> 2, bcol = (t & 3) * 4;  // B tile  64 x 16: 4 per thread
+  const int arow = t >> 1, acol = (t & 1) * 4;  // A tile 128 x 8: 4 per thread and plane
+  const int brow = t >> 2, bcol = (t & 3) * 2;  // B tile  64 x 8: 2 per thread and plane
   const int total = *n_items;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem item = items[w];
@@ -72,37 +82,46 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
     const int mtiles = v.M / BM;
     const int m0 = (item.tile % mtiles) * BM;
     const int n0 = (item.tile / mtiles) * BN;
+    const float* B_lo = v.B + (size_t)v.ldb * v.ldb;
 
-    float ra[8], rb[4];
+    float ra[2][4], rb[2][2];
     auto load = [&](int k0) {
       const int am = m0 + arow, ak = k0 + acol;
       if (STAGE == 0) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          ra[j] = (am < v.arows && ak + j < v.acols) ? v.A[(size_t)am * v.lda + ak + j] : 0.f;
+        for (int j = 0; j < 4; ++j) {
+          const bool in = am < v.arows && ak + j < v.acols;
+          ra[0][j] = in ? v.A[(size_t)am * v.lda + ak + j] : 0.f;
+          ra[1][j] = in ? v.A_lo[(size_t)am * v.lda + ak + j] : 0.f;
+        }
       } else {
-        const float4* pa = reinterpret_cast<const float4*>(v.A + (size_t)am * v.lda + ak);
-        const float4 a0 = pa[0], a1 = pa[1];
-        ra[0] = a0.x; ra[1] = a0.y; ra[2] = a0.z; ra[3] = a0.w;
-        ra[4] = a1.x; ra[5] = a1.y; ra[6] = a1.z; ra[7] = a1.w;
+        const float4 a0 = *reinterpret_cast<const float4*>(v.A + (size_t)am * v.lda + ak);
+        const float4 a1 = *reinterpret_cast<const float4*>(v.A_lo + (size_t)am * v.lda + ak);
+        ra[0][0] = a0.x; ra[0][1] = a0.y; ra[0][2] = a0.z; ra[0][3] = a0.w;
+        ra[1][0] = a1.x; ra[1][1] = a1.y; ra[1][2] = a1.z; ra[1][3] = a1.w;
       }
-      const float4 b0 = *reinterpret_cast<const float4*>(v.B + (size_t)(n0 + brow) * v.ldb + k0 + bcol);
-      rb[0] = b0.x; rb[1] = b0.y; rb[2] = b0.z; rb[3] = b0.w;
+      const size_t bo = (size_t)(n0 + brow) * v.ldb + k0 + bcol;
+      const float2 b0 = *reinterpret_cast<const float2*>(v.B + bo);
+      const float2 b1 = *reinterpret_cast<const float2*>(B_lo + bo);
+      rb[0][0] = b0.x; rb[0][1] = b0.y;
+      rb[1][0] = b1.x; rb[1][1] = b1.y;
     };
     auto store = [&](int buf) {
 #pragma unroll
-      for (int j = 0; j < 8; ++j) As[buf][acol + j][arow] = ra[j];
+      for (int h = 0; h < 2; ++h) {
 #pragma unroll
-      for (int j = 0; j < 4; ++j) Bs[buf][bcol + j][brow] = rb[j];
+        for (int j = 0; j < 4; ++j) As[buf][h][acol + j][arow] = ra[h][j];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) Bs[buf][h][bcol + j][brow] = rb[h][j];
+      }
     };
 
-    // Each 16-term chunk of the k sum is accumulated in FP32 (c); chunks are merged into the
-    // (hi, lo) pair with an error-free TwoSum, so the sum's error does not grow with K.
-    float c[8][4], hi[8][4], lo[8][4];
+    // Dot2 accumulators of the thread's 8 x 4 outputs: running sum s and compensation c
+    float s[8][4], c[8][4];
 #pragma unroll
     for (int i = 0; i < 8; ++i)
 #pragma unroll
-      for (int j = 0; j < 4; ++j) { c[i][j] = 0.f; hi[i][j] = 0.f; lo[i][j] = 0.f; }
+      for (int j = 0; j < 4; ++j) { s[i][j] = 0.f; c[i][j] = 0.f; }
 
     const int nk = v.K / BK;
     load(0);
@@ -113,46 +132,51 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
       if (kt + 1 < nk) load((kt + 1) * BK);
 #pragma unroll
       for (int kk = 0; kk < BK; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][kk][ty * 4]);
-        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][kk][64 + ty * 4]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][kk][tx * 4]);
-        const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-        const float b[4] = {b0.x, b0.y, b0.z, b0.w};
+        const float4 a0 = *reinterpret_cast<const float4*>(&As[buf][0][kk][ty * 4]);
+        const float4 a1 = *reinterpret_cast<const float4*>(&As[buf][0][kk][64 + ty * 4]);
+        const float4 l0 = *reinterpret_cast<const float4*>(&As[buf][1][kk][ty * 4]);
+        const float4 l1 = *reinterpret_cast<const float4*>(&As[buf][1][kk][64 + ty * 4]);
+        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[buf][0][kk][tx * 4]);
+        const float4 bl = *reinterpret_cast<const float4*>(&Bs[buf][1][kk][tx * 4]);
+        const float ah[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+        const float al[8] = {l0.x, l0.y, l0.z, l0.w, l1.x, l1.y, l1.z, l1.w};
+        const float bh[4] = {b0.x, b0.y, b0.z, b0.w};
+        const float bo[4] = {bl.x, bl.y, bl.z, bl.w};
 #pragma unroll
         for (int i = 0; i < 8; ++i)
 #pragma unroll
-          for (int j = 0; j < 4; ++j) c[i][j] = fmaf(a[i], b[j], c[i][j]);
+          for (int j = 0; j < 4; ++j) {
+            const float p = __fmul_rn(ah[i], bh[j]);
+            const float pe = __fmaf_rn(ah[i], bh[j], -p);
+            float e;
+            two_sum(s[i][j], p, s[i][j], e);
+            c[i][j] = __fadd_rn(c[i][j], __fadd_rn(e, __fmaf_rn(ah[i], bo[j], __fmaf_rn(al[i], bh[j], pe))));
+          }
       }
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float e;
-          two_sum(hi[i][j], c[i][j], hi[i][j], e);
-          lo[i][j] = __fadd_rn(lo[i][j], e);
-          c[i][j] = 0.f;
-        }
       if (kt + 1 < nk) store(buf ^ 1);
       __syncthreads();
     }
 
-    // epilogue: element (m, n) of D goes to Out[n][m]
-    CompDot c_rz, c_zq;
+    // epilogue: element (m, n) of D goes to Out[n][m] as a normalised double-float pair
+    CompDotDF c_rz, c_zq;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int n = n0 + tx * 4 + j;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int mb = m0 + h * 64 + ty * 4;
-        float o[4];
+        f2 o[4];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) o[i] = __fadd_rn(hi[h * 4 + i][j], lo[h * 4 + i][j]);
+        for (int i = 0; i < 4; ++i) o[i] = df_norm(s[h * 4 + i][j], c[h * 4 + i][j]);
         if (STAGE == 1) {
 #pragma unroll
-          for (int i = 0; i < 4; ++i) o[i] *= spectral_weight(S, mb + i, n);
+          for (int i = 0; i < 4; ++i) o[i] = df_mul(o[i], spectral_weight(S, mb + i, n));
         }
         if (STAGE <= 2) {
-          *reinterpret_cast<float4*>(v.out + (size_t)n * v.M + mb) = make_float4(o[0], o[1], o[2], o[3]);
+          *reinterpret_cast<float4*>(v.out + (size_t)n * v.M + mb) =
+              make_float4(o[0].hi, o[1].hi, o[2].hi, o[3].hi);
+          *reinterpret_cast<float4*>(v.out_lo + (size_t)n * v.M + mb) =
+              make_float4(o[0].lo, o[1].lo, o[2].lo, o[3].lo);
         } else {
           const int y = n;
           if (y < S.ny) {
@@ -161,10 +185,11 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
               const int x = mb + i;
               if (x < S.nx) {
                 const int g = y * S.nx + x;
-                const float zv = S.mask[g] ? o[i] : 0.f;
-                S.z[g] = zv;
-                c_rz.add(S.r[g], zv);
-                c_zq.add(zv, S.q[g]);
+                const f2 zv = S.mask[g] ? o[i] : f2{0.f, 0.f};
+                S.z[g] = zv.hi;
+                S.z_lo[g] = zv.lo;
+                c_rz.add(S.r[g], S.r_lo[g], zv.hi, zv.lo);
+                c_zq.add(zv.hi, zv.lo, S.q[g], S.q_lo[g]);
               }
             }
           }

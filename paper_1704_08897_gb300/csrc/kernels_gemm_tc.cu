@@ -19,7 +19,8 @@
 //    a compensated (hi, lo) register pair, k-block after k-block, two columns per packed FP32x2
 //    operation.
 // The operands carry 32 bits relative to each 128-block's largest value and the products add no
-// error along K; only the stage output is rounded (to FP32, then sliced).  Three slices on
+// error along K; the stage outputs stay double-float (hi, lo) pairs and are sliced from them
+// directly, and the last stage writes z as a double-float pair.  Three slices on
 // 64-blocks (24 bits) cost this operator 30-80% more CG iterations than exact transforms; four on
 // 128-blocks come within 5-10% of them.  The writer of the next stage's operand computes its
 // block exponents with a four-warp maximum and stores the slices transposed (Out[n][m],
@@ -162,20 +163,24 @@ __device__ __forceinline__ int block_exp(float amax) {
   return max(e, -90);  // keeps 2^(32-E) and 2^(E-16-8d) normal
 }
 
-// The NS integer slices of a value for block exponent E, given s = 2^(8-E) and is = 2^(E-8)
-// (all the powers of two involved are normal for the exponents block_exp returns): every
-// product is exact, so each residual is the value minus the slices so far, rounded once; the last
-// slice is rounded to an integer.
-// Two values at once on packed FP32x2, each lane with its own block factors; the slices' 16-bit
-// codes are returned as (lane x, lane y) pairs.
+// The NS integer slices of double-float values (hi, lo) for block exponent E, given s = 2^(8-E) and
+// is = 2^(E-8) (all the powers of two involved are normal for the exponents block_exp returns),
+// on two lanes with their own block factors: each step takes the integer of the leading plane,
+// removes it exactly (FMA; the product is exact) and renormalises the remainder with the lo plane
+// (TwoSum), so the slices carry the value to 2^-32 of the block whatever its size; the last
+// slice is rounded to an integer.  The 16-bit codes are returned as (lane x, lane y) pairs.
 template <bool BF16>
-__device__ __forceinline__ void slice_codes2(float2 v, float2 s, float2 is, uint32_t (&code)[NS]) {
-  float2 r = v, up = s, down = make_float2(-is.x, -is.y);
+__device__ __forceinline__ void slice_codes2_df(float2 vh, float2 vl, float2 s, float2 is,
+                                                uint32_t (&code)[NS]) {
+  float2 rh = vh, rl = vl, up = s, down = make_float2(-is.x, -is.y);
 #pragma unroll
   for (int k = 0; k < NS; ++k) {
-    const float2 t = __fmul2_rn(r, up);
+    const float2 t = __fmul2_rn(rh, up);
     const float2 c = make_float2(rintf(t.x), rintf(t.y));
-    if (k + 1 < NS) r = __ffma2_rn(c, down, r);
+    if (k + 1 < NS) {
+      const float2 h = __ffma2_rn(c, down, rh);
+      two_sum2(h, rl, rh, rl);
+    }
     up = mul2(256.f, up);
     down = mul2(0.00390625f, down);
     if (BF16) {
@@ -493,12 +498,15 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         ++chunk;
       }
       if (fail_all) break;
-      float val[kEpiCols];
+      // the column sums as normalised double-float pairs (val, vlo)
+      float val[kEpiCols], vlo[kEpiCols];
 #pragma unroll
       for (int i = 0; i < kEpiCols / 2; ++i) {
-        const float2 v = add2(hi[i], lo[i]);
-        val[2 * i] = v.x;
-        val[2 * i + 1] = v.y;
+        const f2x2 v = df_norm2(hi[i], lo[i]);
+        val[2 * i] = v.hi.x;
+        val[2 * i + 1] = v.hi.y;
+        vlo[2 * i] = v.lo.x;
+        vlo[2 * i + 1] = v.lo.y;
       }
       if (STAGE == 1) {
         // weight 1/(lam_y + lam_x)^2 (normalised); lam_y of the warp's columns via shuffles
@@ -507,7 +515,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           const int n = ncol0 + i;
           const float s = __shfl_sync(0xffffffffu, lamy_mine, i) + lamx_m;
           const bool ok = (m < S.nx) && (n < S.ny) && (s > 0.f);
-          val[i] = ok ? val[i] * spectral_weight_of(S.wnorm, s) : 0.f;
+          const f2 wv = df_mul(f2{val[i], vlo[i]}, spectral_weight_of(S.wnorm, s));
+          val[i] = ok ? wv.hi : 0.f;
+          vlo[i] = ok ? wv.lo : 0.f;
         }
       }
       if (STAGE <= 2) {
@@ -537,7 +547,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           const float2 is2 =
               make_float2(__shfl_sync(0xffffffffu, is_mine, i), __shfl_sync(0xffffffffu, is_mine, i + 1));
           uint32_t code[NS];
-          slice_codes2<BF16>(make_float2(val[i], val[i + 1]), s2, is2, code);
+          slice_codes2_df<BF16>(make_float2(val[i], val[i + 1]), make_float2(vlo[i], vlo[i + 1]), s2,
+                                is2, code);
           const size_t i0 = static_cast<size_t>(ncol0 + i) * v.M + m, i1 = i0 + v.M;
 #pragma unroll
           for (int q = 0; q < NS; ++q) {
@@ -549,29 +560,34 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           v.eout[static_cast<size_t>(ncol0 + lane) * (v.M / KC) + (m0 + 32 * quarter) / KC] =
               static_cast<int8_t>(E_mine);
       } else {
-        CompDot c_rz, c_zq;
+        CompDotDF c_rz, c_zq;
         if (m < S.nx) {
-          constexpr int kGrp = kEpiCols < 16 ? kEpiCols : 16;
+          constexpr int kGrp = 8;
+          static_assert(kEpiCols % kGrp == 0, "stage-3 load groups");
 #pragma unroll
           for (int g8 = 0; g8 < kEpiCols; g8 += kGrp) {
-            float rv[kGrp], qv[kGrp];
+            float rv[kGrp], rl[kGrp], qv[kGrp], ql[kGrp];
             uint8_t mk[kGrp];
 #pragma unroll
             for (int i = 0; i < kGrp; ++i) {  // issue the group's loads together
               const int n = ncol0 + g8 + i;
               const int g = (n < S.ny ? n : 0) * S.nx + m;
               rv[i] = S.r[g];
+              rl[i] = S.r_lo[g];
               qv[i] = S.q[g];
+              ql[i] = S.q_lo[g];
               mk[i] = n < S.ny ? S.mask[g] : 0;
             }
 #pragma unroll
             for (int i = 0; i < kGrp; ++i) {
               const int n = ncol0 + g8 + i;
               if (n < S.ny) {
-                const float zv = mk[i] ? val[g8 + i] : 0.f;
-                S.z[n * S.nx + m] = zv;
-                c_rz.add(rv[i], zv);
-                c_zq.add(zv, qv[i]);
+                const float zh = mk[i] ? val[g8 + i] : 0.f;
+                const float zl = mk[i] ? vlo[g8 + i] : 0.f;
+                S.z[n * S.nx + m] = zh;
+                S.z_lo[n * S.nx + m] = zl;
+                c_rz.add(rv[i], rl[i], zh, zl);
+                c_zq.add(zh, zl, qv[i], ql[i]);
               }
             }
           }
@@ -661,7 +677,7 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     // each lane takes adjacent pairs (x, x+1) and writes both codes of a slice in one 4-byte
     // store (x even, rows of nxp even: aligned)
     constexpr int kPairs = KC / 64;
-    float2 v[kRows][kPairs];
+    float2 v[kRows][kPairs], vl[kRows][kPairs];
 #pragma unroll
     for (int j = 0; j < kRows; ++j) {
       const int y = y0 + warp + 8 * j;
@@ -669,8 +685,11 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
       for (int k = 0; k < kPairs; ++k) {
         const int x = x0 + 64 * k + 2 * lane;
         const float* row = S.r + static_cast<size_t>(y) * S.nx;
+        const float* row_lo = S.r_lo + static_cast<size_t>(y) * S.nx;
         v[j][k].x = (x < S.nx && y < S.ny) ? row[x] : 0.f;
         v[j][k].y = (x + 1 < S.nx && y < S.ny) ? row[x + 1] : 0.f;
+        vl[j][k].x = (x < S.nx && y < S.ny) ? row_lo[x] : 0.f;
+        vl[j][k].y = (x + 1 < S.nx && y < S.ny) ? row_lo[x + 1] : 0.f;
       }
     }
     uint32_t* out32 = reinterpret_cast<uint32_t*>(out);
@@ -686,7 +705,7 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
 #pragma unroll
       for (int k = 0; k < kPairs; ++k) {
         uint32_t code[NS];
-        slice_codes2<BF16>(v[j][k], make_float2(s, s), make_float2(is, is), code);
+        slice_codes2_df<BF16>(v[j][k], vl[j][k], make_float2(s, s), make_float2(is, is), code);
         const size_t idx = (static_cast<size_t>(y) * S.nxp + x0 + 64 * k + 2 * lane) / 2;
 #pragma unroll
         for (int q = 0; q < NS; ++q) out32[q * (plane / 2) + idx] = code[q];

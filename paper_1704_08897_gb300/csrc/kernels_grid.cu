@@ -5,6 +5,8 @@
 // The operator is eq. (discrete_biharmonic) of Sec. 2.1 with the boundary rules of Algorithm 1
 // (Dirichlet padding), half-sample reflection (symmetric) or wrap-around (periodic), evaluated
 // matrix-free ("no need to form the 13-banded matrix", Sec. 2.2).
+//
+// CG vectors are double-float pairs of FP32 planes (hi, lo); see SlotDesc.
 #include "async.cuh"
 #include "common.cuh"
 #include "kernels.h"
@@ -33,10 +35,10 @@ __device__ __forceinline__ int halo_src(const SlotDesc& S, int x0, int y0, int i
   return my * S.nx + mx;
 }
 
-// 13-point masked biharmonic of a smem tile (row stride RS) at local (ly+2, lx+2), compensated
-// FP32.
+// 13-point masked biharmonic of a smem tile (row stride RS) at local (ly+2, lx+2), as a
+// compensated FP32 sum (s, c): s + c carries the exact sum of the 13 terms to about 48 bits.
 template <bool ANISO, int RS = kHX>
-__device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, int ly, int lx) {
+__device__ __forceinline__ CompSum stencil13_acc(const SlotDesc& S, const float* t, int ly, int lx) {
   const float* c = t + (ly + 2) * RS + (lx + 2);
   const float C = c[0];
   const float E0 = c[-1], E1 = c[1], N0 = c[-RS], N1 = c[RS];
@@ -62,16 +64,33 @@ __device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, in
                S.wd_l * ((D0 + D1) + (D2 + D3)) + S.wfx_l * (F0 + F1) + S.wfy_l * (G0 + G1);
     acc.c = __fadd_rn(acc.c, lo);
   }
-  return acc.result();
+  return acc;
+}
+
+// The same stencil applied in plain FP32 (for the lo plane of a double-float vector, whose
+// contribution is 2^-24 of the hi plane's: its own rounding is far below the result's ulp).
+template <bool ANISO, int RS>
+__device__ __forceinline__ float stencil13_plain(const SlotDesc& S, const float* t, int ly, int lx) {
+  const float* c = t + (ly + 2) * RS + (lx + 2);
+  const float e = (c[-1] + c[1]), n = (c[-RS] + c[RS]);
+  const float d = (c[-RS - 1] + c[-RS + 1]) + (c[RS - 1] + c[RS + 1]);
+  const float f = c[-2] + c[2], g = c[-2 * RS] + c[2 * RS];
+  if (!ANISO) return 20.f * c[0] - 8.f * (e + n) + 2.f * d + (f + g);
+  return S.wc * c[0] + S.wex * e + S.wey * n + S.wd * d + S.wfx * f + S.wfy * g;
+}
+
+template <bool ANISO, int RS = kHX>
+__device__ __forceinline__ float stencil13(const SlotDesc& S, const float* t, int ly, int lx) {
+  return stencil13_acc<ANISO, RS>(S, t, ly, lx).result();
 }
 
 // The isotropic 13-point stencil at two adjacent nodes (x, x+1) of a smem tile with an even row
 // stride RS; c points at node x, an even index.  Eleven aligned 8-byte loads cover both
-// neighbourhoods, and each lane runs the scalar stencil13's operations in the same order
+// neighbourhoods, and each lane runs the scalar stencil13_acc's operations in the same order
 // (bit-identical results).
 __device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
 template <int RS>
-__device__ __forceinline__ float2 stencil13_pair(const float* c) {
+__device__ __forceinline__ CompSum2 stencil13_pair_acc(const float* c) {
   static_assert(RS % 2 == 0, "pairs of nodes start on 8-byte boundaries");
   const float2 Cm = ld2(c - 2), C = ld2(c), Cp = ld2(c + 2);                  // row y
   const float2 Nm = ld2(c - RS - 2), N = ld2(c - RS), Np = ld2(c - RS + 2);   // row y-1
@@ -86,7 +105,23 @@ __device__ __forceinline__ float2 stencil13_pair(const float* c) {
   acc.add(mul2(-8.f, E0)); acc.add(mul2(-8.f, E1)); acc.add(mul2(-8.f, N)); acc.add(mul2(-8.f, Sv));
   acc.add(mul2(2.f, D0)); acc.add(mul2(2.f, D1)); acc.add(mul2(2.f, D2)); acc.add(mul2(2.f, D3));
   acc.add(Cm); acc.add(Cp); acc.add(NN); acc.add(SS);
-  return acc.result();
+  return acc;
+}
+// plain FP32 stencil of the lo plane at two adjacent nodes
+template <int RS>
+__device__ __forceinline__ float2 stencil13_pair_plain(const float* c) {
+  const float2 Cm = ld2(c - 2), C = ld2(c), Cp = ld2(c + 2);
+  const float2 Nm = ld2(c - RS - 2), N = ld2(c - RS), Np = ld2(c - RS + 2);
+  const float2 Sm = ld2(c + RS - 2), Sv = ld2(c + RS), Sp = ld2(c + RS + 2);
+  const float2 NN = ld2(c - 2 * RS), SS = ld2(c + 2 * RS);
+  const float2 E = add2(make_float2(Cm.y, C.x), make_float2(C.y, Cp.x));
+  const float2 D = add2(add2(make_float2(Nm.y, N.x), make_float2(N.y, Np.x)),
+                        add2(make_float2(Sm.y, Sv.x), make_float2(Sv.y, Sp.x)));
+  const float2 F = add2(add2(Cm, Cp), add2(NN, SS));
+  float2 v = mul2(20.f, C);
+  v = fma2(make_float2(-8.f, -8.f), add2(E, add2(N, Sv)), v);
+  v = fma2(make_float2(2.f, 2.f), D, v);
+  return add2(v, F);
 }
 
 __device__ __forceinline__ double stencil13_f64(const SlotDesc& S, const double* t, int ly, int lx) {
@@ -98,7 +133,8 @@ __device__ __forceinline__ double stencil13_f64(const SlotDesc& S, const double*
 
 // ---------------------------------------------------------------------------------------------
 // Setup: known mask from sign(phi) (Sec. 2.1), b = -M L^2 E_K f in FP64 (Algorithm 1, first
-// statement), zero CG state.  Partials: ||b||^2, number of known nodes, number of NaN phi.
+// statement), zero CG state.  Partials: ||b||^2, number of known nodes, number of invalid inputs
+// (NaN phi, or a non-finite f at a known node).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStThreads)
 k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
@@ -128,7 +164,7 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       sf[i] = v;
     }
     __syncthreads();
-    double bb = 0.0, cnt = 0.0, nan = 0.0;
+    double bb = 0.0, cnt = 0.0, bad = 0.0;
     for (int k = threadIdx.x; k < kStTileX * kStTileY; k += blockDim.x) {
       const int ly = k / kStTileX, lx = k - ly * kStTileX;
       const int gx = x0 + lx, gy = y0 + ly;
@@ -136,23 +172,28 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       const int g = gy * S.nx + gx;
       const float ph = phi[g];
       const bool known = out_dir ? (ph < 0.f) : (ph > 0.f);
-      if (ph != ph) nan += 1.0;
+      if (ph != ph || (known && !isfinite(f[g]))) bad += 1.0;
       double bv = 0.0;
       if (!known) bv = -stencil13_f64(S, sf, ly, lx);
       S.mask[g] = known ? 0 : 1;
       S.b[g] = bv;
       S.xhi[g] = 0.f;
       S.xlo[g] = 0.f;
-      S.r[g] = (float)bv;
+      S.r[g] = 0.f;
+      S.r_lo[g] = 0.f;
       S.p[0][g] = 0.f;
       S.p[1][g] = 0.f;
+      S.p_lo[0][g] = 0.f;
+      S.p_lo[1][g] = 0.f;
       S.q[g] = 0.f;
+      S.q_lo[g] = 0.f;
       S.z[g] = 0.f;
+      S.z_lo[g] = 0.f;
       bb += bv * bv;
       cnt += known ? 1.0 : 0.0;
     }
     block_sum2<kStThreads>(bb, cnt, red);
-    double nn = nan, dummy = 0.0;
+    double nn = bad, dummy = 0.0;
     block_sum2<kStThreads>(nn, dummy, red);
     if (threadIdx.x == 0) {
       S.part[it.tile * 4 + 0] = bb;
@@ -188,8 +229,8 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
         sc->it = 0;
         sc->fold = 0;
         sc->n_known = (int)sk;
-        if (sn > 0.0) {
-          sc->status = -1;  // EXT_EINVAL: NaN in phi
+        if (sn > 0.0 || !isfinite(sb)) {
+          sc->status = -1;  // EXT_EINVAL: NaN in phi or a non-finite known value
           sc->active = 0;
           sc->need_prec = 0;
         } else if (sb == 0.0) {
@@ -207,7 +248,8 @@ k_setup(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
   }
 }
 
-// Set-up, second pass: r = 2^e b in FP32, once the slot's scale exponent e is known.
+// Set-up, second pass: r = 2^e b as a double-float pair, once the slot's scale exponent e is
+// known.
 __global__ void __launch_bounds__(kStThreads)
 k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
             const int* __restrict__ n_items) {
@@ -215,6 +257,7 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem it = items[w];
     const SlotDesc& S = slots[it.slot];
+    if (S.sc->status != ST_RUNNING) continue;
     const int e = S.sc->bexp;
     int x0, y0;
     tile_origin(S, it.tile, x0, y0);
@@ -223,34 +266,40 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
       const int gx = x0 + lx, gy = y0 + ly;
       if (gx >= S.nx || gy >= S.ny) continue;
       const int g = gy * S.nx + gx;
-      S.r[g] = (float)ldexp(S.b[g], e);
+      const f2 v = df_of(ldexp(S.b[g], e));
+      S.r[g] = v.hi;
+      S.r_lo[g] = v.lo;
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------------
-// Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo),
-// q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), per-tile partial p.q;
-// k_pq_finish then forms alpha = rho / p.q for each slot.
+// Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo, in
+// double-float), q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), per-tile
+// partial p.q; k_pq_finish then forms alpha = rho / p.q for each slot.
 //
-// Each block walks its share of the (slot, tile) list with two shared-memory windows.  For a slot
-// whose rows span a multiple of 16 bytes in the mask (nx % 16 == 0), the window of the block's
-// next tile arrives by tensor copies while it computes the current one: z and p_old over rows
-// y0-2 .. y0+33 and columns x0-4 .. x0+67 (two columns wider on the left than the halo, so that
-// each copy starts on a 16-byte boundary) and the tile's mask bytes.  Cells outside the grid
-// arrive as zeros; the ghost cells of a boundary tile (reflected, wrapped or negated copies of
-// grid nodes under the boundary rule) are gathered by plain loads.  Tiles of other slots fill the
-// free window with plain loads.
+// q is the double-float pair of the exact 13-point sum of p's hi plane (compensated FP32) plus
+// the same stencil of p's lo plane in plain FP32.
+//
+// Each block walks its share of the (slot, tile) list with two shared-memory window sets.  For a
+// slot whose rows span a multiple of 16 bytes in the mask (nx % 16 == 0), the window set of the
+// block's next tile arrives by tensor copies while it computes the current one: the hi and lo
+// planes of z and p_old over rows y0-2 .. y0+33 and columns x0-4 .. x0+67 (two columns wider on
+// the left than the halo, so that each copy starts on a 16-byte boundary) and the tile's mask
+// bytes.  Cells outside the grid arrive as zeros; the ghost cells of a boundary tile (reflected,
+// wrapped or negated copies of grid nodes under the boundary rule) are gathered by plain loads.
+// Tiles of other slots fill the free window set with plain loads.
 // ---------------------------------------------------------------------------------------------
 constexpr int kWX = kStWinX;                           // 72: window row, floats
 static_assert(kStWinY == kHY, "the window spans the halo rows");
-constexpr int kWinBytes = kWX * kHY * 4;               // one float window (z, then p; p_old)
+constexpr int kWinBytes = kWX * kHY * 4;               // one FP32 plane window
 constexpr int kMaskBytes = kStTileX * kStTileY;        // the tile's mask
-constexpr int kBufBytes = 2 * kWinBytes + kMaskBytes;  // one window set
+constexpr int kBufBytes = 4 * kWinBytes + kMaskBytes;  // one window set: z, z_lo, p, p_lo, mask
 static_assert(kWinBytes % 128 == 0 && kBufBytes % 128 == 0, "tensor copy destinations");
 constexpr int kGhostSlots = 4 * kHY + 4 * kHX;         // candidate ghost cells of one halo
 static_assert(kGhostSlots <= 2 * kStThreads, "two ghost candidates per thread");
-constexpr int kStBlocksPerSm = 4;
+constexpr int kStBlocksPerSm = 2;
+constexpr int kStSmemBytes = 2 * kBufBytes + 128;      // dynamic: two window sets, alignment slack
 
 // Candidate k of a tile's ghost cells: the four ghost columns (x = -2, -1, nx, nx+1) over the
 // halo's rows, then the four ghost rows over the halo's in-grid columns.  Returns false when the
@@ -278,8 +327,8 @@ __device__ __forceinline__ bool ghost_cell(const SlotDesc& S, int x0, int y0, in
 // w_issue whose slot iterates and has stencil maps) into window set n_issued % 2.
 __device__ __forceinline__ void stencil_issue_next(const SlotDesc* __restrict__ slots,
                                                    const WorkItem* __restrict__ items, int total,
-                                                   unsigned char (*sbuf)[kBufBytes],
-                                                   uint64_t* full, int& w_issue, int& n_issued) {
+                                                   unsigned char* sbuf, uint64_t* full,
+                                                   int& w_issue, int& n_issued) {
   while (w_issue < total) {
     const WorkItem it = items[w_issue];
     w_issue += gridDim.x;
@@ -288,19 +337,18 @@ __device__ __forceinline__ void stencil_issue_next(const SlotDesc* __restrict__ 
     int x0, y0;
     tile_origin(S, it.tile, x0, y0);
     const unsigned char* maps = static_cast<const unsigned char*>(S.st_maps);
-    const void* mz = maps;
-    const void* mp = maps + 128 * (1 + (S.sc->it & 1));
-    const void* mm = maps + 128 * 3;
-    tmap_acquire(mz);
-    tmap_acquire(mp);
-    tmap_acquire(mm);
+    const int par = S.sc->it & 1;
+    const void* src[5] = {maps, maps + 128, maps + 128 * (2 + 2 * par), maps + 128 * (3 + 2 * par),
+                          maps + 128 * 6};
+#pragma unroll
+    for (int k = 0; k < 5; ++k) tmap_acquire(src[k]);
     const int b = n_issued & 1;
-    unsigned char* dst = sbuf[b];
+    unsigned char* dst = sbuf + b * kBufBytes;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     mbar_expect_tx(&full[b], kBufBytes);
-    tma_load_2d(dst, mz, &full[b], x0 - 4, y0 - 2);
-    tma_load_2d(dst + kWinBytes, mp, &full[b], x0 - 4, y0 - 2);
-    tma_load_2d(dst + 2 * kWinBytes, mm, &full[b], x0, y0);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) tma_load_2d(dst + k * kWinBytes, src[k], &full[b], x0 - 4, y0 - 2);
+    tma_load_2d(dst + 4 * kWinBytes, src[4], &full[b], x0, y0);
     ++n_issued;
     return;
   }
@@ -310,7 +358,9 @@ template <bool ANISO>
 __global__ void __launch_bounds__(kStThreads, kStBlocksPerSm)
 k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int* __restrict__ err) {
-  __shared__ __align__(128) unsigned char sbuf[2][kBufBytes];
+  extern __shared__ unsigned char st_smem_raw[];
+  unsigned char* sbuf = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(st_smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ __align__(8) uint64_t full[2];
   __shared__ double red[64];
   __shared__ int s_abort;
@@ -332,11 +382,14 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
     if (!sc->active) continue;
-    const float beta = (float)sc->beta;
+    const f2 beta = df_of(sc->beta);
     const int par = sc->it & 1;
     const float* __restrict__ pold = S.p[par];
+    const float* __restrict__ pold_lo = S.p_lo[par];
     float* __restrict__ pnew = S.p[par ^ 1];
+    float* __restrict__ pnew_lo = S.p_lo[par ^ 1];
     const float* __restrict__ z = S.z;
+    const float* __restrict__ z_lo = S.z_lo;
     int x0, y0;
     tile_origin(S, it.tile, x0, y0);
     // a tile whose halo lies inside the grid has no ghost cell
@@ -345,13 +398,14 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     unsigned char* buf;
     if (S.st_maps != nullptr) {
       const int b = n_used & 1;
-      buf = sbuf[b];
+      buf = sbuf + b * kBufBytes;
       // the other window set finished with the previous tile: start the next tile's copies
       if (threadIdx.x == 0 && n_issued == n_used + 1)
         stencil_issue_next(slots, items, total, sbuf, full, w_issue, n_issued);
       // ghost cells by plain loads, issued before the wait so that both latencies overlap
       int gcell[2] = {-1, -1};
-      float gz[2] = {0.f, 0.f}, gp[2] = {0.f, 0.f}, gs[2] = {0.f, 0.f};
+      float gs[2] = {0.f, 0.f};
+      f2 gz[2] = {{0.f, 0.f}, {0.f, 0.f}}, gp[2] = {{0.f, 0.f}, {0.f, 0.f}};
       if (!interior) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -363,36 +417,48 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             if (s != 0.f) {  // zero-sign ghosts stay the zeros the copy filled in
               gcell[h] = wy * kWX + wx;
               gs[h] = s;
-              gz[h] = __ldg(z + g);
-              gp[h] = __ldg(pold + g);
+              gz[h] = f2{__ldg(z + g), __ldg(z_lo + g)};
+              gp[h] = f2{__ldg(pold + g), __ldg(pold_lo + g)};
             }
           }
         }
       }
       mbar_wait(&full[b], (n_used >> 1) & 1, abort_flag);
       // p = z + beta p_old over the whole window, in place of z
-      float4* zw = reinterpret_cast<float4*>(buf);
-      const float4* pw = reinterpret_cast<const float4*>(buf + kWinBytes);
+      float4* zh = reinterpret_cast<float4*>(buf);
+      float4* zl = reinterpret_cast<float4*>(buf + kWinBytes);
+      const float4* ph = reinterpret_cast<const float4*>(buf + 2 * kWinBytes);
+      const float4* pl = reinterpret_cast<const float4*>(buf + 3 * kWinBytes);
       for (int v = threadIdx.x; v < kWX * kHY / 4; v += kStThreads) {
-        const float4 a = zw[v], c = pw[v];
-        zw[v] = make_float4(__fmaf_rn(beta, c.x, a.x), __fmaf_rn(beta, c.y, a.y),
-                            __fmaf_rn(beta, c.z, a.z), __fmaf_rn(beta, c.w, a.w));
+        const float4 a = zh[v], al = zl[v], c = ph[v], cl = pl[v];
+        const f2x2 u = df_axpy2(beta, {make_float2(c.x, c.y), make_float2(cl.x, cl.y)},
+                                {make_float2(a.x, a.y), make_float2(al.x, al.y)});
+        const f2x2 t = df_axpy2(beta, {make_float2(c.z, c.w), make_float2(cl.z, cl.w)},
+                                {make_float2(a.z, a.w), make_float2(al.z, al.w)});
+        zh[v] = make_float4(u.hi.x, u.hi.y, t.hi.x, t.hi.y);
+        zl[v] = make_float4(u.lo.x, u.lo.y, t.lo.x, t.lo.y);
       }
       __syncthreads();
       if (*abort_flag) break;  // every thread reads the flag after the barrier: uniform
       ++n_used;
       if (!interior) {
-        float* wf = reinterpret_cast<float*>(buf);
+        float* wh = reinterpret_cast<float*>(buf);
+        float* wl = reinterpret_cast<float*>(buf + kWinBytes);
 #pragma unroll
         for (int h = 0; h < 2; ++h)
-          if (gcell[h] >= 0) wf[gcell[h]] = gs[h] * __fmaf_rn(beta, gp[h], gz[h]);
+          if (gcell[h] >= 0) {
+            const f2 v = df_add(gz[h], df_mul(gp[h], beta));
+            wh[gcell[h]] = gs[h] * v.hi;
+            wl[gcell[h]] = gs[h] * v.lo;
+          }
         __syncthreads();
       }
     } else {
       // plain loads into the free window set, kChunk cells per thread in flight at a time
-      buf = sbuf[(n_used + 1) & 1];
-      float* wf = reinterpret_cast<float*>(buf);
-      uint8_t* mt = buf + 2 * kWinBytes;
+      buf = sbuf + ((n_used + 1) & 1) * kBufBytes;
+      float* wh = reinterpret_cast<float*>(buf);
+      float* wl = reinterpret_cast<float*>(buf + kWinBytes);
+      uint8_t* mt = buf + 4 * kWinBytes;
       for (int e = threadIdx.x; e < kMaskBytes; e += kStThreads) {
         const int ly = e / kStTileX, lx = e - ly * kStTileX;
         const int gx = x0 + lx, gy = y0 + ly;
@@ -402,7 +468,8 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
 #pragma unroll 1
       for (int i0 = 0; i0 < kHalo; i0 += kChunk * kStThreads) {
         int gi[kChunk];
-        float gsg[kChunk], zv[kChunk], pv[kChunk];
+        float gsg[kChunk];
+        f2 zv[kChunk], pv[kChunk];
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
           const int i = i0 + threadIdx.x + j * kStThreads;
@@ -412,25 +479,31 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         }
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
-          zv[j] = gsg[j] != 0.f ? __ldg(z + gi[j]) : 0.f;
-          pv[j] = gsg[j] != 0.f ? __ldg(pold + gi[j]) : 0.f;
+          const bool on = gsg[j] != 0.f;
+          zv[j] = on ? f2{__ldg(z + gi[j]), __ldg(z_lo + gi[j])} : f2{0.f, 0.f};
+          pv[j] = on ? f2{__ldg(pold + gi[j]), __ldg(pold_lo + gi[j])} : f2{0.f, 0.f};
         }
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
           const int i = i0 + threadIdx.x + j * kStThreads;
           if (i < kHalo) {
             const int ly = i / kHX, lx = i - ly * kHX;
-            wf[ly * kWX + lx + 2] = gsg[j] * __fmaf_rn(beta, pv[j], zv[j]);
+            const f2 v = df_add(zv[j], df_mul(pv[j], beta));
+            wh[ly * kWX + lx + 2] = gsg[j] * v.hi;
+            wl[ly * kWX + lx + 2] = gsg[j] * v.lo;
           }
         }
       }
       __syncthreads();
     }
-    const float* wf = reinterpret_cast<const float*>(buf);
-    const uint8_t* mt = buf + 2 * kWinBytes;
+    const float* wh = reinterpret_cast<const float*>(buf);
+    const float* wl = reinterpret_cast<const float*>(buf + kWinBytes);
+    const uint8_t* mt = buf + 4 * kWinBytes;
     constexpr int kOwn = kStTileX * kStTileY / kStThreads;
     static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn % 2 == 0, "tile / block size");
-    CompDot dot;
+    CompDotDF dot;
+    float* __restrict__ qh = S.q;
+    float* __restrict__ ql = S.q_lo;
     if (!ANISO) {
       // node pairs (x, x+1): the window's row stride is even and x - x0 is even
 #pragma unroll 1
@@ -440,27 +513,41 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= S.nx || gy >= S.ny) continue;
         const int g = gy * S.nx + gx;
-        const float* c = wf + (ly + 2) * kWX + lx + 4;
-        const float2 pv = ld2(c);
+        const int wc = (ly + 2) * kWX + lx + 4;
+        const float2 pvh = ld2(wh + wc), pvl = ld2(wl + wc);
         const unsigned m2 = *reinterpret_cast<const uint16_t*>(mt + ly * kStTileX + lx);
-        const float2 q2 = m2 ? stencil13_pair<kWX>(c) : make_float2(0.f, 0.f);
-        const float q0 = (m2 & 0xffu) ? q2.x : 0.f;
-        const float q1 = (m2 >> 8) ? q2.y : 0.f;
-        dot.add(pv.x, q0);
+        f2x2 q2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        if (m2) {
+          const CompSum2 a = stencil13_pair_acc<kWX>(wh + wc);
+          const float2 l = stencil13_pair_plain<kWX>(wl + wc);
+          q2 = df_norm2(a.s, add2(a.c, l));
+        }
+        const bool m0 = (m2 & 0xffu) != 0, m1 = (m2 >> 8) != 0;
+        const f2 q0 = m0 ? f2{q2.hi.x, q2.lo.x} : f2{0.f, 0.f};
+        const f2 q1 = m1 ? f2{q2.hi.y, q2.lo.y} : f2{0.f, 0.f};
+        dot.add(pvh.x, pvl.x, q0.hi, q0.lo);
         if (gx + 1 < S.nx) {
-          dot.add(pv.y, q1);
+          dot.add(pvh.y, pvl.y, q1.hi, q1.lo);
           if ((g & 1) == 0) {
-            *reinterpret_cast<float2*>(pnew + g) = pv;
-            *reinterpret_cast<float2*>(S.q + g) = make_float2(q0, q1);
+            *reinterpret_cast<float2*>(pnew + g) = pvh;
+            *reinterpret_cast<float2*>(pnew_lo + g) = pvl;
+            *reinterpret_cast<float2*>(qh + g) = make_float2(q0.hi, q1.hi);
+            *reinterpret_cast<float2*>(ql + g) = make_float2(q0.lo, q1.lo);
           } else {
-            pnew[g] = pv.x;
-            pnew[g + 1] = pv.y;
-            S.q[g] = q0;
-            S.q[g + 1] = q1;
+            pnew[g] = pvh.x;
+            pnew[g + 1] = pvh.y;
+            pnew_lo[g] = pvl.x;
+            pnew_lo[g + 1] = pvl.y;
+            qh[g] = q0.hi;
+            qh[g + 1] = q1.hi;
+            ql[g] = q0.lo;
+            ql[g + 1] = q1.lo;
           }
         } else {
-          pnew[g] = pv.x;
-          S.q[g] = q0;
+          pnew[g] = pvh.x;
+          pnew_lo[g] = pvl.x;
+          qh[g] = q0.hi;
+          ql[g] = q0.lo;
         }
       }
     } else {
@@ -471,15 +558,21 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= S.nx || gy >= S.ny) continue;
         const int g = gy * S.nx + gx;
-        const float pv = wf[(ly + 2) * kWX + lx + 4];
-        float qv = 0.f;
-        if (mt[ly * kStTileX + lx]) qv = stencil13<ANISO, kWX>(S, wf + 2, ly, lx);
-        pnew[g] = pv;
-        S.q[g] = qv;
-        dot.add(pv, qv);
+        const float pvh = wh[(ly + 2) * kWX + lx + 4], pvl = wl[(ly + 2) * kWX + lx + 4];
+        f2 qv = {0.f, 0.f};
+        if (mt[ly * kStTileX + lx]) {
+          const CompSum a = stencil13_acc<ANISO, kWX>(S, wh + 2, ly, lx);
+          const float l = stencil13_plain<ANISO, kWX>(S, wl + 2, ly, lx);
+          qv = df_norm(a.s, __fadd_rn(a.c, l));
+        }
+        pnew[g] = pvh;
+        pnew_lo[g] = pvl;
+        qh[g] = qv.hi;
+        ql[g] = qv.lo;
+        dot.add(pvh, pvl, qv.hi, qv.lo);
       }
     }
-    const double pq = block_sum_comp<kStThreads>(dot, red);
+    const double pq = block_sum_comp<kStThreads>(dot.as_comp(), red);
     if (threadIdx.x == 0) S.part[it.tile * 4 + 1] = pq;  // reduced by k_pq_finish
     __syncthreads();  // the window set is free for the copies started at the next copied tile
   }
@@ -525,11 +618,10 @@ k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
 }
 
 // ---------------------------------------------------------------------------------------------
-// Iteration, stage 2: x += alpha p (double-float), r -= alpha q (FP32), partial ||r||^2.  The
-// last item advances the iteration count and decides stop / residual replacement.
-// The iterate must carry more than FP32: an FP32 increment carries rounding errors of size
-// eps |x|, which for this operator pin the true residual near 1e-6 while the recursive one
-// keeps falling.  Each thread moves 16-byte vectors (4 elements per access).
+// Iteration, stage 2: x += alpha p, r -= alpha q (all double-float), partial ||r||^2.  The last
+// item advances the iteration count and decides stop / residual replacement.  Each thread moves
+// 16-byte vectors (4 elements per access) of every plane; all loads are issued before any
+// arithmetic.
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kVecThreads)
 k_update(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
@@ -542,57 +634,71 @@ k_update(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
     if (!sc->active) continue;
-    const float alpha = (float)sc->alpha;
-    const float* __restrict__ p = S.p[(sc->it & 1) ^ 1];
+    const f2 alpha = df_of(sc->alpha);
+    const f2 nalpha = {-alpha.hi, -alpha.lo};
+    const int pi = (sc->it & 1) ^ 1;
+    const float* __restrict__ p = S.p[pi];
+    const float* __restrict__ p_lo = S.p_lo[pi];
     const int n = S.nx * S.ny;
     const int e0 = it.tile * kVecChunk;
     const int e1 = min(n, e0 + kVecChunk);
-    CompDot dot;
+    CompDotDF dot;
     constexpr int kStep = 4 * kVecThreads;
     constexpr int kVec = kVecChunk / kStep;
     if (e0 + kVecChunk <= n) {
-      // full chunk: issue every load of the thread before any arithmetic
-      float4 pv[kVec], qv[kVec], rv[kVec], xh[kVec], xl[kVec];
+      // full chunk: kU 16-byte vectors of every plane in flight per thread, loads first
+      constexpr int kU = 2;
+      static_assert(kVec % kU == 0, "unroll");
+#pragma unroll 1
+      for (int j0 = 0; j0 < kVec; j0 += kU) {
+        float4 ph[kU], pl[kU], qh[kU], ql[kU], rh[kU], rl[kU], xh[kU], xl[kU];
 #pragma unroll
-      for (int j = 0; j < kVec; ++j) {
-        const int e = e0 + j * kStep + 4 * threadIdx.x;
-        pv[j] = __ldg(reinterpret_cast<const float4*>(p + e));
-        qv[j] = __ldg(reinterpret_cast<const float4*>(S.q + e));
-        rv[j] = *reinterpret_cast<const float4*>(S.r + e);
-        xh[j] = *reinterpret_cast<const float4*>(S.xhi + e);
-        xl[j] = *reinterpret_cast<const float4*>(S.xlo + e);
-      }
+        for (int u = 0; u < kU; ++u) {
+          const int e = e0 + (j0 + u) * kStep + 4 * threadIdx.x;
+          ph[u] = __ldg(reinterpret_cast<const float4*>(p + e));
+          pl[u] = __ldg(reinterpret_cast<const float4*>(p_lo + e));
+          qh[u] = __ldg(reinterpret_cast<const float4*>(S.q + e));
+          ql[u] = __ldg(reinterpret_cast<const float4*>(S.q_lo + e));
+          rh[u] = *reinterpret_cast<const float4*>(S.r + e);
+          rl[u] = *reinterpret_cast<const float4*>(S.r_lo + e);
+          xh[u] = *reinterpret_cast<const float4*>(S.xhi + e);
+          xl[u] = *reinterpret_cast<const float4*>(S.xlo + e);
+        }
 #pragma unroll
-      for (int j = 0; j < kVec; ++j) {
-        const int e = e0 + j * kStep + 4 * threadIdx.x;
-        df_axpy(xh[j].x, xl[j].x, alpha, pv[j].x);
-        df_axpy(xh[j].y, xl[j].y, alpha, pv[j].y);
-        df_axpy(xh[j].z, xl[j].z, alpha, pv[j].z);
-        df_axpy(xh[j].w, xl[j].w, alpha, pv[j].w);
-        rv[j].x = __fmaf_rn(-alpha, qv[j].x, rv[j].x);
-        rv[j].y = __fmaf_rn(-alpha, qv[j].y, rv[j].y);
-        rv[j].z = __fmaf_rn(-alpha, qv[j].z, rv[j].z);
-        rv[j].w = __fmaf_rn(-alpha, qv[j].w, rv[j].w);
-        *reinterpret_cast<float4*>(S.xhi + e) = xh[j];
-        *reinterpret_cast<float4*>(S.xlo + e) = xl[j];
-        *reinterpret_cast<float4*>(S.r + e) = rv[j];
-        dot.add(rv[j].x, rv[j].x);
-        dot.add(rv[j].y, rv[j].y);
-        dot.add(rv[j].z, rv[j].z);
-        dot.add(rv[j].w, rv[j].w);
+        for (int u = 0; u < kU; ++u) {
+          const int e = e0 + (j0 + u) * kStep + 4 * threadIdx.x;
+          df_axpy(xh[u].x, xl[u].x, alpha, ph[u].x, pl[u].x);
+          df_axpy(xh[u].y, xl[u].y, alpha, ph[u].y, pl[u].y);
+          df_axpy(xh[u].z, xl[u].z, alpha, ph[u].z, pl[u].z);
+          df_axpy(xh[u].w, xl[u].w, alpha, ph[u].w, pl[u].w);
+          df_axpy(rh[u].x, rl[u].x, nalpha, qh[u].x, ql[u].x);
+          df_axpy(rh[u].y, rl[u].y, nalpha, qh[u].y, ql[u].y);
+          df_axpy(rh[u].z, rl[u].z, nalpha, qh[u].z, ql[u].z);
+          df_axpy(rh[u].w, rl[u].w, nalpha, qh[u].w, ql[u].w);
+          *reinterpret_cast<float4*>(S.xhi + e) = xh[u];
+          *reinterpret_cast<float4*>(S.xlo + e) = xl[u];
+          *reinterpret_cast<float4*>(S.r + e) = rh[u];
+          *reinterpret_cast<float4*>(S.r_lo + e) = rl[u];
+          dot.add(rh[u].x, rl[u].x, rh[u].x, rl[u].x);
+          dot.add(rh[u].y, rl[u].y, rh[u].y, rl[u].y);
+          dot.add(rh[u].z, rl[u].z, rh[u].z, rl[u].z);
+          dot.add(rh[u].w, rl[u].w, rh[u].w, rl[u].w);
+        }
       }
     } else {
       for (int k = e0 + threadIdx.x; k < e1; k += blockDim.x) {
         float xh = S.xhi[k], xl = S.xlo[k];
-        df_axpy(xh, xl, alpha, p[k]);
+        df_axpy(xh, xl, alpha, p[k], p_lo[k]);
         S.xhi[k] = xh;
         S.xlo[k] = xl;
-        const float rv = __fmaf_rn(-alpha, S.q[k], S.r[k]);
-        S.r[k] = rv;
-        dot.add(rv, rv);
+        float rh = S.r[k], rl = S.r_lo[k];
+        df_axpy(rh, rl, nalpha, S.q[k], S.q_lo[k]);
+        S.r[k] = rh;
+        S.r_lo[k] = rl;
+        dot.add(rh, rl, rh, rl);
       }
     }
-    const double rr = block_sum_comp<kVecThreads>(dot, red);
+    const double rr = block_sum_comp<kVecThreads>(dot.as_comp(), red);
     if (threadIdx.x == 0) S.part[it.tile * 4 + 0] = rr;
     if (last_item_block(&sc->cnt[2], S.n_vec_items, &s_last)) {
       double sums[1];
@@ -615,7 +721,8 @@ k_update(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
 }
 
 // ---------------------------------------------------------------------------------------------
-// Tail: true residual r = b - M L^2 xhat in FP64, replace the recursive residual, and decide: converged / not converged at maxit / continue (with a fresh preconditioner pass).
+// Tail: true residual r = b - M L^2 xhat in FP64, replace the recursive residual, and decide:
+// converged / not converged at maxit / continue (with a fresh preconditioner pass).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kStThreads)
 k_true_residual(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
@@ -646,7 +753,9 @@ k_true_residual(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__
       const int g = gy * S.nx + gx;
       double rv = 0.0;
       if (S.mask[g]) rv = ldexp(S.b[g], be) - stencil13_f64(S, sx, ly, lx);
-      S.r[g] = (float)rv;
+      const f2 v = df_of(rv);
+      S.r[g] = v.hi;
+      S.r_lo[g] = v.lo;
       rr += rv * rv;
     }
     double d2 = 0.0;
@@ -744,7 +853,8 @@ k_output64(const SlotDesc* __restrict__ slots, const float* __restrict__ f, doub
 }
 
 // ---------------------------------------------------------------------------------------------
-// Verification entry: q = M L^2 p for a caller-supplied p (same compensated evaluation).
+// q = M L^2 p for a caller-supplied FP32 p (same compensated evaluation, one node per thread;
+// used by the entry point that allocates nothing).
 // ---------------------------------------------------------------------------------------------
 template <bool ANISO>
 __global__ void __launch_bounds__(kStThreads)
@@ -791,17 +901,25 @@ void launch_rhs_scale(const LaunchCfg& c) {
   k_rhs_scale<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
 }
 void launch_stencil(const LaunchCfg& c, bool aniso, int* err) {
-  if (aniso) k_stencil<true><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, err);
-  else k_stencil<false><<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items, err);
+  if (aniso)
+    k_stencil<true><<<c.grid, kStThreads, kStSmemBytes, c.stream>>>(c.slots, c.items, c.n_items, err);
+  else
+    k_stencil<false><<<c.grid, kStThreads, kStSmemBytes, c.stream>>>(c.slots, c.items, c.n_items, err);
 }
 int stencil_blocks_per_sm() { return kStBlocksPerSm; }
 cudaError_t stencil_init() {
-  // all of the SM's shared memory to the carveout, so that kStBlocksPerSm window pairs fit
-  cudaError_t e = cudaFuncSetAttribute(k_stencil<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       cudaSharedmemCarveoutMaxShared);
-  const cudaError_t e2 = cudaFuncSetAttribute(k_stencil<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                              cudaSharedmemCarveoutMaxShared);
-  return e != cudaSuccess ? e : e2;
+  // the window sets live in dynamic shared memory; all of the SM's shared memory to the
+  // carveout, so that kStBlocksPerSm blocks fit
+  cudaError_t e[4] = {
+      cudaFuncSetAttribute(k_stencil<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmemBytes),
+      cudaFuncSetAttribute(k_stencil<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmemBytes),
+      cudaFuncSetAttribute(k_stencil<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared),
+      cudaFuncSetAttribute(k_stencil<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared)};
+  for (cudaError_t x : e)
+    if (x != cudaSuccess) return x;
+  return cudaSuccess;
 }
 void launch_pq_finish(const LaunchCfg& c) {
   k_pq_finish<<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items);

@@ -69,14 +69,18 @@ AxisBasis make_axis_basis(int n, int bc) {
 
 int pad_to(int n, int m) { return (n + m - 1) / m * m; }
 
-void padded_f32(const AxisBasis& B, int np, std::vector<float>& q, std::vector<float>& qt) {
-  q.assign((size_t)np * np, 0.f);
-  qt.assign((size_t)np * np, 0.f);
+void padded_df(const AxisBasis& B, int np, std::vector<float>& q, std::vector<float>& qt) {
+  const size_t plane = (size_t)np * np;
+  q.assign(2 * plane, 0.f);
+  qt.assign(2 * plane, 0.f);
   for (int i = 0; i < B.n; ++i)
     for (int k = 0; k < B.n; ++k) {
-      const float v = (float)B.Q[(size_t)i * B.n + k];
-      q[(size_t)i * np + k] = v;
-      qt[(size_t)k * np + i] = v;
+      const double v = B.Q[(size_t)i * B.n + k];
+      const float hi = (float)v, lo = (float)(v - (double)hi);
+      q[(size_t)i * np + k] = hi;
+      q[plane + (size_t)i * np + k] = lo;
+      qt[(size_t)k * np + i] = hi;
+      qt[plane + (size_t)k * np + i] = lo;
     }
 }
 

@@ -13,7 +13,8 @@ struct AxisBasis {
 
 AxisBasis make_axis_basis(int n, int bc);
 int pad_to(int n, int m);
-// Zero-padded np x np float copies of Q and Q^T (row-major).
-void padded_f32(const AxisBasis& B, int np, std::vector<float>& q, std::vector<float>& qt);
+// Zero-padded np x np double-float copies of Q and Q^T (row-major): the hi plane, then the lo
+// plane (the FP64 entry minus its FP32 rounding).
+void padded_df(const AxisBasis& B, int np, std::vector<float>& q, std::vector<float>& qt);
 
 }  // namespace bx

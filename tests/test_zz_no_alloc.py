@@ -5,8 +5,9 @@ need the operator: a host application that owns the whole device-memory budget, 
 which cudaMalloc/cudaFree would synchronise the device.  Its scratch is
 one fixed array per device, shared by every call, so the test makes two calls in a row with
 different grids and checks each against ext_apply_biharmonic: q bit for bit (both evaluate the
-same compensated 13-point sum, term by term in the same order) and the sum p.q to 1e-10 relative
-(one sums FP64 per-tile partials, the other the solver stencil's compensated FP32 partials).  This file is collected last; it also passes when run alone.
+same compensated 13-point sum, term by term in the same order) and the sum p.q to 1e-7 relative:
+this entry point sums p times the FP32 q it returns, the context entry point the solver's
+double-float q, which is the same q plus a low part of relative size 2^-24.  This file is collected last; it also passes when run alone.
 """
 
 import numpy as np
@@ -45,7 +46,7 @@ def test_noalloc_apply_matches_context_apply_on_two_calls():
             rc, s = ext.ext_apply_biharmonic_noalloc(prob, phi_d, p_d, q)
             assert rc == ext.EXT_OK
             assert torch.equal(q, q_ref)
-            assert abs(s - s_ref) <= 1e-10 * abs(s_ref)
+            assert abs(s - s_ref) <= 1e-7 * abs(s_ref)
     finally:
         ext.ext_destroy(ctx)
 
