@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=48,
+                    help="batch: requests of the serving leg (config-4 shape); 0 skips it")
     return ap.parse_args()
 
 
@@ -472,6 +474,82 @@ def error_vs_oracle(probs, answers, refs, prec, at="rel-res 1e-8, answers of the
             "at": at}
 
 
+def serving_leg(count=48, seed=None, side_lo=64, side_hi=2048, plain_budget_s=20.0):
+    """A bounded sample of the serving workload (config-4 shape): `count` requests with sides
+    log-uniform in [side_lo, side_hi], star or multi-circle interfaces, extend in or out and
+    symmetric or periodic edges at random, served by ext_submit / ext_poll with the mixed BF16
+    path.  Plans of every shape are built first (an all-known solve per shape); then the stream
+    is offered (1) all at once (saturation: the throughput is the capacity C) and (2) as Poisson
+    arrivals at 0.5 C (below saturation), each reporting p50/p99 latency (arrival to result) and
+    solves/s over wall time.  The serial plain FP32 path is timed on the same requests in arrival
+    order within a time budget."""
+    import numpy as np
+    import torch
+
+    from paper_1704_08897_gb300 import ext, synth
+    seed = synth.BASE_SEED if seed is None else seed
+    reqs = synth.serving_stream(count=count, rate=1.0, seed=seed, side_lo=side_lo, side_hi=side_hi)
+    probs = [r.problem for r in reqs]
+    unit_t = [r.arrival_s for r in reqs]  # arrivals at 1 request/s; scaled per offered rate
+    maxit = 40 * max(p.nx for p in probs)
+    ctx = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, maxit=maxit))
+    dprobs = [ext.problem_of(p) for p in probs]
+    phis = [torch.from_numpy(p.phi).cuda() for p in probs]
+    fs = [torch.from_numpy(p.f).cuda() for p in probs]
+    outs = [torch.empty_like(x) for x in phis]
+    seen = set()
+    for p, dp, f in zip(probs, dprobs, fs):
+        key = (p.nx, p.bc_x)
+        if key in seen:
+            continue
+        seen.add(key)
+        allk = torch.full((p.ny, p.nx), -1.0 if p.direction == "out" else 1.0, device="cuda")
+        ext.ext_solve(ctx, dp, allk, f, torch.empty_like(allk), check=False)
+
+    def offer(times):
+        t0 = time.perf_counter()
+        tickets = []
+        for k in range(len(probs)):
+            while time.perf_counter() - t0 < times[k]:
+                time.sleep(5e-5)
+            tickets.append(ext.ext_submit(ctx, dprobs[k], phis[k], fs[k], outs[k]))
+        ext.ext_drain(ctx)
+        wall = time.perf_counter() - t0
+        res = [ext.ext_poll(ctx, t) for t in tickets]
+        lat = sorted(r["ms_queue"] + r["ms_solve"] for r in res)
+        ok = sum(1 for r in res if r["rc"] == 0)
+        return {"solves_per_s": round(ok / wall, 3), "p50_ms": round(lat[len(lat) // 2], 2),
+                "p99_ms": round(lat[int(0.99 * (len(lat) - 1))], 2), "requests": len(res),
+                "converged": ok, "wall_s": round(wall, 2),
+                "iterations_median": statistics.median(r["iters"] for r in res)}
+
+    sat = offer([0.0] * len(probs))
+    cap = sat["solves_per_s"]
+    low_rate = 0.5 * cap
+    low = offer([t / low_rate for t in unit_t])
+    ext.ext_destroy(ctx)
+    # the serial plain FP32 path on the same requests, in arrival order, within a time budget
+    pctx = ext.ext_create(ext.options("fp32", rtol=1e-8, maxit=maxit))
+    done, t0 = 0, time.perf_counter()
+    for dp, ph, f, o in zip(dprobs, phis, fs, outs):
+        ext.ext_solve(pctx, dp, ph, f, o, check=False)
+        done += 1
+        if time.perf_counter() - t0 > plain_budget_s:
+            break
+    el = time.perf_counter() - t0
+    ext.ext_destroy(pctx)
+    sides = sorted(p.nx for p in probs)
+    return {"workload": f"serve{count}_poisson_sides{side_lo}-{side_hi}_star_or_circles_mixed_bf16",
+            "sides": {"min": sides[0], "median": sides[len(sides) // 2], "max": sides[-1]},
+            "saturated": dict(sat, offered="all requests at once"),
+            "below_saturation": dict(low, offered_rate_per_s=round(low_rate, 3),
+                                     offered="Poisson arrivals at half the saturated throughput"),
+            "p50_ms": low["p50_ms"], "p99_ms": low["p99_ms"],
+            "serial_plain_fp32": {"solves_per_s": round(done / el, 4), "requests": done,
+                                  "sample": f"first {done} requests in arrival order, one "
+                                            f"ext_solve each, FP32 path ({el:.1f} s)"}}
+
+
 def oracle_pcg_iterations(probs, batched_iters, sample_iters, count=3, budget_s=20.0):
     """Iterations of the oracle's FP64 PCG (the same fast Poisson preconditioner and
     Fletcher-Reeves beta, rel-res 1e-8) beside the GPU's on the first grids of the workload."""
@@ -539,6 +617,8 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         dist.init_process_group("nccl")
     out, probs, answers, (sample_answers, sample_iters) = run_ours(args, rank, world)
+    if rank == 0 and args.workload == "batch" and args.serve_requests > 0:
+        out["serving"] = serving_leg(count=args.serve_requests)
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"], refs = cpu_baseline(args, probs)
