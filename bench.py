@@ -256,6 +256,7 @@ def run_ours(args, rank, world):
         step_ms.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     launches = ext.ext_launch_count(ctx) - launches0
+    tile = ext.ext_stencil_tile(ctx)
     # answers of the last timed step, for the error against the oracle (later passes reuse outs)
     answers = [o.cpu().numpy() for o in outs[:32]]
     clk = clocks.stop()
@@ -429,6 +430,7 @@ def run_ours(args, rank, world):
            "all_converged": all(r.get("status", 0) == 0 for r in results),
            "plain_fp32_single_solve": plain, "same_grids": same_grids, "serving": serving,
            "e2e": e2e, "roofline": roofline, "hbm_kernels": kernels_hbm, "kernels": kernels,
+           "stencil_tile": {"x": tile[0], "y": tile[1], "chosen_by": "autotuner"},
            "gpu_launches": launches, "clocks": clk}
     return out, probs, answers, (sample_answers, sample_iters)
 
@@ -528,10 +530,13 @@ def serving_leg(count=48, seed=None, side_lo=64, side_hi=2048, plain_budget_s=20
     low_rate = 0.5 * cap
     low = offer([t / low_rate for t in unit_t])
     ext.ext_destroy(ctx)
-    # the serial plain FP32 path on the same requests, in arrival order, within a time budget
+    # the serial plain FP32 path on the same requests (those with sides up to 512: a single
+    # large request alone takes the path a minute), in arrival order, within a time budget
     pctx = ext.ext_create(ext.options("fp32", rtol=1e-8, maxit=maxit))
     done, t0 = 0, time.perf_counter()
-    for dp, ph, f, o in zip(dprobs, phis, fs, outs):
+    for p, dp, ph, f, o in zip(probs, dprobs, phis, fs, outs):
+        if p.nx > 512:
+            continue
         ext.ext_solve(pctx, dp, ph, f, o, check=False)
         done += 1
         if time.perf_counter() - t0 > plain_budget_s:
@@ -546,8 +551,9 @@ def serving_leg(count=48, seed=None, side_lo=64, side_hi=2048, plain_budget_s=20
                                      offered="Poisson arrivals at half the saturated throughput"),
             "p50_ms": low["p50_ms"], "p99_ms": low["p99_ms"],
             "serial_plain_fp32": {"solves_per_s": round(done / el, 4), "requests": done,
-                                  "sample": f"first {done} requests in arrival order, one "
-                                            f"ext_solve each, FP32 path ({el:.1f} s)"}}
+                                  "sample": f"first {done} requests with sides up to 512 in "
+                                            f"arrival order, one ext_solve each, FP32 path "
+                                            f"({el:.1f} s)"}}
 
 
 def oracle_pcg_iterations(probs, batched_iters, sample_iters, count=3, budget_s=20.0):

@@ -81,6 +81,16 @@ typedef struct {
   int32_t max_slots;       /* serving: most requests in flight at once; default 256            */
   int32_t profile;         /* 1: launch every kernel directly (no CUDA graphs) and time each one
                               with CUDA events on the context stream (ext_profile_read); 0    */
+  int32_t autotune;        /* 1: the stencil's tile height (16 or 32 rows of 64 nodes) is chosen
+                              per workspace shape by timing both on the first solve, and kept in
+                              a process-wide table and, if the environment variable
+                              EXT_TUNE_CACHE names a file, in that file; 0: tile_y; default 1.
+                              Results do not depend on the tile.                              */
+  int32_t tile_y;          /* the stencil's tile height when autotune = 0: 16 or 32 (default) */
+  int64_t wait_cycles;     /* bound, in SM clock cycles, of every wait of a kernel for its own
+                              tensor copies and tensor-core pipeline; a wait that runs out makes
+                              the kernel drain what it issued and return, and the call returns
+                              EXT_ETIMEOUT; 0 = 4e9 (about two seconds)                       */
 } ext_options;
 
 /* Kernel kinds reported by ext_profile_read. */
@@ -109,6 +119,10 @@ typedef struct {
   int32_t n_known;     /* |Omega|                                                              */
   double ms_queue;     /* serving: submit -> admission                                         */
   double ms_solve;     /* admission (or call start) -> result written                          */
+  double err_est;      /* estimated relative A-norm error ||x* - x||_A / ||x*||_A of the returned
+                          iterate: CG's step terms alpha_j rho_j (rho = r.z) of the last 8
+                          iterations over their sum over all iterations (the Hestenes-Stiefel
+                          estimate with a delay of 8; 0 when no iteration ran)                 */
 } ext_result;
 
 enum {
@@ -147,6 +161,14 @@ int ext_solve(ext_ctx* ctx, const ext_problem* prob, const float* phi, const flo
 int ext_solve_batch(ext_ctx* ctx, int count, const ext_problem* probs, const float* const* phi,
                     const float* const* f, float* const* out, ext_result* results);
 
+/* Several fields known on the same Omega (one phi, e.g. the components of a velocity field, as in
+ * the level-set application of Sec. 5 of the paper, where each step extends more than one field):
+ * f[i] and out[i], i < count, are the fields and their extensions; phi, the problem and the
+ * transform plans are shared and the fields iterate together in the same launches.  Each result
+ * equals ext_solve of that field alone.  Pointers as for ext_solve_batch. */
+int ext_solve_multi(ext_ctx* ctx, const ext_problem* prob, const float* phi, int count,
+                    const float* const* f, float* const* out, ext_result* results);
+
 /* Serving: enqueue one request (returns at once with a ticket).  A device-resident loop admits
  * queued requests as slots and HBM free up (continuous batching: new requests join the
  * iterations of those already running).  Thread-safe. */
@@ -171,6 +193,9 @@ int ext_profile_read(ext_ctx* ctx, int kinds, double* total_ms, int64_t* launche
 
 /* Number of kernels this context has launched (graph replays count every kernel node). */
 int64_t ext_launch_count(ext_ctx* ctx);
+
+/* Stencil tile (x by y nodes) of the workspace the context's last solve used. */
+int ext_stencil_tile(ext_ctx* ctx, int32_t* tile_x, int32_t* tile_y);
 
 /* Text of the last CUDA or allocation failure seen by the calling thread ("" if none). */
 const char* ext_last_error(void);

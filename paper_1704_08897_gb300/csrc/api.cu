@@ -20,6 +20,7 @@
 #include <cmath>
 #include <condition_variable>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -80,8 +81,13 @@ struct Workspace {
   SlotScalars* h_sc = nullptr;  // pinned
   WorkItem *d_st = nullptr, *d_vec = nullptr, *d_gm = nullptr;
   WorkItem* d_sl = nullptr;     // one item per slot (tile 0), for the per-slot scalar kernels
-  int *d_counts = nullptr;      // [0] stencil items, [1] vector items, [2] gemm items, [3] slots
+  int *d_counts = nullptr;      // [0] grid tiles, [1] vector items, [2] gemm items, [3] slots,
+                                // [4] stencil tiles
   int n_st = 0, n_vec = 0, n_gm = 0, n_sl = 0;
+  WorkItem* d_sten = nullptr;   // the stencil kernel's tiles (64 x sten_ty)
+  int n_sten = 0;
+  int sten_ty = 32;             // stencil tile height of this workspace (autotuned)
+  bool tuned = false;
   const float** d_phis = nullptr;
   const float** d_fs = nullptr;
   float** d_outs = nullptr;
@@ -124,6 +130,7 @@ struct ext_ctx {
   std::vector<cudaEvent_t> ev_pool;
   double prof_ms[EXT_KERNEL_KINDS] = {0};
   int64_t prof_n[EXT_KERNEL_KINDS] = {0};
+  int last_tile_y = 0;  // stencil tile height of the last solve's workspace
   // serving
   struct Serve;
   Serve* serve = nullptr;
@@ -218,15 +225,15 @@ static int make_tmap(CUtensorMap* m, void* base, bool bf16, uint64_t inner, uint
 // (two extra columns on the left keep each copy's start on a 16-byte boundary) and the mask as
 // 8-bit boxes of the tile.  The mask rows must span a multiple of 16 bytes (nx % 16 == 0).
 static bool stencil_copies_fit(int nx) { return nx % 16 == 0; }
-static int make_stencil_maps(CUtensorMap (&m)[kStMaps], const SlotDesc& d) {
-  const uint32_t wx = kStWinX, wy = kStWinY;
+static int make_stencil_maps(CUtensorMap (&m)[kStMaps], const SlotDesc& d, int ty) {
+  const uint32_t wx = kStWinX, wy = (uint32_t)ty + 4;
   float* const vec[6] = {d.z, d.z_lo, d.p[0], d.p_lo[0], d.p[1], d.p_lo[1]};
   for (int k = 0; k < 6; ++k) {
     const int rc = make_tmap_2d(&m[k], vec[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, d.nx, d.ny, wx, wy,
                                 CU_TENSOR_MAP_SWIZZLE_NONE);
     if (rc) return rc;
   }
-  return make_tmap_2d(&m[6], d.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.nx, d.ny, kStTileX, kStTileY,
+  return make_tmap_2d(&m[6], d.mask, CU_TENSOR_MAP_DATA_TYPE_UINT8, 1, d.nx, d.ny, kStTileX, (uint32_t)ty,
                       CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
@@ -375,6 +382,7 @@ static void free_workspace(Workspace* W) {
   cudaFree(W->d_slots);
   cudaFree(W->d_sc);
   cudaFree(W->d_st);
+  cudaFree(W->d_sten);
   cudaFree(W->d_vec);
   cudaFree(W->d_gm);
   cudaFree(W->d_sl);
@@ -421,6 +429,8 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.bcx = prob.bc_x;
   d.bcy = prob.bc_y;
   d.n_st_tiles = ((nx + kStTileX - 1) / kStTileX) * ((ny + kStTileY - 1) / kStTileY);
+  d.sten_ty = 32;
+  d.n_sten_tiles = d.n_st_tiles;
   const size_t N = (size_t)nx * ny;
   d.n_vec_items = (int)((N + kVecChunk - 1) / kVecChunk);
   const int n_gm = (d.nxp / 128) * (d.nyp / 64);
@@ -433,6 +443,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const size_t o_b = take(8 * N), o_x = take(4 * N), o_xl = take(4 * N);
   const size_t o_part = take(8 * 4 * (size_t)n_part);
+  const size_t o_pqp = take(8 * (size_t)ny * ((nx + 31) / 32));
   const size_t o_r = take(4 * N), o_p0 = take(4 * N), o_p1 = take(4 * N);
   const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
   const size_t o_rl = take(4 * N), o_p0l = take(4 * N), o_p1l = take(4 * N);
@@ -471,6 +482,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.xhi = (float*)(A + o_x);
   d.xlo = (float*)(A + o_xl);  // own 256-byte aligned slot: the update kernel loads float4
   d.part = (double*)(A + o_part);
+  d.pq_part = (double*)(A + o_pqp);
   d.r = (float*)(A + o_r);
   d.p[0] = (float*)(A + o_p0);
   d.p[1] = (float*)(A + o_p1);
@@ -492,7 +504,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.st_maps = nullptr;
   if (st_copy) {
     CUtensorMap smaps[kStMaps];
-    const int rc1 = make_stencil_maps(smaps, d);
+    const int rc1 = make_stencil_maps(smaps, d, d.sten_ty);
     if (rc1) return rc1;
     BX_CUDA(cudaMemcpy(A + o_smaps, smaps, sizeof(smaps), cudaMemcpyHostToDevice));
     d.st_maps = A + o_smaps;
@@ -618,7 +630,10 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   BX_CUDA(cudaMemcpy(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * sl.size()));
   BX_CUDA(cudaMemcpy(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice));
-  int counts[4] = {W->n_st, W->n_vec, W->n_gm, W->n_sl};
+  W->n_sten = W->n_st;
+  BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * st.size()));
+  BX_CUDA(cudaMemcpy(W->d_sten, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice));
+  int counts[5] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten};
   BX_CUDA(cudaMalloc(&W->d_counts, sizeof(counts)));
   BX_CUDA(cudaMemcpy(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * count));
@@ -654,6 +669,7 @@ static int get_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bool
 
 static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
   LaunchCfg c;
+  c.wait_cycles = ctx->opt.wait_cycles;
   c.slots = W->d_slots;
   c.stream = W->stream ? W->stream : ctx->stream;
   const int cap = ctx->sm_count * 8;
@@ -669,6 +685,11 @@ static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
     c.items = W->d_sl;
     c.n_items = W->d_counts + 3;
     c.grid = std::max(1, std::min(W->n_sl, cap));
+  } else if (which == 4) {
+    // persistent: the resident blocks, each double-buffering its tiles
+    c.items = W->d_sten;
+    c.n_items = W->d_counts + 4;
+    c.grid = std::max(1, std::min(W->n_sten, ctx->sm_count * stencil_blocks_per_sm(W->sten_ty)));
   } else {
     c.items = W->d_gm;
     c.n_items = W->d_counts + 2;
@@ -755,10 +776,9 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
 
 static void enqueue_iterations(ext_ctx* ctx, Workspace* W, int iters) {
   const LaunchCfg st = cfg_of(ctx, W, 0), vc = cfg_of(ctx, W, 1);
-  LaunchCfg sc = st;  // persistent: the resident blocks, each double-buffering its tiles
-  sc.grid = std::max(1, std::min(W->n_st, ctx->sm_count * stencil_blocks_per_sm()));
+  const LaunchCfg sc = cfg_of(ctx, W, 4);
   for (int i = 0; i < iters; ++i) {
-    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, ctx->d_err); }, st.stream);
+    timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, W->sten_ty, ctx->d_err); }, st.stream);
     const LaunchCfg pf = cfg_of(ctx, W, 3);  // one block per slot
     timed(ctx, EXT_KERNEL_PQ_FINISH, [&] { launch_pq_finish(pf); }, st.stream);
     timed(ctx, EXT_KERNEL_UPDATE, [&] { launch_update(vc); }, st.stream);
@@ -808,6 +828,134 @@ static int ensure_graph(ext_ctx* ctx, Workspace* W) {
   }
   W->graph_iters = G;
   return EXT_OK;
+}
+
+// ---- stencil tile shape and its autotuner ----------------------------------------------------
+// Re-tile the stencil of every slot of W with tiles 64 x ty: the work list, the tile counts and
+// the tensor maps' box heights.  The p.q partials do not depend on the tile (32-node row
+// segments), so any shape gives the same results.
+static int set_stencil_shape(ext_ctx* ctx, Workspace* W, int ty) {
+  if (W->sten_ty == ty) return EXT_OK;
+  cudaStream_t s = W->stream ? W->stream : ctx->stream;
+  BX_CUDA(cudaStreamSynchronize(s));
+  std::vector<WorkItem> sten;
+  std::vector<SlotDesc> descs;
+  for (int i = 0; i < (int)W->slots.size(); ++i) {
+    SlotDesc& d = W->slots[i].d;
+    d.sten_ty = ty;
+    d.n_sten_tiles = ((d.nx + kStTileX - 1) / kStTileX) * ((d.ny + ty - 1) / ty);
+    for (int t = 0; t < d.n_sten_tiles; ++t) sten.push_back({i, t});
+    if (d.st_maps) {
+      CUtensorMap m[kStMaps];
+      const int rc = make_stencil_maps(m, d, ty);
+      if (rc) return rc;
+      BX_CUDA(cudaMemcpy(const_cast<void*>(d.st_maps), m, sizeof(m), cudaMemcpyHostToDevice));
+    }
+    descs.push_back(d);
+  }
+  cudaFree(W->d_sten);
+  W->d_sten = nullptr;
+  BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * sten.size()));
+  BX_CUDA(cudaMemcpy(W->d_sten, sten.data(), sizeof(WorkItem) * sten.size(), cudaMemcpyHostToDevice));
+  W->n_sten = (int)sten.size();
+  BX_CUDA(cudaMemcpy(W->d_counts + 4, &W->n_sten, sizeof(int), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(W->d_slots, descs.data(), sizeof(SlotDesc) * descs.size(), cudaMemcpyHostToDevice));
+  W->sten_ty = ty;
+  if (W->graph) {
+    cudaGraphExecDestroy(W->graph);
+    W->graph = nullptr;
+  }
+  return EXT_OK;
+}
+
+// Tuning results by workspace shape, shared by the contexts of the process and, when the
+// environment variable EXT_TUNE_CACHE names a file, kept there (one "key tile_y" line each).
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune;
+bool g_tune_loaded = false;
+
+std::string tune_key(const Workspace* W) {
+  char buf[32];
+  snprintf(buf, sizeof(buf), "%016llx", (unsigned long long)std::hash<std::string>{}(W->key));
+  return buf;
+}
+
+int tune_lookup(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  if (!g_tune_loaded) {
+    g_tune_loaded = true;
+    if (const char* path = std::getenv("EXT_TUNE_CACHE")) {
+      if (FILE* f = std::fopen(path, "r")) {
+        char k[64];
+        int ty = 0;
+        while (std::fscanf(f, "%63s %d", k, &ty) == 2)
+          if (ty == 16 || ty == 32) g_tune[k] = ty;
+        std::fclose(f);
+      }
+    }
+  }
+  auto it = g_tune.find(key);
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+void tune_store(const std::string& key, int ty) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = ty;
+  if (const char* path = std::getenv("EXT_TUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s %d\n", key.c_str(), ty);
+      std::fclose(f);
+    }
+  }
+}
+}  // namespace
+
+// Choose the stencil tile height of W: from the cache, or by timing each candidate on the
+// workspace's own slots right after their set-up (iteration 0: beta = 0 and z = 0, so the
+// launches write zeros that the first iteration overwrites).
+static int autotune_stencil(ext_ctx* ctx, Workspace* W) {
+  const std::string key = tune_key(W);
+  int ty = tune_lookup(key);
+  if (!ty) {
+    cudaStream_t s = W->stream ? W->stream : ctx->stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    BX_CUDA(cudaEventCreate(&e0));
+    BX_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    for (int cand : {32, 16}) {
+      int rc = set_stencil_shape(ctx, W, cand);
+      if (rc) return rc;
+      const LaunchCfg sc = cfg_of(ctx, W, 4);
+      launch_stencil(sc, W->aniso, cand, ctx->d_err);  // warm
+      BX_CUDA(cudaEventRecord(e0, s));
+      constexpr int kReps = 5;
+      for (int r = 0; r < kReps; ++r) launch_stencil(sc, W->aniso, cand, ctx->d_err);
+      BX_CUDA(cudaEventRecord(e1, s));
+      BX_CUDA(cudaEventSynchronize(e1));
+      ctx->launches += kReps + 1;
+      float ms = 0.f;
+      BX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        ty = cand;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    tune_store(key, ty);
+  }
+  W->tuned = true;
+  return set_stencil_shape(ctx, W, ty);
+}
+
+// Relative A-norm error estimate of the returned iterate from the CG step terms alpha_j rho_j.
+static double err_estimate(const SlotScalars& sc) {
+  if (!(sc.aro_total > 0.0)) return 0.0;
+  double tail = 0.0;
+  const int n = std::min(sc.aro_n, kErrDelay);
+  for (int i = 0; i < n; ++i) tail += sc.aro_ring[i];
+  return std::sqrt(tail / sc.aro_total);
 }
 
 static int map_status(int st, int n_known, const ext_problem& p) {
@@ -862,10 +1010,16 @@ static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const
     sc.status = ST_RUNNING;
   }
   BX_CUDA(cudaMemcpyAsync(W->d_sc, W->h_sc, sizeof(SlotScalars) * count, cudaMemcpyHostToDevice, s));
-  int rc = ensure_graph(ctx, W);
+  int rc = EXT_OK;
+  if (!ctx->opt.autotune) rc = set_stencil_shape(ctx, W, ctx->opt.tile_y == 16 ? 16 : 32);
   if (rc) return rc;
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_setup(cfg_of(ctx, W, 0), W->d_phis, W->d_fs, W->d_dirs); });
   timed(ctx, EXT_KERNEL_SETUP, [&] { launch_rhs_scale(cfg_of(ctx, W, 0)); });
+  if (ctx->opt.autotune && !W->tuned) rc = autotune_stencil(ctx, W);
+  if (rc) return rc;
+  ctx->last_tile_y = W->sten_ty;
+  rc = ensure_graph(ctx, W);
+  if (rc) return rc;
   launch_prec(ctx, W, 1);
   BX_CUDA(cudaGetLastError());
   int max_blocks = 0;
@@ -929,6 +1083,7 @@ static int run_solve(ext_ctx* ctx, Workspace* W, const float* const* phis, const
       r.n_unknown = p.nx * p.ny - sc.n_known;
       r.ms_queue = 0.0;
       r.ms_solve = ms;
+      r.err_est = err_estimate(sc);
     }
     if (st != EXT_OK && worst == EXT_OK) worst = st;
   }
@@ -952,6 +1107,8 @@ void ext_options_default(ext_options* o) {
   o->hbm_budget = 0;
   o->flexible = 0;
   o->max_slots = 256;
+  o->autotune = 1;
+  o->tile_y = 32;
 }
 
 const char* ext_strerror(int code) {
@@ -1076,6 +1233,16 @@ int ext_solve_batch(ext_ctx* ctx, int count, const ext_problem* probs, const flo
   return run_solve(ctx, W, phi, f, out, dirs.data(), results);
 }
 
+int ext_solve_multi(ext_ctx* ctx, const ext_problem* prob, const float* phi, int count,
+                    const float* const* f, float* const* out, ext_result* results) {
+  if (!ctx || !prob || !phi || count <= 0 || !f || !out) return EXT_EINVAL;
+  // every field is one slot of the same shape reading the same phi: one workspace shape, one pair
+  // of transform plans, and all fields iterate together in the same launches
+  std::vector<ext_problem> probs(count, *prob);
+  std::vector<const float*> phis(count, phi);
+  return ext_solve_batch(ctx, count, probs.data(), phis.data(), f, out, results);
+}
+
 int ext_solve(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f, float* out,
               ext_result* res) {
   const float* phis[1] = {phi};
@@ -1119,6 +1286,13 @@ int ext_profile_read(ext_ctx* ctx, int kinds, double* total_ms, int64_t* launche
 
 int64_t ext_launch_count(ext_ctx* ctx) { return ctx ? ctx->launches.load() : 0; }
 
+int ext_stencil_tile(ext_ctx* ctx, int32_t* tile_x, int32_t* tile_y) {
+  if (!ctx) return EXT_EINVAL;
+  if (tile_x) *tile_x = kStTileX;
+  if (tile_y) *tile_y = ctx->last_tile_y;
+  return EXT_OK;
+}
+
 // ---- verification entry points (device pointers) ----
 
 static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi, const float* f,
@@ -1128,6 +1302,8 @@ static int single_setup(ext_ctx* ctx, const ext_problem* prob, const float* phi,
   if (!is_device_ptr(phi) || !is_device_ptr(f)) return EXT_EINVAL;
   Workspace* W = nullptr;
   rc = get_workspace(ctx, 1, prob, false, &W);
+  if (rc) return rc;
+  if (!ctx->opt.autotune) rc = set_stencil_shape(ctx, W, ctx->opt.tile_y == 16 ? 16 : 32);
   if (rc) return rc;
   cudaStream_t s = ctx->stream;
   const float** h_phis = (const float**)W->h_ptrs;
@@ -1173,13 +1349,12 @@ int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi
   BX_CUDA(cudaMemcpyAsync(dsc + offsetof(SlotScalars, it), &it0, sizeof(int), cudaMemcpyHostToDevice, s));
   BX_CUDA(cudaMemcpyAsync(dsc + offsetof(SlotScalars, active), &on, sizeof(int), cudaMemcpyHostToDevice, s));
   BX_CUDA(cudaMemcpyAsync(dsc + offsetof(SlotScalars, beta), &zero, sizeof(double), cudaMemcpyHostToDevice, s));
-  LaunchCfg sc = cfg_of(ctx, W, 0);
-  sc.grid = std::max(1, std::min(W->n_st, ctx->sm_count * stencil_blocks_per_sm()));
-  timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, ctx->d_err); });
+  const LaunchCfg sc = cfg_of(ctx, W, 4);
+  timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, W->sten_ty, ctx->d_err); });
   BX_CUDA(cudaGetLastError());
   BX_CUDA(cudaMemcpyAsync(q, sl.d.q, 4 * N, cudaMemcpyDeviceToDevice, s));
-  std::vector<double> part(4 * (size_t)sl.d.n_st_tiles);
-  BX_CUDA(cudaMemcpyAsync(part.data(), sl.d.part, 8 * part.size(), cudaMemcpyDeviceToHost, s));
+  std::vector<double> part((size_t)prob->ny * ((prob->nx + 31) / 32));
+  BX_CUDA(cudaMemcpyAsync(part.data(), sl.d.pq_part, 8 * part.size(), cudaMemcpyDeviceToHost, s));
   BX_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   BX_CUDA(cudaStreamSynchronize(s));
   if (*ctx->h_err) {
@@ -1190,7 +1365,7 @@ int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi
   }
   if (sum_pq) {
     double acc = 0.0;
-    for (int t = 0; t < sl.d.n_st_tiles; ++t) acc += part[4 * (size_t)t + 1];
+    for (double v : part) acc += v;
     *sum_pq = acc;
   }
   return EXT_OK;
@@ -1294,18 +1469,20 @@ struct ext_ctx::Serve {
 static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
   Workspace* W = S->W;
   cudaFree(W->d_st);
+  cudaFree(W->d_sten);
   cudaFree(W->d_vec);
   cudaFree(W->d_gm);
   cudaFree(S->d_new);
   cudaFree(S->d_ret);
-  W->d_st = W->d_vec = W->d_gm = S->d_new = S->d_ret = nullptr;
+  W->d_st = W->d_sten = W->d_vec = W->d_gm = S->d_new = S->d_ret = nullptr;
   BX_CUDA(cudaMalloc(&W->d_st, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_vec, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_gm, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&S->d_new, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&S->d_ret, sizeof(WorkItem) * cap));
   S->cap_items = cap;
-  W->n_st = W->n_vec = W->n_gm = cap;  // persistent grids sized for the capacity
+  W->n_st = W->n_vec = W->n_gm = W->n_sten = cap;  // persistent grids sized for the capacity
   if (W->graph) {
     cudaGraphExecDestroy(W->graph);
     W->graph = nullptr;
@@ -1326,8 +1503,8 @@ static int serve_init(ext_ctx* ctx) {
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * cap));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * cap));
   memset(W->h_sc, 0, sizeof(SlotScalars) * cap);
-  BX_CUDA(cudaMalloc(&W->d_counts, 4 * sizeof(int)));
-  BX_CUDA(cudaMemset(W->d_counts, 0, 4 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_counts, 5 * sizeof(int)));
+  BX_CUDA(cudaMemset(W->d_counts, 0, 5 * sizeof(int)));
   BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * cap));
   W->n_sl = cap;  // the per-slot grid is sized for the slot table
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * cap));
@@ -1377,10 +1554,12 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
   W->aniso = aniso;
   cudaStream_t s = W->stream;
   if (!st.empty()) BX_CUDA(cudaMemcpyAsync(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice, s));
+  // the serving table keeps the 64 x 32 stencil tiles: its stencil list is the grid-tile list
+  if (!st.empty()) BX_CUDA(cudaMemcpyAsync(W->d_sten, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice, s));
   if (!vec.empty()) BX_CUDA(cudaMemcpyAsync(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice, s));
   if (!gm.empty()) BX_CUDA(cudaMemcpyAsync(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice, s));
   if (!sl.empty()) BX_CUDA(cudaMemcpyAsync(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice, s));
-  int counts[4] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size()};
+  int counts[5] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size()};
   BX_CUDA(cudaMemcpyAsync(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
   // the host vectors die here: the copies above must finish first (pageable sources are staged)
   BX_CUDA(cudaStreamSynchronize(s));
@@ -1540,6 +1719,7 @@ static int serve_retire(ext_ctx* ctx, const std::vector<int>& done) {
     r->res.n_unknown = r->prob.nx * r->prob.ny - sc.n_known;
     r->res.ms_queue = std::chrono::duration<double, std::milli>(r->t_admit - r->t_submit).count();
     r->res.ms_solve = std::chrono::duration<double, std::milli>(now - r->t_admit).count();
+    r->res.err_est = err_estimate(sc);
     S->pool.emplace(S->slots[i].bytes, W->slots[i].arena);
     W->slots[i].arena = nullptr;
     S->used -= S->slots[i].bytes;

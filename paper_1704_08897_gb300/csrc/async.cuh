@@ -39,12 +39,29 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase of the given parity; false on time-out or when another role aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Non-blocking test of the same phase.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase of the given parity (at most `budget` SM clock cycles); false on
+// time-out or when another role aborted.  Budgets shorter than the suspend hint poll with the
+// non-blocking test, so that they run out as set.
+constexpr long long kShortBudget = 100000;
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          long long budget = kWaitCycles) {
   const long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
+  const bool short_budget = budget < kShortBudget;
+  while (!(short_budget ? mbar_test(bar, parity) : mbar_try(bar, parity))) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       return false;
     }

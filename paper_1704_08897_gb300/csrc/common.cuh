@@ -53,13 +53,22 @@ struct __align__(16) SlotScalars {
   int n_known;      // known nodes, counted by the set-up kernel
   int bexp;         // the iteration solves A x' = 2^bexp b; the answer is x = 2^-bexp x'
   double rho_prev;  // r.z of the previous iteration (Fletcher-Reeves beta)
+  // error estimate: in CG, ||x* - x_k||_A^2 = sum_{j >= k} alpha_j rho_j, so the terms of the last
+  // kErrDelay iterations over the sum of all terms estimate the relative A-norm error of the
+  // iterate kErrDelay steps before the end (an upper estimate for the returned one)
+  double aro_total;
+  double aro_ring[8];
+  int aro_n;
 };
+constexpr int kErrDelay = 8;
 
 // Static description of one slot (device copy).  Padded transform dims are multiples of kPad.
 struct SlotDesc {
   int nx, ny, nxp, nyp;
   int bcx, bcy;
-  int n_st_tiles;    // stencil tiles: ceil(nx/64) * ceil(ny/32)
+  int n_st_tiles;    // grid tiles of the set-up, residual and slicing kernels: ceil(nx/64) * ceil(ny/32)
+  int n_sten_tiles;  // tiles of the stencil kernel: ceil(nx/64) * ceil(ny/sten_ty)
+  int sten_ty;       // the stencil kernel's tile height (16 or 32)
   int n_vec_items;   // vector chunks: ceil(nx*ny / kVecChunk)
   int n_gm_tiles;    // output tiles of one transform stage
   float wc, wex, wey, wd, wfx, wfy;  // stencil weights (hi), scaled so that max(a, c) = 1
@@ -110,6 +119,7 @@ struct SlotDesc {
   int n_tc_tiles;    // output tiles of one tensor-core transform stage
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
+  double* pq_part;   // p.q partial sums of the stencil, one per 32-node row segment [ny][nx/32]
 };
 
 struct WorkItem {

@@ -14,6 +14,7 @@ struct LaunchCfg {
   const int* n_items;      // device count of valid items (persistent kernels read it)
   int grid;
   cudaStream_t stream;
+  long long wait_cycles = 0;  // bound of the kernels' pipeline waits (0: the default bound)
 };
 
 // host helpers (api.cu): stencil weights of (L_y (+) L_x)^2 for spacings hx, hy; the problem
@@ -27,9 +28,9 @@ bool is_device_ptr(const void* p);
 void launch_setup(const LaunchCfg& c, const float* const* phis, const float* const* fs,
                   const int* dirs);
 void launch_rhs_scale(const LaunchCfg& c);
-// err receives 1 if a bounded wait for a tensor copy ran out
-void launch_stencil(const LaunchCfg& c, bool aniso, int* err);
-int stencil_blocks_per_sm();
+// err receives 1 if a bounded wait for a tensor copy ran out; tile_y = 16 or 32 (tiles 64 wide)
+void launch_stencil(const LaunchCfg& c, bool aniso, int tile_y, int* err);
+int stencil_blocks_per_sm(int tile_y);
 // shared-memory carveout of the stencil kernels (once per process and device)
 cudaError_t stencil_init();
 // per-slot p.q -> alpha (after the stencil)

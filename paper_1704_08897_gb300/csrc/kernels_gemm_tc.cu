@@ -248,7 +248,7 @@ __device__ __forceinline__ TcStage tc_stage(const SlotDesc& S, int stage) {
 template <bool BF16, int STAGE>
 __global__ void __maxnreg__(kMaxRegs)
 k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
-          const int* __restrict__ n_items, int mode, int* __restrict__ err) {
+          const int* __restrict__ n_items, int mode, int* __restrict__ err, long long wait_cycles) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -299,7 +299,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const int mt = v.M / BM;
         const int m0 = (it.tile % mt) * BM, n0 = (it.tile / mt) * BN;
         for (int kb = 0; kb < v.K / BK; ++kb) {
-          if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_flag)) break;
+          if (!mbar_wait(&ctl->empty[stage], phase ^ 1, abort_flag, wait_cycles)) break;
           mbar_expect_tx(&ctl->full[stage], STAGE_BYTES);
           unsigned char* sa = smem + stage * STAGE_BYTES;
           unsigned char* sb = sa + NS * A_PLANE;
@@ -346,8 +346,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         for (int kb = 0; kb < v.K / BK; ++kb) {
           const int half_kb = kb % KPC;  // position inside the accumulation block
           const int cb = chunk % kChunks;
-          if ((half_kb == 0 && !mbar_wait(&ctl->tempty[cb], ((chunk / kChunks) & 1) ^ 1, abort_flag)) ||
-              !mbar_wait(&ctl->full[stage], phase, abort_flag)) {
+          if ((half_kb == 0 &&
+               !mbar_wait(&ctl->tempty[cb], ((chunk / kChunks) & 1) ^ 1, abort_flag, wait_cycles)) ||
+              !mbar_wait(&ctl->full[stage], phase, abort_flag, wait_cycles)) {
             ok = false;
             break;
           }
@@ -443,7 +444,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         const float sa = pow2f(static_cast<int>(ea_row[kb]) - 16);
         const float sb_mine = pow2f(eb_col[kb]);
         // all epilogue warps leave together if any of them gave up waiting
-        const uint32_t fail = mbar_wait(&ctl->tfull[cb], (chunk / kChunks) & 1, abort_flag) ? 0u : 1u;
+        const uint32_t fail =
+            mbar_wait(&ctl->tfull[cb], (chunk / kChunks) & 1, abort_flag, wait_cycles) ? 0u : 1u;
         uint32_t any_fail;
         asm volatile(
             "{\n\t.reg .pred p, q;\n\t"
@@ -722,11 +724,12 @@ cudaError_t set_attr() {
 
 template <bool BF16>
 void launch_all(const LaunchCfg& c, int stage, int mode, int* err) {
+  const long long wc = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
   switch (stage) {
-    case 0: k_prec_tc<BF16, 0><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
-    case 1: k_prec_tc<BF16, 1><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
-    case 2: k_prec_tc<BF16, 2><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
-    default: k_prec_tc<BF16, 3><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err); break;
+    case 0: k_prec_tc<BF16, 0><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc); break;
+    case 1: k_prec_tc<BF16, 1><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc); break;
+    case 2: k_prec_tc<BF16, 2><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc); break;
+    default: k_prec_tc<BF16, 3><<<c.grid, kThreads, SMEM_BYTES, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc); break;
   }
 }
 

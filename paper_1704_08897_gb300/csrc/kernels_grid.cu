@@ -275,67 +275,104 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
 
 // ---------------------------------------------------------------------------------------------
 // Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo, in
-// double-float), q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), per-tile
-// partial p.q; k_pq_finish then forms alpha = rho / p.q for each slot.
+// double-float), q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), and p.q as
+// partial sums over fixed 32-node row segments; k_pq_finish then forms alpha = rho / p.q.
 //
 // q is the double-float pair of the exact 13-point sum of p's hi plane (compensated FP32) plus
 // the same stencil of p's lo plane in plain FP32.
 //
-// Each block walks its share of the (slot, tile) list with two shared-memory window sets.  For a
-// slot whose rows span a multiple of 16 bytes in the mask (nx % 16 == 0), the window set of the
-// block's next tile arrives by tensor copies while it computes the current one: the hi and lo
-// planes of z and p_old over rows y0-2 .. y0+33 and columns x0-4 .. x0+67 (two columns wider on
-// the left than the halo, so that each copy starts on a 16-byte boundary) and the tile's mask
-// bytes.  Cells outside the grid arrive as zeros; the ghost cells of a boundary tile (reflected,
-// wrapped or negated copies of grid nodes under the boundary rule) are gathered by plain loads.
-// Tiles of other slots fill the free window set with plain loads.
+// Tiles are 64 nodes wide and TY rows high (TY = 16 or 32, chosen per workspace by the
+// autotuner).  Each block walks its share of the (slot, tile) list with two shared-memory window
+// sets.  For a slot whose rows span a multiple of 16 bytes in the mask (nx % 16 == 0), the window
+// set of the block's next tile arrives by tensor copies while it computes the current one: the hi
+// and lo planes of z and p_old over rows y0-2 .. y0+TY+1 and columns x0-4 .. x0+67 (two columns
+// wider on the left than the halo, so that each copy starts on a 16-byte boundary) and the tile's
+// mask bytes.  Cells outside the grid arrive as zeros; the ghost cells of a boundary tile
+// (reflected, wrapped or negated copies of grid nodes under the boundary rule) are gathered by
+// plain loads.  Tiles of other slots fill the free window set with plain loads.
+//
+// The p.q partials do not depend on TY: each 32-node row segment is summed by one half warp
+// (isotropic kernel, two nodes per lane) or one warp (anisotropic kernel) in a fixed butterfly,
+// and k_pq_finish adds the segments in index order, so every tile height gives the same bits.
 // ---------------------------------------------------------------------------------------------
-constexpr int kWX = kStWinX;                           // 72: window row, floats
-static_assert(kStWinY == kHY, "the window spans the halo rows");
-constexpr int kWinBytes = kWX * kHY * 4;               // one FP32 plane window
-constexpr int kMaskBytes = kStTileX * kStTileY;        // the tile's mask
-constexpr int kBufBytes = 4 * kWinBytes + kMaskBytes;  // one window set: z, z_lo, p, p_lo, mask
-static_assert(kWinBytes % 128 == 0 && kBufBytes % 128 == 0, "tensor copy destinations");
-constexpr int kGhostSlots = 4 * kHY + 4 * kHX;         // candidate ghost cells of one halo
-static_assert(kGhostSlots <= 2 * kStThreads, "two ghost candidates per thread");
-constexpr int kStBlocksPerSm = 2;
-constexpr int kStSmemBytes = 2 * kBufBytes + 128;      // dynamic: two window sets, alignment slack
+constexpr int kWX = kStWinX;  // 72: window row, floats
+static_assert(kStWinX == kStTileX + 8, "window columns");
+
+template <int TY>
+struct StGeom {
+  static constexpr int kHYt = TY + 4;                       // halo rows
+  static constexpr int kHalo = kHX * kHYt;                   // halo cells
+  static constexpr int kWinBytes = kWX * kHYt * 4;           // one FP32 plane window
+  static constexpr int kMaskBytes = kStTileX * TY;           // the tile's mask
+  static constexpr int kBufBytes = 4 * kWinBytes + kMaskBytes;  // z, z_lo, p, p_lo, mask
+  static constexpr int kGhostSlots = 4 * kHYt + 4 * kHX;     // candidate ghost cells of one halo
+  static constexpr int kBlocksPerSm = TY == 32 ? 2 : 3;
+  static constexpr int kSmemBytes = 2 * kBufBytes + 128;     // two window sets, alignment slack
+  static constexpr int kOwn = kStTileX * TY / kStThreads;    // nodes per thread
+  static_assert(kWinBytes % 128 == 0 && kBufBytes % 128 == 0, "tensor copy destinations");
+  static_assert(kGhostSlots <= 2 * kStThreads, "two ghost candidates per thread");
+  static_assert(kOwn * kStThreads == kStTileX * TY && kOwn % 2 == 0, "tile / block size");
+  static_assert(kBlocksPerSm * (kSmemBytes + 1024) <= 228 * 1024, "window sets per SM");
+};
+
+__device__ __forceinline__ void tile_origin_ty(const SlotDesc& S, int tile, int ty, int& x0, int& y0) {
+  const int tx = (S.nx + kStTileX - 1) / kStTileX;
+  x0 = (tile % tx) * kStTileX;
+  y0 = (tile / tx) * ty;
+}
 
 // Candidate k of a tile's ghost cells: the four ghost columns (x = -2, -1, nx, nx+1) over the
 // halo's rows, then the four ghost rows over the halo's in-grid columns.  Returns false when the
 // candidate lies outside the halo or beyond the second ghost line; (wy, wx) is its window cell.
+template <int TY>
 __device__ __forceinline__ bool ghost_cell(const SlotDesc& S, int x0, int y0, int k, int& wy,
                                            int& wx) {
-  if (k < 4 * kHY) {
-    const int j = k / kHY;
-    wy = k - j * kHY;
+  constexpr int kHYt = StGeom<TY>::kHYt;
+  if (k < 4 * kHYt) {
+    const int j = k / kHYt;
+    wy = k - j * kHYt;
     const int gx = j < 2 ? j - 2 : S.nx + (j - 2);
     const int lx = gx - (x0 - 2);
     wx = lx + 2;
     return lx >= 0 && lx < kHX && y0 - 2 + wy <= S.ny + 1;
   }
-  const int kk = k - 4 * kHY;
+  const int kk = k - 4 * kHYt;
   const int j = kk / kHX, lx = kk - j * kHX;
   const int gy = j < 2 ? j - 2 : S.ny + (j - 2);
   const int gx = x0 - 2 + lx;
   wy = gy - (y0 - 2);
   wx = lx + 2;
-  return wy >= 0 && wy < kHY && gx >= 0 && gx < S.nx;
+  return wy >= 0 && wy < kHYt && gx >= 0 && gx < S.nx;
+}
+
+// Halo cell i of a TY-row tile: (global index, sign); sign 0 = outside / zero node.
+template <int TY>
+__device__ __forceinline__ int halo_src_ty(const SlotDesc& S, int x0, int y0, int i, float& s) {
+  const int ly = i / kHX, lx = i - ly * kHX;
+  const int gy = y0 - 2 + ly, gx = x0 - 2 + lx;
+  if (gx > S.nx + 1 || gy > S.ny + 1) { s = 0.f; return 0; }
+  float sx, sy;
+  const int mx = ghost(gx, S.nx, S.bcx, sx);
+  const int my = ghost(gy, S.ny, S.bcy, sy);
+  s = sx * sy;
+  return my * S.nx + mx;
 }
 
 // Thread 0: start the tensor copies of the block's next copied tile (the next item at or after
 // w_issue whose slot iterates and has stencil maps) into window set n_issued % 2.
+template <int TY>
 __device__ __forceinline__ void stencil_issue_next(const SlotDesc* __restrict__ slots,
                                                    const WorkItem* __restrict__ items, int total,
                                                    unsigned char* sbuf, uint64_t* full,
                                                    int& w_issue, int& n_issued) {
+  using G = StGeom<TY>;
   while (w_issue < total) {
     const WorkItem it = items[w_issue];
     w_issue += gridDim.x;
     const SlotDesc& S = slots[it.slot];
     if (S.st_maps == nullptr || !S.sc->active) continue;
     int x0, y0;
-    tile_origin(S, it.tile, x0, y0);
+    tile_origin_ty(S, it.tile, TY, x0, y0);
     const unsigned char* maps = static_cast<const unsigned char*>(S.st_maps);
     const int par = S.sc->it & 1;
     const void* src[5] = {maps, maps + 128, maps + 128 * (2 + 2 * par), maps + 128 * (3 + 2 * par),
@@ -343,28 +380,44 @@ __device__ __forceinline__ void stencil_issue_next(const SlotDesc* __restrict__ 
 #pragma unroll
     for (int k = 0; k < 5; ++k) tmap_acquire(src[k]);
     const int b = n_issued & 1;
-    unsigned char* dst = sbuf + b * kBufBytes;
+    unsigned char* dst = sbuf + b * G::kBufBytes;
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    mbar_expect_tx(&full[b], kBufBytes);
+    mbar_expect_tx(&full[b], G::kBufBytes);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) tma_load_2d(dst + k * kWinBytes, src[k], &full[b], x0 - 4, y0 - 2);
-    tma_load_2d(dst + 4 * kWinBytes, src[4], &full[b], x0, y0);
+    for (int k = 0; k < 4; ++k) tma_load_2d(dst + k * G::kWinBytes, src[k], &full[b], x0 - 4, y0 - 2);
+    tma_load_2d(dst + 4 * G::kWinBytes, src[4], &full[b], x0, y0);
     ++n_issued;
     return;
   }
 }
 
-template <bool ANISO>
-__global__ void __launch_bounds__(kStThreads, kStBlocksPerSm)
+// Compensated sum of (s, c) pairs over the lanes of groups of W consecutive lanes (W = 16 or 32),
+// in a fixed butterfly; the group's total (as FP64) is valid in every lane of the group.
+template <int W>
+__device__ __forceinline__ double group_sum_comp(float s, float c) {
+#pragma unroll
+  for (int o = W / 2; o > 0; o >>= 1) {
+    const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+    float e;
+    two_sum(s, s2, s, e);
+    c = __fadd_rn(c, __fadd_rn(c2, e));
+  }
+  return (double)s + (double)c;
+}
+
+template <bool ANISO, int TY>
+__global__ void __launch_bounds__(kStThreads, StGeom<TY>::kBlocksPerSm)
 k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
-          const int* __restrict__ n_items, int* __restrict__ err) {
+          const int* __restrict__ n_items, int* __restrict__ err, long long wait_cycles) {
+  using G = StGeom<TY>;
   extern __shared__ unsigned char st_smem_raw[];
   unsigned char* sbuf = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(st_smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ __align__(8) uint64_t full[2];
-  __shared__ double red[64];
   __shared__ int s_abort;
   const int total = *n_items;
+  const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     mbar_init(&full[0], 1);
     mbar_init(&full[1], 1);
@@ -376,7 +429,7 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   volatile int* abort_flag = &s_abort;
   int w_issue = blockIdx.x, n_issued = 0;  // thread 0: the tensor-copy cursor
   int n_used = 0;                          // copied windows consumed (uniform over the block)
-  if (threadIdx.x == 0) stencil_issue_next(slots, items, total, sbuf, full, w_issue, n_issued);
+  if (threadIdx.x == 0) stencil_issue_next<TY>(slots, items, total, sbuf, full, w_issue, n_issued);
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem it = items[w];
     const SlotDesc& S = slots[it.slot];
@@ -391,17 +444,16 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     const float* __restrict__ z = S.z;
     const float* __restrict__ z_lo = S.z_lo;
     int x0, y0;
-    tile_origin(S, it.tile, x0, y0);
+    tile_origin_ty(S, it.tile, TY, x0, y0);
     // a tile whose halo lies inside the grid has no ghost cell
-    const bool interior =
-        x0 >= 2 && y0 >= 2 && x0 + kStTileX + 2 <= S.nx && y0 + kStTileY + 2 <= S.ny;
+    const bool interior = x0 >= 2 && y0 >= 2 && x0 + kStTileX + 2 <= S.nx && y0 + TY + 2 <= S.ny;
     unsigned char* buf;
     if (S.st_maps != nullptr) {
       const int b = n_used & 1;
-      buf = sbuf + b * kBufBytes;
+      buf = sbuf + b * G::kBufBytes;
       // the other window set finished with the previous tile: start the next tile's copies
       if (threadIdx.x == 0 && n_issued == n_used + 1)
-        stencil_issue_next(slots, items, total, sbuf, full, w_issue, n_issued);
+        stencil_issue_next<TY>(slots, items, total, sbuf, full, w_issue, n_issued);
       // ghost cells by plain loads, issued before the wait so that both latencies overlap
       int gcell[2] = {-1, -1};
       float gs[2] = {0.f, 0.f};
@@ -411,9 +463,9 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         for (int h = 0; h < 2; ++h) {
           const int k = threadIdx.x + h * kStThreads;
           int wy, wx;
-          if (k < kGhostSlots && ghost_cell(S, x0, y0, k, wy, wx)) {
+          if (k < G::kGhostSlots && ghost_cell<TY>(S, x0, y0, k, wy, wx)) {
             float s;
-            const int g = halo_src(S, x0, y0, wy * kHX + (wx - 2), s);
+            const int g = halo_src_ty<TY>(S, x0, y0, wy * kHX + (wx - 2), s);
             if (s != 0.f) {  // zero-sign ghosts stay the zeros the copy filled in
               gcell[h] = wy * kWX + wx;
               gs[h] = s;
@@ -423,13 +475,13 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           }
         }
       }
-      mbar_wait(&full[b], (n_used >> 1) & 1, abort_flag);
+      mbar_wait(&full[b], (n_used >> 1) & 1, abort_flag, wait_cycles);
       // p = z + beta p_old over the whole window, in place of z
       float4* zh = reinterpret_cast<float4*>(buf);
-      float4* zl = reinterpret_cast<float4*>(buf + kWinBytes);
-      const float4* ph = reinterpret_cast<const float4*>(buf + 2 * kWinBytes);
-      const float4* pl = reinterpret_cast<const float4*>(buf + 3 * kWinBytes);
-      for (int v = threadIdx.x; v < kWX * kHY / 4; v += kStThreads) {
+      float4* zl = reinterpret_cast<float4*>(buf + G::kWinBytes);
+      const float4* ph = reinterpret_cast<const float4*>(buf + 2 * G::kWinBytes);
+      const float4* pl = reinterpret_cast<const float4*>(buf + 3 * G::kWinBytes);
+      for (int v = threadIdx.x; v < kWX * G::kHYt / 4; v += kStThreads) {
         const float4 a = zh[v], al = zl[v], c = ph[v], cl = pl[v];
         const f2x2 u = df_axpy2(beta, {make_float2(c.x, c.y), make_float2(cl.x, cl.y)},
                                 {make_float2(a.x, a.y), make_float2(al.x, al.y)});
@@ -443,7 +495,7 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       ++n_used;
       if (!interior) {
         float* wh = reinterpret_cast<float*>(buf);
-        float* wl = reinterpret_cast<float*>(buf + kWinBytes);
+        float* wl = reinterpret_cast<float*>(buf + G::kWinBytes);
 #pragma unroll
         for (int h = 0; h < 2; ++h)
           if (gcell[h] >= 0) {
@@ -455,18 +507,18 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       }
     } else {
       // plain loads into the free window set, kChunk cells per thread in flight at a time
-      buf = sbuf + ((n_used + 1) & 1) * kBufBytes;
+      buf = sbuf + ((n_used + 1) & 1) * G::kBufBytes;
       float* wh = reinterpret_cast<float*>(buf);
-      float* wl = reinterpret_cast<float*>(buf + kWinBytes);
-      uint8_t* mt = buf + 4 * kWinBytes;
-      for (int e = threadIdx.x; e < kMaskBytes; e += kStThreads) {
+      float* wl = reinterpret_cast<float*>(buf + G::kWinBytes);
+      uint8_t* mt = buf + 4 * G::kWinBytes;
+      for (int e = threadIdx.x; e < G::kMaskBytes; e += kStThreads) {
         const int ly = e / kStTileX, lx = e - ly * kStTileX;
         const int gx = x0 + lx, gy = y0 + ly;
         mt[e] = (gx < S.nx && gy < S.ny) ? S.mask[gy * S.nx + gx] : 0;
       }
       constexpr int kChunk = 4;
 #pragma unroll 1
-      for (int i0 = 0; i0 < kHalo; i0 += kChunk * kStThreads) {
+      for (int i0 = 0; i0 < G::kHalo; i0 += kChunk * kStThreads) {
         int gi[kChunk];
         float gsg[kChunk];
         f2 zv[kChunk], pv[kChunk];
@@ -475,7 +527,7 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           const int i = i0 + threadIdx.x + j * kStThreads;
           gsg[j] = 0.f;
           gi[j] = 0;
-          if (i < kHalo) gi[j] = halo_src(S, x0, y0, i, gsg[j]);
+          if (i < G::kHalo) gi[j] = halo_src_ty<TY>(S, x0, y0, i, gsg[j]);
         }
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
@@ -486,7 +538,7 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
           const int i = i0 + threadIdx.x + j * kStThreads;
-          if (i < kHalo) {
+          if (i < G::kHalo) {
             const int ly = i / kHX, lx = i - ly * kHX;
             const f2 v = df_add(zv[j], df_mul(pv[j], beta));
             wh[ly * kWX + lx + 2] = gsg[j] * v.hi;
@@ -497,83 +549,92 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       __syncthreads();
     }
     const float* wh = reinterpret_cast<const float*>(buf);
-    const float* wl = reinterpret_cast<const float*>(buf + kWinBytes);
-    const uint8_t* mt = buf + 4 * kWinBytes;
-    constexpr int kOwn = kStTileX * kStTileY / kStThreads;
-    static_assert(kOwn * kStThreads == kStTileX * kStTileY && kOwn % 2 == 0, "tile / block size");
-    CompDotDF dot;
+    const float* wl = reinterpret_cast<const float*>(buf + G::kWinBytes);
+    const uint8_t* mt = buf + 4 * G::kWinBytes;
     float* __restrict__ qh = S.q;
     float* __restrict__ ql = S.q_lo;
+    const int nseg = (S.nx + 31) >> 5;  // 32-node row segments per grid row
     if (!ANISO) {
-      // node pairs (x, x+1): the window's row stride is even and x - x0 is even
+      // node pairs (x, x+1): the window's row stride is even and x - x0 is even.  In step j the
+      // warp covers one tile row; lanes 0-15 its first 32 nodes, lanes 16-31 the next 32.
 #pragma unroll 1
-      for (int j = 0; j < kOwn / 2; ++j) {
+      for (int j = 0; j < G::kOwn / 2; ++j) {
         const int k = threadIdx.x + j * kStThreads;
         const int ly = k / (kStTileX / 2), lx = 2 * (k - ly * (kStTileX / 2));
         const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= S.nx || gy >= S.ny) continue;
-        const int g = gy * S.nx + gx;
-        const int wc = (ly + 2) * kWX + lx + 4;
-        const float2 pvh = ld2(wh + wc), pvl = ld2(wl + wc);
-        const unsigned m2 = *reinterpret_cast<const uint16_t*>(mt + ly * kStTileX + lx);
-        f2x2 q2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        if (m2) {
-          const CompSum2 a = stencil13_pair_acc<kWX>(wh + wc);
-          const float2 l = stencil13_pair_plain<kWX>(wl + wc);
-          q2 = df_norm2(a.s, add2(a.c, l));
-        }
-        const bool m0 = (m2 & 0xffu) != 0, m1 = (m2 >> 8) != 0;
-        const f2 q0 = m0 ? f2{q2.hi.x, q2.lo.x} : f2{0.f, 0.f};
-        const f2 q1 = m1 ? f2{q2.hi.y, q2.lo.y} : f2{0.f, 0.f};
-        dot.add(pvh.x, pvl.x, q0.hi, q0.lo);
-        if (gx + 1 < S.nx) {
-          dot.add(pvh.y, pvl.y, q1.hi, q1.lo);
-          if ((g & 1) == 0) {
-            *reinterpret_cast<float2*>(pnew + g) = pvh;
-            *reinterpret_cast<float2*>(pnew_lo + g) = pvl;
-            *reinterpret_cast<float2*>(qh + g) = make_float2(q0.hi, q1.hi);
-            *reinterpret_cast<float2*>(ql + g) = make_float2(q0.lo, q1.lo);
+        CompDotDF dot;
+        if (gx < S.nx && gy < S.ny) {
+          const int g = gy * S.nx + gx;
+          const int wc = (ly + 2) * kWX + lx + 4;
+          const float2 pvh = ld2(wh + wc), pvl = ld2(wl + wc);
+          const unsigned m2 = *reinterpret_cast<const uint16_t*>(mt + ly * kStTileX + lx);
+          f2x2 q2 = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          if (m2) {
+            const CompSum2 a = stencil13_pair_acc<kWX>(wh + wc);
+            const float2 l = stencil13_pair_plain<kWX>(wl + wc);
+            q2 = df_norm2(a.s, add2(a.c, l));
+          }
+          const bool m0 = (m2 & 0xffu) != 0, m1 = (m2 >> 8) != 0;
+          const f2 q0 = m0 ? f2{q2.hi.x, q2.lo.x} : f2{0.f, 0.f};
+          const f2 q1 = m1 ? f2{q2.hi.y, q2.lo.y} : f2{0.f, 0.f};
+          dot.add(pvh.x, pvl.x, q0.hi, q0.lo);
+          if (gx + 1 < S.nx) {
+            dot.add(pvh.y, pvl.y, q1.hi, q1.lo);
+            if ((g & 1) == 0) {
+              *reinterpret_cast<float2*>(pnew + g) = pvh;
+              *reinterpret_cast<float2*>(pnew_lo + g) = pvl;
+              *reinterpret_cast<float2*>(qh + g) = make_float2(q0.hi, q1.hi);
+              *reinterpret_cast<float2*>(ql + g) = make_float2(q0.lo, q1.lo);
+            } else {
+              pnew[g] = pvh.x;
+              pnew[g + 1] = pvh.y;
+              pnew_lo[g] = pvl.x;
+              pnew_lo[g + 1] = pvl.y;
+              qh[g] = q0.hi;
+              qh[g + 1] = q1.hi;
+              ql[g] = q0.lo;
+              ql[g + 1] = q1.lo;
+            }
           } else {
             pnew[g] = pvh.x;
-            pnew[g + 1] = pvh.y;
             pnew_lo[g] = pvl.x;
-            pnew_lo[g + 1] = pvl.y;
             qh[g] = q0.hi;
-            qh[g + 1] = q1.hi;
             ql[g] = q0.lo;
-            ql[g + 1] = q1.lo;
           }
-        } else {
-          pnew[g] = pvh.x;
-          pnew_lo[g] = pvl.x;
-          qh[g] = q0.hi;
-          ql[g] = q0.lo;
         }
+        // the half warp's row segment: every lane joins the butterfly
+        const double seg = group_sum_comp<16>(dot.s, dot.c);
+        const int sx = (x0 + (lane & 16) * 2) >> 5;
+        if ((lane & 15) == 0 && gy < S.ny && sx < nseg) S.pq_part[gy * nseg + sx] = seg;
       }
     } else {
+      // one node per lane; in step j the warp covers 32 consecutive nodes of one tile row
 #pragma unroll 1
-      for (int j = 0; j < kOwn; ++j) {
+      for (int j = 0; j < G::kOwn; ++j) {
         const int k = threadIdx.x + j * kStThreads;
         const int ly = k / kStTileX, lx = k - ly * kStTileX;
         const int gx = x0 + lx, gy = y0 + ly;
-        if (gx >= S.nx || gy >= S.ny) continue;
-        const int g = gy * S.nx + gx;
-        const float pvh = wh[(ly + 2) * kWX + lx + 4], pvl = wl[(ly + 2) * kWX + lx + 4];
-        f2 qv = {0.f, 0.f};
-        if (mt[ly * kStTileX + lx]) {
-          const CompSum a = stencil13_acc<ANISO, kWX>(S, wh + 2, ly, lx);
-          const float l = stencil13_plain<ANISO, kWX>(S, wl + 2, ly, lx);
-          qv = df_norm(a.s, __fadd_rn(a.c, l));
+        CompDotDF dot;
+        if (gx < S.nx && gy < S.ny) {
+          const int g = gy * S.nx + gx;
+          const float pvh = wh[(ly + 2) * kWX + lx + 4], pvl = wl[(ly + 2) * kWX + lx + 4];
+          f2 qv = {0.f, 0.f};
+          if (mt[ly * kStTileX + lx]) {
+            const CompSum a = stencil13_acc<ANISO, kWX>(S, wh + 2, ly, lx);
+            const float l = stencil13_plain<ANISO, kWX>(S, wl + 2, ly, lx);
+            qv = df_norm(a.s, __fadd_rn(a.c, l));
+          }
+          pnew[g] = pvh;
+          pnew_lo[g] = pvl;
+          qh[g] = qv.hi;
+          ql[g] = qv.lo;
+          dot.add(pvh, pvl, qv.hi, qv.lo);
         }
-        pnew[g] = pvh;
-        pnew_lo[g] = pvl;
-        qh[g] = qv.hi;
-        ql[g] = qv.lo;
-        dot.add(pvh, pvl, qv.hi, qv.lo);
+        const double seg = group_sum_comp<32>(dot.s, dot.c);
+        const int sx = (x0 + (lx & ~31)) >> 5;
+        if (lane == 0 && gy < S.ny && sx < nseg) S.pq_part[gy * nseg + sx] = seg;
       }
     }
-    const double pq = block_sum_comp<kStThreads>(dot.as_comp(), red);
-    if (threadIdx.x == 0) S.part[it.tile * 4 + 1] = pq;  // reduced by k_pq_finish
     __syncthreads();  // the window set is free for the copies started at the next copied tile
   }
   if (threadIdx.x == 0) {
@@ -587,8 +648,8 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   }
 }
 
-// One block per slot (the slot's tile-0 stencil item): p.q from the stencil's per-tile partials
-// in a fixed order, alpha = rho / p.q, breakdown detection.
+// One block per slot (the slot's tile-0 item of the per-slot list): p.q from the stencil's
+// row-segment partials in a fixed order, alpha = rho / p.q, breakdown detection.
 __global__ void __launch_bounds__(256)
 k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
             const int* __restrict__ n_items) {
@@ -601,7 +662,8 @@ k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
     SlotScalars* sc = S.sc;
     if (!sc->active) continue;
     double a = 0.0, b = 0.0;
-    for (int t = threadIdx.x; t < S.n_st_tiles; t += blockDim.x) a += S.part[t * 4 + 1];
+    const int nparts = S.ny * ((S.nx + 31) >> 5);
+    for (int t = threadIdx.x; t < nparts; t += blockDim.x) a += __ldcg(&S.pq_part[t]);
     block_sum2<256>(a, b, red);
     if (threadIdx.x == 0) {
       sc->pq = a;
@@ -611,6 +673,10 @@ k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
         sc->fold = 1;  // the tail replaces the residual and reports the best iterate
       } else {
         sc->alpha = sc->rho / a;
+        const double aro = sc->alpha * sc->rho;
+        sc->aro_total += aro;
+        sc->aro_ring[sc->aro_n % kErrDelay] = aro;
+        sc->aro_n += 1;
       }
     }
     __syncthreads();
@@ -900,23 +966,36 @@ void launch_setup(const LaunchCfg& c, const float* const* phis, const float* con
 void launch_rhs_scale(const LaunchCfg& c) {
   k_rhs_scale<<<c.grid, kStThreads, 0, c.stream>>>(c.slots, c.items, c.n_items);
 }
-void launch_stencil(const LaunchCfg& c, bool aniso, int* err) {
+template <int TY>
+static void launch_stencil_ty(const LaunchCfg& c, bool aniso, int* err, long long wc) {
+  constexpr int smem = StGeom<TY>::kSmemBytes;
   if (aniso)
-    k_stencil<true><<<c.grid, kStThreads, kStSmemBytes, c.stream>>>(c.slots, c.items, c.n_items, err);
+    k_stencil<true, TY><<<c.grid, kStThreads, smem, c.stream>>>(c.slots, c.items, c.n_items, err, wc);
   else
-    k_stencil<false><<<c.grid, kStThreads, kStSmemBytes, c.stream>>>(c.slots, c.items, c.n_items, err);
+    k_stencil<false, TY><<<c.grid, kStThreads, smem, c.stream>>>(c.slots, c.items, c.n_items, err, wc);
 }
-int stencil_blocks_per_sm() { return kStBlocksPerSm; }
-cudaError_t stencil_init() {
+void launch_stencil(const LaunchCfg& c, bool aniso, int tile_y, int* err) {
+  const long long wc = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
+  if (tile_y == 16) launch_stencil_ty<16>(c, aniso, err, wc);
+  else launch_stencil_ty<32>(c, aniso, err, wc);
+}
+int stencil_blocks_per_sm(int tile_y) {
+  return tile_y == 16 ? StGeom<16>::kBlocksPerSm : StGeom<32>::kBlocksPerSm;
+}
+template <bool ANISO, int TY>
+static cudaError_t stencil_attr() {
   // the window sets live in dynamic shared memory; all of the SM's shared memory to the
-  // carveout, so that kStBlocksPerSm blocks fit
-  cudaError_t e[4] = {
-      cudaFuncSetAttribute(k_stencil<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmemBytes),
-      cudaFuncSetAttribute(k_stencil<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmemBytes),
-      cudaFuncSetAttribute(k_stencil<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared),
-      cudaFuncSetAttribute(k_stencil<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared)};
+  // carveout, so that kBlocksPerSm blocks fit
+  const cudaError_t e = cudaFuncSetAttribute(k_stencil<ANISO, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             StGeom<TY>::kSmemBytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_stencil<ANISO, TY>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
+}
+cudaError_t stencil_init() {
+  const cudaError_t e[4] = {stencil_attr<false, 32>(), stencil_attr<true, 32>(),
+                            stencil_attr<false, 16>(), stencil_attr<true, 16>()};
   for (cudaError_t x : e)
     if (x != cudaSuccess) return x;
   return cudaSuccess;

@@ -25,11 +25,12 @@ EXT_EINVAL, EXT_ENOKNOWN, EXT_ENOMEM, EXT_EADMIT = -1, -2, -3, -4
 EXT_ENOTCONV, EXT_EBREAKDOWN, EXT_ETIMEOUT, EXT_ECUDA = -5, -6, -7, -8
 EXT_ENOTSUP, EXT_ENOTFOUND = -9, -10
 
-EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch", "ext_submit",
+EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch", "ext_solve_multi",
+            "ext_submit",
             "ext_poll", "ext_drain", "ext_destroy", "ext_strerror", "ext_last_error",
             "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
             "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
-            "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices"]
+            "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices", "ext_stencil_tile"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
                 "pq_finish"]
@@ -45,13 +46,14 @@ class ExtOptions(C.Structure):
                 ("true_res_every", C.c_int32), ("replace_factor", C.c_double),
                 ("iters_per_launch", C.c_int32),
                 ("hbm_budget", C.c_size_t), ("flexible", C.c_int32), ("max_slots", C.c_int32),
-                ("profile", C.c_int32)]
+                ("profile", C.c_int32), ("autotune", C.c_int32), ("tile_y", C.c_int32),
+                ("wait_cycles", C.c_int64)]
 
 
 class ExtResult(C.Structure):
     _fields_ = [("status", C.c_int32), ("iters", C.c_int32), ("relres_true", C.c_double),
                 ("relres_rec", C.c_double), ("n_unknown", C.c_int32), ("n_known", C.c_int32),
-                ("ms_queue", C.c_double), ("ms_solve", C.c_double)]
+                ("ms_queue", C.c_double), ("ms_solve", C.c_double), ("err_est", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -87,6 +89,9 @@ def load():
     lib.ext_solve_batch.argtypes = [P, I, C.POINTER(ExtProblem), C.POINTER(P), C.POINTER(P),
                                     C.POINTER(P), C.POINTER(ExtResult)]
     lib.ext_solve_batch.restype = I
+    lib.ext_solve_multi.argtypes = [P, C.POINTER(ExtProblem), P, I, C.POINTER(P), C.POINTER(P),
+                                    C.POINTER(ExtResult)]
+    lib.ext_solve_multi.restype = I
     lib.ext_submit.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(C.c_uint64)]
     lib.ext_submit.restype = I
     lib.ext_poll.argtypes = [P, C.c_uint64, C.POINTER(ExtResult)]
@@ -107,6 +112,8 @@ def load():
     lib.ext_apply_preconditioner.restype = I
     lib.ext_profile_read.argtypes = [P, I, C.POINTER(D), C.POINTER(C.c_int64), I]
     lib.ext_profile_read.restype = I
+    lib.ext_stencil_tile.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    lib.ext_stencil_tile.restype = I
     lib.ext_launch_count.argtypes = [P]
     lib.ext_launch_count.restype = C.c_int64
     lib.ext_apply_biharmonic_noalloc.argtypes = [C.POINTER(ExtProblem), P, P, P, C.POINTER(D), P]
@@ -161,7 +168,8 @@ def problem_of(p):
 
 
 def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launch=10,
-            hbm_budget=0, flexible=0, max_slots=256, replace_factor=1e-2, profile=0):
+            hbm_budget=0, flexible=0, max_slots=256, replace_factor=1e-2, profile=0,
+            wait_cycles=0, autotune=1, tile_y=32):
     o = ExtOptions()
     load().ext_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -169,6 +177,8 @@ def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launc
     o.replace_factor = float(replace_factor)
     o.iters_per_launch, o.hbm_budget = int(iters_per_launch), int(hbm_budget)
     o.flexible, o.max_slots, o.profile = int(flexible), int(max_slots), int(profile)
+    o.wait_cycles = int(wait_cycles)
+    o.autotune, o.tile_y = int(autotune), int(tile_y)
     return o
 
 
@@ -229,6 +239,18 @@ def ext_solve_batch(ctx, probs, phis, fs, outs, check=True):
                                 PA(*[_ptr(a) for a in fs]), PA(*[_ptr(a) for a in outs]), res)
     if check:
         _check(rc, "ext_solve_batch")
+    return rc, [r.as_dict() for r in res]
+
+
+def ext_solve_multi(ctx, prob, phi, fs, outs, check=True):
+    """Several fields sharing one phi; returns (rc, [result dicts])."""
+    n = len(fs)
+    PA = C.c_void_p * n
+    res = (ExtResult * n)()
+    rc = load().ext_solve_multi(ctx, C.byref(prob), _ptr(phi), n, PA(*[_ptr(a) for a in fs]),
+                                PA(*[_ptr(a) for a in outs]), res)
+    if check:
+        _check(rc, "ext_solve_multi")
     return rc, [r.as_dict() for r in res]
 
 
@@ -323,6 +345,13 @@ def ext_profile_read(ctx, reset=True):
     cnt = (C.c_int64 * n)()
     _check(load().ext_profile_read(ctx, n, ms, cnt, int(reset)), "ext_profile_read")
     return {KERNEL_KINDS[i]: (ms[i], cnt[i]) for i in range(n)}
+
+
+def ext_stencil_tile(ctx):
+    """(tile_x, tile_y) of the stencil in the context's last solve."""
+    tx, ty = C.c_int32(), C.c_int32()
+    _check(load().ext_stencil_tile(ctx, C.byref(tx), C.byref(ty)), "ext_stencil_tile")
+    return tx.value, ty.value
 
 
 def ext_launch_count(ctx):

@@ -42,6 +42,13 @@ def ctx(ext):
     ext.ext_destroy(c)
 
 
+@pytest.fixture(scope="module", params=[32, 16], ids=["tile32", "tile16"])
+def ctx_tile(ext, request):
+    c = ext.ext_create(ext.options("fp32", rtol=1e-8, autotune=0, tile_y=request.param))
+    yield c
+    ext.ext_destroy(c)
+
+
 @pytest.fixture(scope="module")
 def ctx_tight(ext):
     c = ext.ext_create(ext.options("fp32", rtol=1e-11))
@@ -66,12 +73,13 @@ def _rand_phi(nx, ny, seed, frac=0.4):
 @pytest.mark.parametrize("bc_x,bc_y", PAIRS)
 @pytest.mark.parametrize("nx,ny", [(4, 4), (5, 7), (64, 16), (65, 17), (100, 37), (130, 129),
                                    (48, 40), (256, 96), (512, 384), (200, 300)])
-def test_operator_bitwise_on_integers(ext, ctx, bc_x, bc_y, nx, ny):
+def test_operator_bitwise_on_integers(ext, ctx_tile, bc_x, bc_y, nx, ny):
     """ext_apply_biharmonic runs the solver's stencil kernel (iteration 0, beta = 0, z = p).  With
     h = 1 and integer p (|p| <= 2^10) every 13-point sum is an exact integer below 2^24, so q must
-    equal the oracle's operator bit for bit.  nx a multiple of 16 (48, 64, 256, 512) takes the
-    tensor-copy window path, other widths the plain-load path; the sizes cover interior, edge and
-    corner tiles and ragged last tiles in both axes."""
+    equal the oracle's operator bit for bit, for both stencil tile heights (16 and 32 rows).  nx a
+    multiple of 16 (48, 64, 256, 512) takes the tensor-copy window path, other widths the
+    plain-load path; the sizes cover interior, edge and corner tiles and ragged last tiles in
+    both axes."""
     phi = _rand_phi(nx, ny, nx * 7 + ny)
     known = ob.known_mask(phi.astype(np.float64), "out")
     rng = np.random.default_rng(nx + 3 * ny)
@@ -81,7 +89,7 @@ def test_operator_bitwise_on_integers(ext, ctx, bc_x, bc_y, nx, ny):
     ref = (L2 @ p.astype(np.float64).ravel()).reshape(ny, nx)
     ref[known] = 0
     q = torch.empty((ny, nx), device="cuda")
-    pq = ext.ext_apply_biharmonic(ctx, ext.problem(nx, ny, bc_x, bc_y, "out"), dev(phi), dev(p), q)
+    pq = ext.ext_apply_biharmonic(ctx_tile, ext.problem(nx, ny, bc_x, bc_y, "out"), dev(phi), dev(p), q)
     np.testing.assert_array_equal(q.cpu().numpy().astype(np.float64), ref)
     exact = float(p.astype(np.float64).ravel() @ ref.ravel())
     assert abs(pq - exact) <= 1e-9 * abs(exact), (pq, exact)
