@@ -87,6 +87,10 @@ typedef struct {
                               EXT_TUNE_CACHE names a file, in that file; 0: tile_y; default 1.
                               Results do not depend on the tile.                              */
   int32_t tile_y;          /* the stencil's tile height when autotune = 0: 16 or 32 (default) */
+  int32_t low_modes;       /* mixed modes: 1 = the lowest 32 x 32 modes of the preconditioner
+                              (those with the largest weights) come from six-slice tensor-core
+                              products of about 48 bits instead of the four-slice stages
+                              (default); 0 = all modes from the four-slice stages              */
   int64_t wait_cycles;     /* bound, in SM clock cycles, of every wait of a kernel for its own
                               tensor copies and tensor-core pipeline; a wait that runs out makes
                               the kernel drain what it issued and return, and the call returns
@@ -107,7 +111,10 @@ enum {
   EXT_KERNEL_SPLIT = 9,          /* residual -> 16-bit integer slices (mixed modes)           */
   EXT_KERNEL_PREC_FINISH = 10,   /* per-slot r.z, z.q -> rho, beta                            */
   EXT_KERNEL_PQ_FINISH = 11,     /* per-slot p.q -> alpha                                     */
-  EXT_KERNEL_KINDS = 12
+  EXT_KERNEL_LOW_FWD = 12,       /* low-mode correction: forward product, middle, inverse    */
+  EXT_KERNEL_LOW_MID = 13,
+  EXT_KERNEL_LOW_INV = 14,
+  EXT_KERNEL_KINDS = 15
 };
 
 typedef struct {

@@ -60,6 +60,10 @@ struct PlanDev {
   std::vector<double> lam;
   void* tc = nullptr;   // tensor-core operand planes: [Q planes][Q^T planes], 2-byte elements
   int tc_split = -1;
+  // low-mode operands (six slices): Q^T rows k < 32 [6][32][np] with exponents [32][np/128];
+  // Q columns k < 32 as rows [6][np][64] with exponents [np]; Q[:, :32] double-float [2][np][32]
+  void* low = nullptr;
+  size_t low_off_te = 0, low_off_q = 0, low_off_qe = 0, low_off_d = 0;
 };
 
 // One problem's device state inside a workspace.
@@ -88,6 +92,8 @@ struct Workspace {
   int n_sten = 0;
   int sten_ty = 32;             // stencil tile height of this workspace (autotuned)
   bool tuned = false;
+  WorkItem *d_l1 = nullptr, *d_l3 = nullptr;  // tiles of the low-mode products
+  int n_l1 = 0, n_l3 = 0;
   const float** d_phis = nullptr;
   const float** d_fs = nullptr;
   float** d_outs = nullptr;
@@ -312,6 +318,57 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
   BX_CUDA(cudaMemcpy(P->tc, h.data(), 2 * h.size(), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMemcpy((char*)P->tc + 2 * h.size(), ex.data(), ex.size(), cudaMemcpyHostToDevice));
   P->tc_split = ctx->split;
+  // low-mode operands of the same basis
+  if (P->low) {
+    cudaFree(P->low);
+    P->low = nullptr;
+  }
+  const int np = P->np, nkb = np / tc_block();
+  const int m = std::min(kLowM, P->n);
+  AxisBasis B = make_axis_basis(P->n, P->bc);
+  auto Qv = [&](int i, int k) { return (i < P->n && k < m) ? B.Q[(size_t)i * P->n + k] : 0.0; };
+  const size_t pt = (size_t)kLowM * np, pq = (size_t)np * kLowK3;
+  std::vector<uint16_t> lt(kLowNS * pt, 0), lq(kLowNS * pq, 0);
+  std::vector<int8_t> lte((size_t)kLowM * nkb, 0), lqe(np, 0);
+  std::vector<float> ld(2 * (size_t)np * kLowM, 0.f);
+  std::vector<double> blk(std::max(tc_block(), kLowK3));
+  for (int k = 0; k < kLowM; ++k)      // forward B operand: row k = Q[:, k], 128-wide blocks along i
+    for (int kb = 0; kb < nkb; ++kb) {
+      for (int t = 0; t < tc_block(); ++t) blk[t] = Qv(kb * tc_block() + t, k);
+      const int E = block_exp_host(blk.data(), 1, tc_block());
+      lte[(size_t)k * nkb + kb] = (int8_t)E;
+      for (int t = 0; t < tc_block(); ++t)
+        slice_host(blk[t], E, ctx->split, kLowNS, lt.data(), pt, (size_t)k * np + kb * tc_block() + t);
+    }
+  for (int i = 0; i < np; ++i) {       // inverse B operand: row i = Q[i, :32], one block
+    for (int t = 0; t < kLowK3; ++t) blk[t] = t < kLowM ? Qv(i, t) : 0.0;
+    const int E = block_exp_host(blk.data(), 1, kLowK3);
+    lqe[i] = (int8_t)E;
+    for (int t = 0; t < kLowK3; ++t) slice_host(blk[t], E, ctx->split, kLowNS, lq.data(), pq, (size_t)i * kLowK3 + t);
+    for (int k = 0; k < kLowM; ++k) {
+      const double v = Qv(i, k);
+      const float hi = (float)v;
+      ld[(size_t)i * kLowM + k] = hi;
+      ld[(size_t)np * kLowM + (size_t)i * kLowM + k] = (float)(v - (double)hi);
+    }
+  }
+  P->low_off_te = 2 * lt.size();
+  P->low_off_q = align_up(P->low_off_te + lte.size(), 256);
+  P->low_off_qe = P->low_off_q + 2 * lq.size();
+  P->low_off_d = align_up(P->low_off_qe + lqe.size(), 256);
+  const size_t lbytes = P->low_off_d + 4 * ld.size();
+  if (cudaMalloc(&P->low, lbytes) != cudaSuccess) {
+    cudaGetLastError();
+    P->low = nullptr;
+    g_last_error = "cudaMalloc of low-mode plan failed";
+    return EXT_ENOMEM;
+  }
+  char* L = (char*)P->low;
+  BX_CUDA(cudaMemcpy(L, lt.data(), 2 * lt.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(L + P->low_off_te, lte.data(), lte.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(L + P->low_off_q, lq.data(), 2 * lq.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(L + P->low_off_qe, lqe.data(), lqe.size(), cudaMemcpyHostToDevice));
+  BX_CUDA(cudaMemcpy(L + P->low_off_d, ld.data(), 4 * ld.size(), cudaMemcpyHostToDevice));
   return EXT_OK;
 }
 
@@ -386,6 +443,8 @@ static void free_workspace(Workspace* W) {
   cudaFree(W->d_vec);
   cudaFree(W->d_gm);
   cudaFree(W->d_sl);
+  cudaFree(W->d_l1);
+  cudaFree(W->d_l3);
   cudaFree(W->d_counts);
   cudaFree(W->d_phis);
   cudaFree(W->d_fs);
@@ -458,14 +517,23 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   const size_t o_smaps = st_copy ? take(kStMaps * sizeof(CUtensorMap)) : 0;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
   size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0;
+  size_t o_lh = 0, o_ljt = 0, o_ljte = 0, o_lz = 0, o_lmaps = 0;
   const size_t nex = Np / 64;  // block exponents of one operand
+  const bool low = ctx->tc && ctx->opt.low_modes != 0;
   if (ctx->tc) {
-    o_tr = take(2 * NS * Np);
+    o_tr = take(2 * (low ? kLowNS : NS) * Np);
     o_tt1 = take(2 * NS * Np);
     o_tt2 = take(2 * NS * Np);
     o_tt3 = take(2 * NS * Np);
     o_maps = take(8 * sizeof(CUtensorMap));
     o_ex = take(4 * nex);
+  }
+  if (low) {
+    o_lh = take(2 * 4 * (size_t)ny * kLowM);
+    o_ljt = take(2 * (size_t)kLowNS * d.nxp * kLowK3);
+    o_ljte = take((size_t)d.nxp);
+    o_lz = take(2 * 4 * N);
+    o_lmaps = take(4 * sizeof(CUtensorMap));
   }
   s.bytes = off;
   if (size_only) return EXT_OK;
@@ -523,7 +591,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
     d.tc_eb[1] = plan_exps(py, 1);  // Qy^T rows
     d.tc_eb[2] = plan_exps(px, 0);  // Qx rows
     d.tc_eb[3] = plan_exps(py, 0);  // Qy rows
-    BX_CUDA(cudaMemset(d.tc_r, 0, 2 * NS * Np));
+    BX_CUDA(cudaMemset(d.tc_r, 0, 2 * (low ? kLowNS : NS) * Np));
     BX_CUDA(cudaMemset(A + o_ex, 0, 4 * nex));
     const bool bf = ctx->split == 1;
     const size_t qplane = 0;
@@ -544,6 +612,32 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
     if (!rc3) rc3 = make_tmap(&maps[7], qyb, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
     if (rc3) return rc3;
     BX_CUDA(cudaMemcpy(A + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+  }
+  d.lowm_x = d.lowm_y = 0;
+  if (low) {
+    d.lowm_x = std::min(kLowM, nx);
+    d.lowm_y = std::min(kLowM, ny);
+    d.low_h = (float*)(A + o_lh);
+    d.low_jt = A + o_ljt;
+    d.low_jt_e = (int8_t*)(A + o_ljte);
+    d.low_z = (float*)(A + o_lz);
+    const char* lx = (const char*)px->low;
+    const char* ly = (const char*)py->low;
+    d.low_qxd = (const float*)(lx + px->low_off_d);
+    d.low_qyd = (const float*)(ly + py->low_off_d);
+    d.low_qxt_e = (const int8_t*)(lx + px->low_off_te);
+    d.low_qy_e = (const int8_t*)(ly + py->low_off_qe);
+    d.n_l1_tiles = d.nyp / 128;
+    d.n_l3_tiles = (d.nxp / 128) * (d.nyp / kLowM);
+    const bool bf = ctx->split == 1;
+    CUtensorMap lm[4];
+    int rc4 = make_tmap(&lm[0], d.tc_r, bf, d.nxp, (uint64_t)kLowNS * d.nyp, 128);
+    if (!rc4) rc4 = make_tmap(&lm[1], px->low, bf, d.nxp, (uint64_t)kLowNS * kLowM, kLowM);
+    if (!rc4) rc4 = make_tmap(&lm[2], d.low_jt, bf, kLowK3, (uint64_t)kLowNS * d.nxp, 128);
+    if (!rc4) rc4 = make_tmap(&lm[3], (char*)py->low + py->low_off_q, bf, kLowK3, (uint64_t)kLowNS * d.nyp, kLowM);
+    if (rc4) return rc4;
+    BX_CUDA(cudaMemcpy(A + o_lmaps, lm, sizeof(lm), cudaMemcpyHostToDevice));
+    d.low_maps = A + o_lmaps;
   }
   d.qx = px->q;
   d.qxt = px->qt;
@@ -592,7 +686,7 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   W->key = shape_key(count, probs, host_io);
   W->host_io = host_io;
   W->slots.resize(count);
-  std::vector<WorkItem> st, vec, gm;
+  std::vector<WorkItem> st, vec, gm, l1, l3;
   for (int i = 0; i < count; ++i) {
     SlotHost& s = W->slots[i];
     int rc = build_slot(ctx, probs[i], host_io, s);
@@ -606,6 +700,10 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
     for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
+    if (d.lowm_x) {
+      for (int t = 0; t < d.n_l1_tiles; ++t) l1.push_back({i, t});
+      for (int t = 0; t < d.n_l3_tiles; ++t) l3.push_back({i, t});
+    }
   }
   longest_first(gm, W->slots);
   std::vector<WorkItem> sl;
@@ -633,7 +731,13 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   W->n_sten = W->n_st;
   BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * st.size()));
   BX_CUDA(cudaMemcpy(W->d_sten, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice));
-  int counts[5] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten};
+  W->n_l1 = (int)l1.size();
+  W->n_l3 = (int)l3.size();
+  BX_CUDA(cudaMalloc(&W->d_l1, sizeof(WorkItem) * std::max<size_t>(1, l1.size())));
+  BX_CUDA(cudaMalloc(&W->d_l3, sizeof(WorkItem) * std::max<size_t>(1, l3.size())));
+  if (!l1.empty()) BX_CUDA(cudaMemcpy(W->d_l1, l1.data(), sizeof(WorkItem) * l1.size(), cudaMemcpyHostToDevice));
+  if (!l3.empty()) BX_CUDA(cudaMemcpy(W->d_l3, l3.data(), sizeof(WorkItem) * l3.size(), cudaMemcpyHostToDevice));
+  int counts[7] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten, W->n_l1, W->n_l3};
   BX_CUDA(cudaMalloc(&W->d_counts, sizeof(counts)));
   BX_CUDA(cudaMemcpy(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * count));
@@ -685,6 +789,10 @@ static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
     c.items = W->d_sl;
     c.n_items = W->d_counts + 3;
     c.grid = std::max(1, std::min(W->n_sl, cap));
+  } else if (which == 5 || which == 6) {
+    c.items = which == 5 ? W->d_l1 : W->d_l3;
+    c.n_items = W->d_counts + which;
+    c.grid = std::max(1, std::min(which == 5 ? W->n_l1 : W->n_l3, ctx->sm_count));
   } else if (which == 4) {
     // persistent: the resident blocks, each double-buffering its tiles
     c.items = W->d_sten;
@@ -763,6 +871,13 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
     const LaunchCfg st = cfg_of(ctx, W, 0);
     timed(ctx, EXT_KERNEL_SPLIT, [&] { launch_prec_tc_prepare(st, mode, ctx->split); }, g.stream);
     g.grid = std::max(1, std::min(W->n_gm, ctx->sm_count));
+    if (W->n_l1 > 0) {
+      // the lowest modes in high precision: forward product, middle, inverse product
+      const LaunchCfg c1 = cfg_of(ctx, W, 5), cm = cfg_of(ctx, W, 3), c3 = cfg_of(ctx, W, 6);
+      timed(ctx, EXT_KERNEL_LOW_FWD, [&] { launch_low_tc(c1, 0, mode, ctx->split, ctx->d_err); }, g.stream);
+      timed(ctx, EXT_KERNEL_LOW_MID, [&] { launch_low_mid(cm, mode, ctx->split); }, g.stream);
+      timed(ctx, EXT_KERNEL_LOW_INV, [&] { launch_low_tc(c3, 1, mode, ctx->split, ctx->d_err); }, g.stream);
+    }
   }
   for (int s = 0; s < 4; ++s) {
     timed(ctx, EXT_KERNEL_PREC0 + s, [&] {
@@ -1109,6 +1224,7 @@ void ext_options_default(ext_options* o) {
   o->max_slots = 256;
   o->autotune = 1;
   o->tile_y = 32;
+  o->low_modes = 1;
 }
 
 const char* ext_strerror(int code) {
@@ -1203,6 +1319,7 @@ void ext_destroy(ext_ctx* ctx) {
     cudaFree(kv.second.q);
     cudaFree(kv.second.qt);
     cudaFree(kv.second.tc);
+    cudaFree(kv.second.low);
   }
   harvest(ctx);
   cudaFree(ctx->d_err);
@@ -1472,17 +1589,21 @@ static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
   cudaFree(W->d_sten);
   cudaFree(W->d_vec);
   cudaFree(W->d_gm);
+  cudaFree(W->d_l1);
+  cudaFree(W->d_l3);
   cudaFree(S->d_new);
   cudaFree(S->d_ret);
-  W->d_st = W->d_sten = W->d_vec = W->d_gm = S->d_new = S->d_ret = nullptr;
+  W->d_st = W->d_sten = W->d_vec = W->d_gm = W->d_l1 = W->d_l3 = S->d_new = S->d_ret = nullptr;
   BX_CUDA(cudaMalloc(&W->d_st, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_l1, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_l3, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_vec, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_gm, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&S->d_new, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&S->d_ret, sizeof(WorkItem) * cap));
   S->cap_items = cap;
-  W->n_st = W->n_vec = W->n_gm = W->n_sten = cap;  // persistent grids sized for the capacity
+  W->n_st = W->n_vec = W->n_gm = W->n_sten = W->n_l1 = W->n_l3 = cap;  // grids sized for the capacity
   if (W->graph) {
     cudaGraphExecDestroy(W->graph);
     W->graph = nullptr;
@@ -1503,8 +1624,8 @@ static int serve_init(ext_ctx* ctx) {
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * cap));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * cap));
   memset(W->h_sc, 0, sizeof(SlotScalars) * cap);
-  BX_CUDA(cudaMalloc(&W->d_counts, 5 * sizeof(int)));
-  BX_CUDA(cudaMemset(W->d_counts, 0, 5 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_counts, 7 * sizeof(int)));
+  BX_CUDA(cudaMemset(W->d_counts, 0, 7 * sizeof(int)));
   BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * cap));
   W->n_sl = cap;  // the per-slot grid is sized for the slot table
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * cap));
@@ -1527,7 +1648,7 @@ static int serve_init(ext_ctx* ctx) {
 static int serve_rebuild_lists(ext_ctx* ctx) {
   ext_ctx::Serve* S = ctx->serve;
   Workspace* W = S->W;
-  std::vector<WorkItem> st, vec, gm, sl;
+  std::vector<WorkItem> st, vec, gm, sl, l1, l3;
   bool aniso = false;
   for (int i = 0; i < (int)S->slots.size(); ++i) {
     if (!S->slots[i].used) continue;
@@ -1536,10 +1657,14 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
     for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
+    if (d.lowm_x) {
+      for (int t = 0; t < d.n_l1_tiles; ++t) l1.push_back({i, t});
+      for (int t = 0; t < d.n_l3_tiles; ++t) l3.push_back({i, t});
+    }
     sl.push_back({i, 0});
   }
   longest_first(gm, W->slots);
-  const int need = (int)std::max(st.size(), std::max(vec.size(), gm.size()));
+  const int need = (int)std::max(std::max(st.size(), l3.size()), std::max(vec.size(), gm.size()));
   if (need > S->cap_items) {
     int cap = S->cap_items;
     while (cap < need) cap *= 2;
@@ -1559,7 +1684,10 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
   if (!vec.empty()) BX_CUDA(cudaMemcpyAsync(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice, s));
   if (!gm.empty()) BX_CUDA(cudaMemcpyAsync(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice, s));
   if (!sl.empty()) BX_CUDA(cudaMemcpyAsync(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice, s));
-  int counts[5] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size()};
+  if (!l1.empty()) BX_CUDA(cudaMemcpyAsync(W->d_l1, l1.data(), sizeof(WorkItem) * l1.size(), cudaMemcpyHostToDevice, s));
+  if (!l3.empty()) BX_CUDA(cudaMemcpyAsync(W->d_l3, l3.data(), sizeof(WorkItem) * l3.size(), cudaMemcpyHostToDevice, s));
+  int counts[7] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size(),
+                   (int)l1.size(), (int)l3.size()};
   BX_CUDA(cudaMemcpyAsync(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
   // the host vectors die here: the copies above must finish first (pageable sources are staged)
   BX_CUDA(cudaStreamSynchronize(s));

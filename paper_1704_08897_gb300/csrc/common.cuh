@@ -21,6 +21,9 @@ constexpr int kStThreads = 256;
 constexpr int kStWinX = kStTileX + 8;
 constexpr int kStWinY = kStTileY + 4;
 constexpr int kStMaps = 7;          // stencil tensor maps per slot
+constexpr int kLowM = 32;           // low modes per axis computed in high precision
+constexpr int kLowNS = 6;           // integer slices per operand of the low-mode products
+constexpr int kLowK3 = 64;          // k extent of the inverse low-mode product (32 modes, zero-padded)
 constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels
 constexpr int kVecThreads = 256;
 
@@ -117,6 +120,21 @@ struct SlotDesc {
                         // p_lo[0], p[1], p_lo[1], mask); null when a mask row is not a multiple
                         // of 16 bytes
   int n_tc_tiles;    // output tiles of one tensor-core transform stage
+  // Low-mode correction of the tensor-core preconditioner: the modes kx < lowm_x, ky < lowm_y
+  // (the smoothest, with the largest weights) are left out of the four 32-bit transform stages and
+  // added from thin transforms with six slices per operand (about 48 bits).  0 = off.
+  int lowm_x, lowm_y;
+  float* low_h;             // H = r Qx[:, :32]: [ny][32] hi plane, lo plane at + ny * 32
+  void* low_jt;             // J^T slices [kLowNS][nxp][kLowK3] (16-bit codes), J = W o G Qx_low^T
+  int8_t* low_jt_e;         // block exponent of each J^T row [nxp]
+  float* low_z;             // zl = Qy_low J: [ny][nx] hi plane, lo plane at + nx * ny
+  const float* low_qxd;     // Qx[x][kx < 32] double-float: [nxp][32] hi, lo plane at + nxp * 32
+  const float* low_qyd;     // Qy[y][ky < 32] double-float: [nyp][32] hi, lo plane at + nyp * 32
+  const int8_t* low_qxt_e;  // exponents of the forward product's B operand: [32][nxp / 128]
+  const int8_t* low_qy_e;   // exponents of the inverse product's B operand: [nyp]
+  const void* low_maps;     // 4 CUtensorMap: r slices, Qx_low^T slices, J^T slices, Qy_low slices
+  int n_l1_tiles;           // tiles of the forward product: nyp / 128
+  int n_l3_tiles;           // tiles of the inverse product: (nxp / 128) * (nyp / 32)
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
   double* pq_part;   // p.q partial sums of the stencil, one per 32-node row segment [ny][nx/32]

@@ -56,6 +56,10 @@ void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int
 // residual -> integer slice planes of the first stage's A operand (stencil tile work list)
 void launch_prec_tc_prepare(const LaunchCfg& c, int mode, int split_kind);
 int tc_planes(int split_kind);
+// low-mode correction of the tensor-core preconditioner: kind 0 = forward product (one tile per
+// 128 rows of y), kind 1 = inverse product (tiles of 128 x 32); the middle step one block per slot
+void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* err);
+void launch_low_mid(const LaunchCfg& c, int mode, int split_kind);
 int tc_block();
 bool tc_supported();
 // opt the tensor-core kernels into their dynamic shared memory (once per process and device)

@@ -169,15 +169,15 @@ __device__ __forceinline__ int block_exp(float amax) {
 // removes it exactly (FMA; the product is exact) and renormalises the remainder with the lo plane
 // (TwoSum), so the slices carry the value to 2^-32 of the block whatever its size; the last
 // slice is rounded to an integer.  The 16-bit codes are returned as (lane x, lane y) pairs.
-template <bool BF16>
+template <bool BF16, int NSL = NS>
 __device__ __forceinline__ void slice_codes2_df(float2 vh, float2 vl, float2 s, float2 is,
-                                                uint32_t (&code)[NS]) {
+                                                uint32_t (&code)[NSL]) {
   float2 rh = vh, rl = vl, up = s, down = make_float2(-is.x, -is.y);
 #pragma unroll
-  for (int k = 0; k < NS; ++k) {
+  for (int k = 0; k < NSL; ++k) {
     const float2 t = __fmul2_rn(rh, up);
     const float2 c = make_float2(rintf(t.x), rintf(t.y));
-    if (k + 1 < NS) {
+    if (k + 1 < NSL) {
       const float2 h = __ffma2_rn(c, down, rh);
       two_sum2(h, rl, rh, rl);
     }
@@ -516,7 +516,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         for (int i = 0; i < kEpiCols; ++i) {
           const int n = ncol0 + i;
           const float s = __shfl_sync(0xffffffffu, lamy_mine, i) + lamx_m;
-          const bool ok = (m < S.nx) && (n < S.ny) && (s > 0.f);
+          // the low block (m < lowm_x, n < lowm_y) comes from the six-slice products instead
+          const bool ok = (m < S.nx) && (n < S.ny) && (s > 0.f) && !(m < S.lowm_x && n < S.lowm_y);
           const f2 wv = df_mul(f2{val[i], vlo[i]}, spectral_weight_of(S.wnorm, s));
           val[i] = ok ? wv.hi : 0.f;
           vlo[i] = ok ? wv.lo : 0.f;
@@ -568,8 +569,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           static_assert(kEpiCols % kGrp == 0, "stage-3 load groups");
 #pragma unroll
           for (int g8 = 0; g8 < kEpiCols; g8 += kGrp) {
-            float rv[kGrp], rl[kGrp], qv[kGrp], ql[kGrp];
+            float rv[kGrp], rl[kGrp], qv[kGrp], ql[kGrp], wh[kGrp], wl[kGrp];
             uint8_t mk[kGrp];
+            const size_t nn = static_cast<size_t>(S.nx) * S.ny;
 #pragma unroll
             for (int i = 0; i < kGrp; ++i) {  // issue the group's loads together
               const int n = ncol0 + g8 + i;
@@ -579,13 +581,17 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               qv[i] = S.q[g];
               ql[i] = S.q_lo[g];
               mk[i] = n < S.ny ? S.mask[g] : 0;
+              wh[i] = S.lowm_x ? S.low_z[g] : 0.f;
+              wl[i] = S.lowm_x ? S.low_z[nn + g] : 0.f;
             }
 #pragma unroll
             for (int i = 0; i < kGrp; ++i) {
               const int n = ncol0 + g8 + i;
               if (n < S.ny) {
-                const float zh = mk[i] ? val[g8 + i] : 0.f;
-                const float zl = mk[i] ? vlo[g8 + i] : 0.f;
+                // the 32-bit stages' result plus the low-mode part, as one double-float value
+                const f2 zsum = df_add(f2{val[g8 + i], vlo[g8 + i]}, f2{wh[i], wl[i]});
+                const float zh = mk[i] ? zsum.hi : 0.f;
+                const float zl = mk[i] ? zsum.lo : 0.f;
                 S.z[n * S.nx + m] = zh;
                 S.z_lo[n * S.nx + m] = zl;
                 c_rz.add(rv[i], rl[i], zh, zl);
@@ -706,14 +712,334 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
       const float s = pow2f(8 - E), is = pow2f(E - 8);
 #pragma unroll
       for (int k = 0; k < kPairs; ++k) {
-        uint32_t code[NS];
-        slice_codes2_df<BF16>(v[j][k], vl[j][k], make_float2(s, s), make_float2(is, is), code);
+        // six slices: the first four are stage 0's operand, all six the low-mode product's
+        uint32_t code[kLowNS];
+        slice_codes2_df<BF16, kLowNS>(v[j][k], vl[j][k], make_float2(s, s), make_float2(is, is), code);
         const size_t idx = (static_cast<size_t>(y) * S.nxp + x0 + 64 * k + 2 * lane) / 2;
-#pragma unroll
-        for (int q = 0; q < NS; ++q) out32[q * (plane / 2) + idx] = code[q];
+        const int nsl = S.lowm_x ? kLowNS : NS;
+        for (int q = 0; q < nsl; ++q) out32[q * (plane / 2) + idx] = code[q];
       }
       if (lane == 0) S.tc_e[0][static_cast<size_t>(y) * kblocks + x0 / KC] = static_cast<int8_t>(E);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Low-mode correction (mixed modes).  The weights 1/(lam_y + lam_x)^2 of the smoothest modes are up
+// to (64/lam_min)^2 times those of the roughest, so rounding noise of the 32-bit stages, relative
+// to |r|, is amplified in exactly these modes and costs CG iterations.  The modes kx < 32,
+// ky < 32 are therefore left out of stage 1's weights and computed here to about 48 bits:
+//   forward (KIND 0):  H[y][kx] = sum_x r[y][x] Qx[x][kx]            six slices each side
+//   middle (k_low_mid): G = Qy_low^T H, G' = w o G, J[ky][x] = sum_kx G'[ky][kx] Qx[x][kx]
+//                      (double-float dot products on the CUDA cores), J^T cut into six slices
+//   inverse (KIND 1):  zl[y][x] = sum_ky Qy[y][ky] J[ky][x]           six slices each side
+// and stage 3 adds zl to its result.  With six 8-bit slices per operand the products of orders
+// 0..5 (21 of them) are kept, each order in its own TMEM accumulator; per k, the products of one
+// order add up to at most 2^17 in magnitude, so over a 128-wide block every partial sum is an
+// exact integer of at most 2^24.  Orders 0..2 are merged into the double-float result with TwoSum,
+// orders 3..5 (below 2^-24 of it) in plain FP32.
+//
+// One CTA per output tile of 128 rows x 32 columns, four warps; thread 0 issues the tensor copies
+// and the MMAs one 64-wide k step at a time (the products are thin, so a simple serial pipeline
+// suffices), and every thread drains its own TMEM lane after each exponent block.
+// ---------------------------------------------------------------------------------------------
+constexpr int LBN = kLowM;                   // N tile (columns)
+constexpr int LBK = 64;                      // k per tensor copy
+constexpr int LA_PLANE = BM * LBK * 2;       // 16 KB
+constexpr int LB_PLANE = LBN * LBK * 2;      // 4 KB
+constexpr int kLowThreads = 128;
+constexpr int kLowTmemCols = 256;            // >= kLowNS * LBN
+constexpr int kLowSmem = kLowNS * (LA_PLANE + LB_PLANE) + 1024 + 256;
+static_assert(kLowNS * LBN <= kLowTmemCols, "low-mode TMEM columns");
+static_assert(kLowK3 == LBK, "the inverse product's k fits one copy");
+
+struct LowCtl {
+  uint64_t full, done;
+  uint32_t tmem;
+  int abort_flag;
+};
+
+// Exponent of a block whose largest magnitude is amax: amax < 2^E and amax 2^(8-E) < 255.5.
+__device__ __forceinline__ int low_block_exp(float amax) {
+  if (!(amax > 0.f)) return 0;
+  int e;
+  frexpf(amax, &e);
+  if (amax * pow2f(8 - e) >= 255.5f) ++e;
+  return max(e, -90);
+}
+
+template <bool BF16, int KIND>
+__global__ void __launch_bounds__(kLowThreads, 1)
+k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+         const int* __restrict__ n_items, int mode, int* __restrict__ err, long long wait_cycles) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  LowCtl* ctl = reinterpret_cast<LowCtl*>(smem + kLowNS * (LA_PLANE + LB_PLANE));
+  volatile int* abort_flag = &ctl->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = *n_items;
+  if (threadIdx.x == 0) {
+    mbar_init(&ctl->full, 1);
+    mbar_init(&ctl->done, 1);
+    ctl->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem)),
+                 "r"(kLowTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = ctl->tmem;
+  uint32_t ph_full = 0, ph_done = 0;
+  int inflight = 0;     // thread 0: tensor copies issued and not yet waited for (0 or 1)
+  int mma_pending = 0;  // thread 0: MMAs committed and not yet waited for (0 or 1)
+  const int row = warp * 32 + lane;  // TMEM lane of this thread = tile row
+  bool failed = false;
+  for (int w = blockIdx.x; w < total && !failed; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    if (!slot_runs(S.sc, mode) || S.lowm_x == 0) continue;
+    // geometry of this product
+    int m0, n0, K, KC, rowsA, rowsB;
+    const unsigned char* maps = static_cast<const unsigned char*>(S.low_maps);
+    const void* ma = maps + 128 * (KIND == 0 ? 0 : 2);
+    const void* mb = maps + 128 * (KIND == 0 ? 1 : 3);
+    if (KIND == 0) {
+      m0 = it.tile * BM;
+      n0 = 0;
+      K = S.nxp;
+      KC = 128;
+      rowsA = S.nyp;
+      rowsB = kLowM;
+    } else {
+      const int mt = S.nxp / BM;
+      m0 = (it.tile % mt) * BM;
+      n0 = (it.tile / mt) * LBN;
+      K = kLowK3;
+      KC = kLowK3;
+      rowsA = S.nxp;
+      rowsB = S.nyp;
+    }
+    if (threadIdx.x == 0) {
+      tmap_acquire(ma);
+      tmap_acquire(mb);
+    }
+    const int m = m0 + row;
+    // double-float result of the thread's row, one per column
+    float hi[LBN], lo[LBN];
+#pragma unroll
+    for (int c = 0; c < LBN; ++c) {
+      hi[c] = 0.f;
+      lo[c] = 0.f;
+    }
+    for (int kb = 0; kb < K / KC && !failed; ++kb) {
+      if (threadIdx.x == 0) {
+        for (int sub = 0; sub < KC / LBK; ++sub) {
+          const int k0 = kb * KC + sub * LBK;
+          unsigned char* sa = smem;
+          unsigned char* sb = smem + kLowNS * LA_PLANE;
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect_tx(&ctl->full, kLowNS * (LA_PLANE + LB_PLANE));
+#pragma unroll
+          for (int p = 0; p < kLowNS; ++p) tma_load_2d(sa + p * LA_PLANE, ma, &ctl->full, k0, p * rowsA + m0);
+#pragma unroll
+          for (int p = 0; p < kLowNS; ++p) tma_load_2d(sb + p * LB_PLANE, mb, &ctl->full, k0, p * rowsB + n0);
+          inflight = 1;
+          if (!mbar_wait(&ctl->full, ph_full, abort_flag, wait_cycles)) break;
+          inflight = 0;
+          ph_full ^= 1;
+          tc_fence_after();
+          const uint32_t a0 = smem_u32(sa), b0 = smem_u32(sb);
+#pragma unroll
+          for (int j = 0; j < LBK / 16; ++j) {
+#pragma unroll
+            for (int i = 0; i < kLowNS; ++i) {
+              // slice i of A against the B slices 0 .. kLowNS-1-i stacked along N: order i + j'
+              // lands in the accumulator at column (i + j') * LBN
+              umma(tmem_base + i * LBN, sdesc(a0 + i * LA_PLANE) + 2 * j, sdesc(b0) + 2 * j,
+                   idesc_f16(BF16, BM, (kLowNS - i) * LBN), (sub > 0 || j > 0 || i > 0) ? 1u : 0u);
+            }
+          }
+          umma_commit(&ctl->done);
+          // the next copy reuses the shared memory, and the block's sums must be complete
+          mma_pending = 1;
+          if (!mbar_wait(&ctl->done, ph_done, abort_flag, wait_cycles)) break;
+          mma_pending = 0;
+          ph_done ^= 1;
+        }
+      }
+      __syncthreads();
+      if (*abort_flag) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      // exponents of the block: the thread's row (A) and every column (B)
+      int ea;
+      if (KIND == 0) ea = S.tc_e[0][static_cast<size_t>(min(m, S.nyp - 1)) * (S.nxp / 128) + kb];
+      else ea = S.low_jt_e[min(m, S.nxp - 1)];
+      // 2^(E_A + E_B - 16) of every column (exact products of powers of two)
+      float scl[LBN];
+#pragma unroll
+      for (int c = 0; c < LBN; ++c) {
+        const int eb = KIND == 0 ? S.low_qxt_e[static_cast<size_t>(c) * (S.nxp / 128) + kb]
+                                 : S.low_qy_e[min(n0 + c, S.nyp - 1)];
+        scl[c] = pow2f(ea - 16) * pow2f(eb);
+      }
+#pragma unroll 1
+      for (int d = 0; d < kLowNS; ++d) {
+        const float od = pow2f(-8 * d);
+        uint32_t v[16];
+#pragma unroll
+        for (int h = 0; h < LBN / 16; ++h) {
+          tmem_ld16(tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + d * LBN + h * 16, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c0 = 0; c0 < 16; ++c0) {
+            const int c = h * 16 + c0;
+            const float t = __uint_as_float(v[c0]) * scl[c] * od;
+            if (d <= 2) {
+              float e;
+              two_sum(hi[c], t, hi[c], e);
+              lo[c] = __fadd_rn(lo[c], e);
+            } else {
+              lo[c] = __fadd_rn(lo[c], t);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncthreads();  // the next block's MMAs overwrite the accumulators
+    }
+    if (failed) break;
+    // the tile's double-float results
+    if (KIND == 0) {
+      if (m < S.ny) {
+        float* hh = S.low_h + static_cast<size_t>(m) * kLowM;
+        float* hl = S.low_h + static_cast<size_t>(S.ny) * kLowM + static_cast<size_t>(m) * kLowM;
+#pragma unroll
+        for (int c = 0; c < LBN; ++c) {
+          const f2 v = df_norm(hi[c], lo[c]);
+          hh[c] = v.hi;
+          hl[c] = v.lo;
+        }
+      }
+    } else {
+      const size_t nn = static_cast<size_t>(S.nx) * S.ny;
+      if (m < S.nx) {
+#pragma unroll
+        for (int c = 0; c < LBN; ++c) {
+          const int n = n0 + c;
+          if (n < S.ny) {
+            const f2 v = df_norm(hi[c], lo[c]);
+            const size_t g = static_cast<size_t>(n) * S.nx + m;
+            S.low_z[g] = v.hi;
+            S.low_z[nn + g] = v.lo;
+          }
+        }
+      }
+    }
+  }
+  if (threadIdx.x == 0) {
+    // after an abort: a copy still in flight lands, and committed MMAs complete, before the CTA
+    // frees its TMEM and leaves
+    if (inflight) {
+      const long long t0 = clock64();
+      while (!mbar_try(&ctl->full, ph_full) && clock64() - t0 < kWaitCycles / 4) {
+      }
+    }
+    if (mma_pending) {
+      const long long t0 = clock64();
+      while (!mbar_try(&ctl->done, ph_done) && clock64() - t0 < kWaitCycles / 4) {
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kLowTmemCols)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
+}
+
+// The slices of one double-float value on a single lane (the packed routine on lane x).
+template <bool BF16>
+__device__ __forceinline__ void slice_codes_df(float vh, float vl, float s, float is,
+                                               uint16_t (&code)[kLowNS]) {
+  uint32_t c2[kLowNS];
+  slice_codes2_df<BF16, kLowNS>(make_float2(vh, 0.f), make_float2(vl, 0.f), make_float2(s, s),
+                                make_float2(is, is), c2);
+#pragma unroll
+  for (int k = 0; k < kLowNS; ++k) code[k] = static_cast<uint16_t>(c2[k] & 0xffffu);
+}
+
+// Middle of the low-mode correction, one block per slot: G = Qy_low^T H and J = (w o G) Qx_low^T
+// by compensated dot products of double-float operands (Ogita-Rump-Oishi), then J^T cut into six
+// slices per row with its block exponent (the inverse product's A operand).
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+          const int* __restrict__ n_items, int mode) {
+  __shared__ float gh[kLowM][kLowM + 1], gl[kLowM][kLowM + 1];
+  const int total = *n_items;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    if (it.tile != 0) continue;
+    const SlotDesc& S = slots[it.slot];
+    if (!slot_runs(S.sc, mode) || S.lowm_x == 0) continue;
+    const float* qy_h = S.low_qyd;
+    const float* qy_l = S.low_qyd + static_cast<size_t>(S.nyp) * kLowM;
+    const float* qx_h = S.low_qxd;
+    const float* qx_l = S.low_qxd + static_cast<size_t>(S.nxp) * kLowM;
+    const float* h_h = S.low_h;
+    const float* h_l = S.low_h + static_cast<size_t>(S.ny) * kLowM;
+    // G[ky][kx] over y < ny; thread t: kx = lane, ky = warp + 8 r
+#pragma unroll 1
+    for (int r = 0; r < kLowM / 8; ++r) {
+      const int ky = warp + 8 * r, kx = lane;
+      CompDotDF acc;
+      for (int y = 0; y < S.ny; ++y) {
+        const size_t a = static_cast<size_t>(y) * kLowM;
+        acc.add(__ldg(qy_h + a + ky), __ldg(qy_l + a + ky), __ldg(h_h + a + kx), __ldg(h_l + a + kx));
+      }
+      f2 g = df_norm(acc.s, acc.c);
+      const float sw = S.lamy[min(ky, S.nyp - 1)] + S.lamx[min(kx, S.nxp - 1)];
+      const bool ok = ky < S.lowm_y && kx < S.lowm_x && sw > 0.f;
+      g = ok ? df_mul(g, spectral_weight_of(S.wnorm, sw)) : f2{0.f, 0.f};
+      gh[ky][kx] = g.hi;
+      gl[ky][kx] = g.lo;
+    }
+    __syncthreads();
+    // J^T rows x (one warp per row, lane = ky), sliced for the inverse product
+    uint16_t* jt = static_cast<uint16_t*>(S.low_jt);
+    const size_t plane = static_cast<size_t>(S.nxp) * kLowK3;
+    for (int x = warp; x < S.nxp; x += 8) {
+      CompDotDF acc;
+      const size_t a = static_cast<size_t>(x) * kLowM;
+#pragma unroll 4
+      for (int kx = 0; kx < kLowM; ++kx)
+        acc.add(gh[lane][kx], gl[lane][kx], __ldg(qx_h + a + kx), __ldg(qx_l + a + kx));
+      const f2 j = df_norm(acc.s, acc.c);
+      const int E = low_block_exp(warp_max(fabsf(j.hi)));
+      uint16_t code[kLowNS];
+      slice_codes_df<BF16>(j.hi, j.lo, pow2f(8 - E), pow2f(E - 8), code);
+#pragma unroll
+      for (int p = 0; p < kLowNS; ++p) {
+        jt[p * plane + static_cast<size_t>(x) * kLowK3 + lane] = code[p];
+        jt[p * plane + static_cast<size_t>(x) * kLowK3 + kLowM + lane] = 0;  // padding columns
+      }
+      if (lane == 0) S.low_jt_e[x] = static_cast<int8_t>(E);
+    }
+    __syncthreads();
   }
 }
 
@@ -758,13 +1084,36 @@ int tc_planes(int) { return NS; }
 
 int tc_block() { return KC; }
 
+template <bool BF16, int KIND>
+static cudaError_t set_low_attr() {
+  return cudaFuncSetAttribute(k_low_tc<BF16, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowSmem);
+}
+
 cudaError_t tc_init() {
   cudaError_t e = cudaSuccess;
-  const cudaError_t r[8] = {set_attr<false, 0>(), set_attr<false, 1>(), set_attr<false, 2>(), set_attr<false, 3>(),
-                            set_attr<true, 0>(),  set_attr<true, 1>(),  set_attr<true, 2>(),  set_attr<true, 3>()};
+  const cudaError_t r[12] = {set_attr<false, 0>(), set_attr<false, 1>(), set_attr<false, 2>(), set_attr<false, 3>(),
+                             set_attr<true, 0>(),  set_attr<true, 1>(),  set_attr<true, 2>(),  set_attr<true, 3>(),
+                             set_low_attr<false, 0>(), set_low_attr<false, 1>(), set_low_attr<true, 0>(),
+                             set_low_attr<true, 1>()};
   for (cudaError_t x : r)
     if (x != cudaSuccess) e = x;
   return e;
+}
+
+void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* err) {
+  const long long wc = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
+  if (split_kind == 0) {
+    if (kind == 0) k_low_tc<false, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    else k_low_tc<false, 1><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+  } else {
+    if (kind == 0) k_low_tc<true, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    else k_low_tc<true, 1><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+  }
+}
+
+void launch_low_mid(const LaunchCfg& c, int mode, int split_kind) {
+  if (split_kind == 0) k_low_mid<false><<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
+  else k_low_mid<true><<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
 }
 
 void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int* err) {

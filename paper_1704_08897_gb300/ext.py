@@ -33,7 +33,7 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices", "ext_stencil_tile"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
-                "pq_finish"]
+                "pq_finish", "low_fwd", "low_mid", "low_inv"]
 
 
 class ExtProblem(C.Structure):
@@ -47,7 +47,7 @@ class ExtOptions(C.Structure):
                 ("iters_per_launch", C.c_int32),
                 ("hbm_budget", C.c_size_t), ("flexible", C.c_int32), ("max_slots", C.c_int32),
                 ("profile", C.c_int32), ("autotune", C.c_int32), ("tile_y", C.c_int32),
-                ("wait_cycles", C.c_int64)]
+                ("low_modes", C.c_int32), ("wait_cycles", C.c_int64)]
 
 
 class ExtResult(C.Structure):
@@ -169,7 +169,7 @@ def problem_of(p):
 
 def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launch=10,
             hbm_budget=0, flexible=0, max_slots=256, replace_factor=1e-2, profile=0,
-            wait_cycles=0, autotune=1, tile_y=32):
+            wait_cycles=0, autotune=1, tile_y=32, low_modes=1):
     o = ExtOptions()
     load().ext_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -178,7 +178,7 @@ def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launc
     o.iters_per_launch, o.hbm_budget = int(iters_per_launch), int(hbm_budget)
     o.flexible, o.max_slots, o.profile = int(flexible), int(max_slots), int(profile)
     o.wait_cycles = int(wait_cycles)
-    o.autotune, o.tile_y = int(autotune), int(tile_y)
+    o.autotune, o.tile_y, o.low_modes = int(autotune), int(tile_y), int(low_modes)
     return o
 
 
