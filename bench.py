@@ -95,16 +95,28 @@ TC_PRODUCTS = 10
 TC_PAD = 128
 
 
+# The low-mode products use six slices per operand: orders 0..5, 21 products per useful product,
+# with k padded to 64 in the inverse product.
+TC_LOW_PRODUCTS = 21
+
+
 def issued_tensor_flop(probs, kind):
     """Flops the tensor cores execute in one launch of transform stage `kind` (mixed modes)."""
-    s = int(kind[-1])
     pad = lambda n: -(-n // TC_PAD) * TC_PAD
+    if kind == "low_fwd":
+        return sum(2 * TC_LOW_PRODUCTS * pad(p.ny) * 32 * pad(p.nx) for p in probs)
+    if kind == "low_inv":
+        return sum(2 * TC_LOW_PRODUCTS * pad(p.nx) * pad(p.ny) * 64 for p in probs)
+    s = int(kind[-1])
     return sum(2 * TC_PRODUCTS * pad(p.nx) * pad(p.ny) * pad(p.nx if s in (0, 2) else p.ny)
                for p in probs)
 
 
 def algorithmic_cost(probs, kind):
     """(amount, unit) per launch of one kernel kind over the workload's instances."""
+    if kind in ("low_fwd", "low_inv"):
+        # the lowest 32 modes of one axis against the whole grid: 2 * nx * ny * 32 flop
+        return sum(2 * p.nx * p.ny * min(32, p.nx) for p in probs), "flop"
     if kind.startswith("prec_stage"):
         # stage k contracts one axis: 2 * nx * ny * (length of that axis) flop
         s = int(kind[-1])
@@ -411,7 +423,8 @@ def run_ours(args, rank, world):
                 # what the tensor pipe actually executes: the exact slice products on padded tiles
                 issued = issued_tensor_flop(probs, dom) / per_launch_s / 1e12
                 roofline["issued"] = {"achieved": round(issued, 3), "frac": round(issued / peak, 4),
-                                      "products_per_useful_product": TC_PRODUCTS,
+                                      "products_per_useful_product":
+                                          TC_LOW_PRODUCTS if dom.startswith("low") else TC_PRODUCTS,
                                       "pad": TC_PAD}
 
     ext.ext_destroy(ctx)

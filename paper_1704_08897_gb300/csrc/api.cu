@@ -628,7 +628,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
     d.low_qxt_e = (const int8_t*)(lx + px->low_off_te);
     d.low_qy_e = (const int8_t*)(ly + py->low_off_qe);
     d.n_l1_tiles = d.nyp / 128;
-    d.n_l3_tiles = (d.nxp / 128) * (d.nyp / kLowM);
+    d.n_l3_tiles = d.nxp / 128;  // inverse product: one item per 128 rows of x
     const bool bf = ctx->split == 1;
     CUtensorMap lm[4];
     int rc4 = make_tmap(&lm[0], d.tc_r, bf, d.nxp, (uint64_t)kLowNS * d.nyp, 128);

@@ -134,7 +134,7 @@ struct SlotDesc {
   const int8_t* low_qy_e;   // exponents of the inverse product's B operand: [nyp]
   const void* low_maps;     // 4 CUtensorMap: r slices, Qx_low^T slices, J^T slices, Qy_low slices
   int n_l1_tiles;           // tiles of the forward product: nyp / 128
-  int n_l3_tiles;           // tiles of the inverse product: (nxp / 128) * (nyp / 32)
+  int n_l3_tiles;           // items of the inverse product: nxp / 128 (each walks every y-tile)
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
   double* pq_part;   // p.q partial sums of the stencil, one per 32-node row segment [ny][nx/32]

@@ -569,9 +569,26 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           static_assert(kEpiCols % kGrp == 0, "stage-3 load groups");
 #pragma unroll
           for (int g8 = 0; g8 < kEpiCols; g8 += kGrp) {
-            float rv[kGrp], rl[kGrp], qv[kGrp], ql[kGrp], wh[kGrp], wl[kGrp];
+            if (S.lowm_x) {
+              // the low-mode part first: the 32-bit stages' result plus zl, one double-float value
+              const size_t nn = static_cast<size_t>(S.nx) * S.ny;
+              float wh[kGrp], wl[kGrp];
+#pragma unroll
+              for (int i = 0; i < kGrp; ++i) {
+                const int n = ncol0 + g8 + i;
+                const size_t g = static_cast<size_t>(n < S.ny ? n : 0) * S.nx + m;
+                wh[i] = S.low_z[g];
+                wl[i] = S.low_z[nn + g];
+              }
+#pragma unroll
+              for (int i = 0; i < kGrp; ++i) {
+                const f2 zsum = df_add(f2{val[g8 + i], vlo[g8 + i]}, f2{wh[i], wl[i]});
+                val[g8 + i] = zsum.hi;
+                vlo[g8 + i] = zsum.lo;
+              }
+            }
+            float rv[kGrp], rl[kGrp], qv[kGrp], ql[kGrp];
             uint8_t mk[kGrp];
-            const size_t nn = static_cast<size_t>(S.nx) * S.ny;
 #pragma unroll
             for (int i = 0; i < kGrp; ++i) {  // issue the group's loads together
               const int n = ncol0 + g8 + i;
@@ -581,17 +598,13 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               qv[i] = S.q[g];
               ql[i] = S.q_lo[g];
               mk[i] = n < S.ny ? S.mask[g] : 0;
-              wh[i] = S.lowm_x ? S.low_z[g] : 0.f;
-              wl[i] = S.lowm_x ? S.low_z[nn + g] : 0.f;
             }
 #pragma unroll
             for (int i = 0; i < kGrp; ++i) {
               const int n = ncol0 + g8 + i;
               if (n < S.ny) {
-                // the 32-bit stages' result plus the low-mode part, as one double-float value
-                const f2 zsum = df_add(f2{val[g8 + i], vlo[g8 + i]}, f2{wh[i], wl[i]});
-                const float zh = mk[i] ? zsum.hi : 0.f;
-                const float zl = mk[i] ? zsum.lo : 0.f;
+                const float zh = mk[i] ? val[g8 + i] : 0.f;
+                const float zl = mk[i] ? vlo[g8 + i] : 0.f;
                 S.z[n * S.nx + m] = zh;
                 S.z_lo[n * S.nx + m] = zl;
                 c_rz.add(rv[i], rl[i], zh, zl);
@@ -970,6 +983,195 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
   if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
 }
 
+// Inverse low-mode product, zl[y][x] = sum_ky Qy[y][ky] J[ky][x], one item per (slot, 128-row
+// tile of x).  The tile's six J^T slice planes (its A operand, k = ky padded to 64) are copied
+// once; the B operand (Qy_low's slices for 32 values of y) is double-buffered, and the products of
+// consecutive y-tiles go to two TMEM sets, so that the MMAs of one y-tile run while the four warps
+// merge and store the previous one.
+struct LowInvCtl {
+  uint64_t fa, fb[2], md[2];
+  uint32_t tmem;
+  int abort_flag;
+};
+constexpr int kLowInvSmem = kLowNS * LA_PLANE + 2 * kLowNS * LB_PLANE + 1024 + 256;
+constexpr int kLowInvTmemCols = 512;  // two sets of kLowNS * LBN columns, at 0 and 256
+static_assert(kLowNS * LBN <= 256, "low-mode TMEM set");
+
+template <bool BF16>
+__global__ void __launch_bounds__(kLowThreads, 1)
+k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
+          const int* __restrict__ n_items, int mode, int* __restrict__ err, long long wait_cycles) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + kLowNS * LA_PLANE;  // two buffers of kLowNS * LB_PLANE
+  LowInvCtl* ctl = reinterpret_cast<LowInvCtl*>(sB + 2 * kLowNS * LB_PLANE);
+  volatile int* abort_flag = &ctl->abort_flag;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = *n_items;
+  if (threadIdx.x == 0) {
+    mbar_init(&ctl->fa, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&ctl->fb[b], 1);
+      mbar_init(&ctl->md[b], 1);
+    }
+    ctl->abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&ctl->tmem)),
+                 "r"(kLowInvTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = ctl->tmem;
+  // thread 0's barrier bookkeeping: phases and the waits still owed
+  uint32_t ph_fa = 0, ph_fb[2] = {0, 0}, ph_md[2] = {0, 0};
+  int owe_fa = 0, owe_fb[2] = {0, 0}, owe_md[2] = {0, 0};
+  const int row = warp * 32 + lane;
+  bool failed = false;
+  for (int w = blockIdx.x; w < total && !failed; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    if (!slot_runs(S.sc, mode) || S.lowm_x == 0) continue;
+    const unsigned char* maps = static_cast<const unsigned char*>(S.low_maps);
+    const void* ma = maps + 128 * 2;
+    const void* mb = maps + 128 * 3;
+    const int m0 = it.tile * BM;
+    const int nt = S.nyp / LBN;
+    auto issue_b = [&](int j) {  // thread 0: B slices of y-tile j into buffer j & 1
+      const int b = j & 1;
+      unsigned char* dst = sB + b * kLowNS * LB_PLANE;
+      mbar_expect_tx(&ctl->fb[b], kLowNS * LB_PLANE);
+#pragma unroll
+      for (int p = 0; p < kLowNS; ++p) tma_load_2d(dst + p * LB_PLANE, mb, &ctl->fb[b], 0, p * S.nyp + j * LBN);
+      owe_fb[b] = 1;
+    };
+    auto issue_mma = [&](int j) -> bool {  // thread 0: wait for B(j), products into set j & 1
+      const int b = j & 1;
+      if (!mbar_wait(&ctl->fb[b], ph_fb[b], abort_flag, wait_cycles)) return false;
+      owe_fb[b] = 0;
+      ph_fb[b] ^= 1;
+      tc_fence_after();
+      const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + b * kLowNS * LB_PLANE);
+      const uint32_t dset = tmem_base + b * 256;
+#pragma unroll
+      for (int jj = 0; jj < LBK / 16; ++jj) {
+#pragma unroll
+        for (int i = 0; i < kLowNS; ++i)
+          umma(dset + i * LBN, sdesc(a0 + i * LA_PLANE) + 2 * jj, sdesc(b0) + 2 * jj,
+               idesc_f16(BF16, BM, (kLowNS - i) * LBN), (jj > 0 || i > 0) ? 1u : 0u);
+      }
+      umma_commit(&ctl->md[b]);
+      owe_md[b] = 1;
+      return true;
+    };
+    if (threadIdx.x == 0) {
+      tmap_acquire(ma);
+      tmap_acquire(mb);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_expect_tx(&ctl->fa, kLowNS * LA_PLANE);
+#pragma unroll
+      for (int p = 0; p < kLowNS; ++p) tma_load_2d(sA + p * LA_PLANE, ma, &ctl->fa, 0, p * S.nxp + m0);
+      owe_fa = 1;
+      issue_b(0);
+      bool ok = mbar_wait(&ctl->fa, ph_fa, abort_flag, wait_cycles);
+      if (ok) {
+        owe_fa = 0;
+        ph_fa ^= 1;
+        ok = issue_mma(0);
+      }
+    }
+    const int m = m0 + row;
+    const float sa = pow2f(static_cast<int>(S.low_jt_e[min(m, S.nxp - 1)]) - 16);
+    const size_t nn = static_cast<size_t>(S.nx) * S.ny;
+    for (int j = 0; j < nt; ++j) {
+      const int b = j & 1;
+      if (threadIdx.x == 0 && !*abort_flag) {
+        if (j + 1 < nt) issue_b(j + 1);
+        if (mbar_wait(&ctl->md[b], ph_md[b], abort_flag, wait_cycles)) {
+          owe_md[b] = 0;
+          ph_md[b] ^= 1;
+          if (j + 1 < nt) issue_mma(j + 1);
+        }
+      }
+      __syncthreads();
+      if (*abort_flag) {
+        failed = true;
+        break;
+      }
+      tc_fence_after();
+      const int n0 = j * LBN;
+      float hi[LBN], lo[LBN], scl[LBN];
+#pragma unroll
+      for (int c = 0; c < LBN; ++c) {
+        hi[c] = 0.f;
+        lo[c] = 0.f;
+        scl[c] = sa * pow2f(S.low_qy_e[n0 + c]);
+      }
+#pragma unroll 1
+      for (int d = 0; d < kLowNS; ++d) {
+        const float od = pow2f(-8 * d);
+        uint32_t v[16];
+#pragma unroll
+        for (int h = 0; h < LBN / 16; ++h) {
+          tmem_ld16(tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + b * 256 + d * LBN + h * 16, v);
+          tmem_wait_ld();
+#pragma unroll
+          for (int c0 = 0; c0 < 16; ++c0) {
+            const int c = h * 16 + c0;
+            const float t = __uint_as_float(v[c0]) * scl[c] * od;
+            if (d <= 2) {
+              float e;
+              two_sum(hi[c], t, hi[c], e);
+              lo[c] = __fadd_rn(lo[c], e);
+            } else {
+              lo[c] = __fadd_rn(lo[c], t);
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      if (m < S.nx) {
+#pragma unroll
+        for (int c = 0; c < LBN; ++c) {
+          const int y = n0 + c;
+          if (y < S.ny) {
+            const f2 v = df_norm(hi[c], lo[c]);
+            const size_t g = static_cast<size_t>(y) * S.nx + m;
+            S.low_z[g] = v.hi;
+            S.low_z[nn + g] = v.lo;
+          }
+        }
+      }
+      __syncthreads();  // TMEM set b and B buffer b are free for y-tile j + 2
+    }
+  }
+  if (threadIdx.x == 0) {
+    // after an abort: copies still in flight land and committed MMAs complete before the CTA
+    // frees its TMEM and leaves
+    const long long t0 = clock64();
+    if (owe_fa) while (!mbar_try(&ctl->fa, ph_fa) && clock64() - t0 < kWaitCycles / 4) {}
+    for (int b = 0; b < 2; ++b) {
+      if (owe_fb[b]) while (!mbar_try(&ctl->fb[b], ph_fb[b]) && clock64() - t0 < kWaitCycles / 4) {}
+      if (owe_md[b]) while (!mbar_try(&ctl->md[b], ph_md[b]) && clock64() - t0 < kWaitCycles / 4) {}
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kLowInvTmemCols)
+                 : "memory");
+  }
+  if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
+}
+
 // The slices of one double-float value on a single lane (the packed routine on lane x).
 template <bool BF16>
 __device__ __forceinline__ void slice_codes_df(float vh, float vl, float s, float is,
@@ -983,12 +1185,15 @@ __device__ __forceinline__ void slice_codes_df(float vh, float vl, float s, floa
 
 // Middle of the low-mode correction, one block per slot: G = Qy_low^T H and J = (w o G) Qx_low^T
 // by compensated dot products of double-float operands (Ogita-Rump-Oishi), then J^T cut into six
-// slices per row with its block exponent (the inverse product's A operand).
+// slices per row with its block exponent (the inverse product's A operand).  G's k sum runs over
+// 32-row chunks of H and Qy_low staged in shared memory; J's row of Qx_low is broadcast across
+// the warp by shuffles, so neither loop waits on global memory per term.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int mode) {
   __shared__ float gh[kLowM][kLowM + 1], gl[kLowM][kLowM + 1];
+  __shared__ float hh[32][kLowM], hl[32][kLowM], yh[32][kLowM], yl[32][kLowM];
   const int total = *n_items;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
@@ -1002,16 +1207,32 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     const float* qx_l = S.low_qxd + static_cast<size_t>(S.nxp) * kLowM;
     const float* h_h = S.low_h;
     const float* h_l = S.low_h + static_cast<size_t>(S.ny) * kLowM;
-    // G[ky][kx] over y < ny; thread t: kx = lane, ky = warp + 8 r
-#pragma unroll 1
+    // G[ky][kx]: thread t owns kx = lane and ky = warp + 8 r, r = 0..3
+    CompDotDF acc[kLowM / 8];
+    for (int y0 = 0; y0 < S.ny; y0 += 32) {
+      // stage rows y0 .. y0+31 of H and Qy_low (zeros beyond ny)
+      for (int e = t; e < 32 * kLowM; e += 256) {
+        const int yy = e / kLowM, c = e - yy * kLowM, y = y0 + yy;
+        const bool in = y < S.ny;
+        const size_t a = static_cast<size_t>(y) * kLowM + c;
+        hh[yy][c] = in ? h_h[a] : 0.f;
+        hl[yy][c] = in ? h_l[a] : 0.f;
+        yh[yy][c] = in ? qy_h[a] : 0.f;
+        yl[yy][c] = in ? qy_l[a] : 0.f;
+      }
+      __syncthreads();
+#pragma unroll 4
+      for (int yy = 0; yy < 32; ++yy) {
+        const float bh = hh[yy][lane], bl = hl[yy][lane];
+#pragma unroll
+        for (int r = 0; r < kLowM / 8; ++r) acc[r].add(yh[yy][warp + 8 * r], yl[yy][warp + 8 * r], bh, bl);
+      }
+      __syncthreads();
+    }
+#pragma unroll
     for (int r = 0; r < kLowM / 8; ++r) {
       const int ky = warp + 8 * r, kx = lane;
-      CompDotDF acc;
-      for (int y = 0; y < S.ny; ++y) {
-        const size_t a = static_cast<size_t>(y) * kLowM;
-        acc.add(__ldg(qy_h + a + ky), __ldg(qy_l + a + ky), __ldg(h_h + a + kx), __ldg(h_l + a + kx));
-      }
-      f2 g = df_norm(acc.s, acc.c);
+      f2 g = df_norm(acc[r].s, acc[r].c);
       const float sw = S.lamy[min(ky, S.nyp - 1)] + S.lamx[min(kx, S.nxp - 1)];
       const bool ok = ky < S.lowm_y && kx < S.lowm_x && sw > 0.f;
       g = ok ? df_mul(g, spectral_weight_of(S.wnorm, sw)) : f2{0.f, 0.f};
@@ -1022,13 +1243,20 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     // J^T rows x (one warp per row, lane = ky), sliced for the inverse product
     uint16_t* jt = static_cast<uint16_t*>(S.low_jt);
     const size_t plane = static_cast<size_t>(S.nxp) * kLowK3;
+    float gr_h[kLowM], gr_l[kLowM];  // the lane's row ky of G'
+#pragma unroll
+    for (int kx = 0; kx < kLowM; ++kx) {
+      gr_h[kx] = gh[lane][kx];
+      gr_l[kx] = gl[lane][kx];
+    }
     for (int x = warp; x < S.nxp; x += 8) {
-      CompDotDF acc;
       const size_t a = static_cast<size_t>(x) * kLowM;
-#pragma unroll 4
+      const float qh = __ldg(qx_h + a + lane), ql = __ldg(qx_l + a + lane);
+      CompDotDF acc2;
+#pragma unroll
       for (int kx = 0; kx < kLowM; ++kx)
-        acc.add(gh[lane][kx], gl[lane][kx], __ldg(qx_h + a + kx), __ldg(qx_l + a + kx));
-      const f2 j = df_norm(acc.s, acc.c);
+        acc2.add(gr_h[kx], gr_l[kx], __shfl_sync(0xffffffffu, qh, kx), __shfl_sync(0xffffffffu, ql, kx));
+      const f2 j = df_norm(acc2.s, acc2.c);
       const int E = low_block_exp(warp_max(fabsf(j.hi)));
       uint16_t code[kLowNS];
       slice_codes_df<BF16>(j.hi, j.lo, pow2f(8 - E), pow2f(E - 8), code);
@@ -1086,7 +1314,9 @@ int tc_block() { return KC; }
 
 template <bool BF16, int KIND>
 static cudaError_t set_low_attr() {
-  return cudaFuncSetAttribute(k_low_tc<BF16, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowSmem);
+  if (KIND == 0)
+    return cudaFuncSetAttribute(k_low_tc<BF16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowSmem);
+  return cudaFuncSetAttribute(k_low_inv<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowInvSmem);
 }
 
 cudaError_t tc_init() {
@@ -1104,10 +1334,10 @@ void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* 
   const long long wc = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
   if (split_kind == 0) {
     if (kind == 0) k_low_tc<false, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
-    else k_low_tc<false, 1><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    else k_low_inv<false><<<c.grid, kLowThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
   } else {
     if (kind == 0) k_low_tc<true, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
-    else k_low_tc<true, 1><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    else k_low_inv<true><<<c.grid, kLowThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
   }
 }
 
