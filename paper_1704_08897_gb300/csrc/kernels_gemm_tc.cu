@@ -760,7 +760,8 @@ constexpr int LBN = kLowM;                   // N tile (columns)
 constexpr int LBK = 64;                      // k per tensor copy
 constexpr int LA_PLANE = BM * LBK * 2;       // 16 KB
 constexpr int LB_PLANE = LBN * LBK * 2;      // 4 KB
-constexpr int kLowThreads = 128;
+constexpr int kLowThreads = 512;              // 16 warps: four per TMEM lane quarter
+constexpr int kLowCols = LBN / 4;             // columns per warp in the merge
 constexpr int kLowTmemCols = 256;            // >= kLowNS * LBN
 constexpr int kLowSmem = kLowNS * (LA_PLANE + LB_PLANE) + 1024 + 256;
 static_assert(kLowNS * LBN <= kLowTmemCols, "low-mode TMEM columns");
@@ -812,7 +813,8 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
   uint32_t ph_full = 0, ph_done = 0;
   int inflight = 0;     // thread 0: tensor copies issued and not yet waited for (0 or 1)
   int mma_pending = 0;  // thread 0: MMAs committed and not yet waited for (0 or 1)
-  const int row = warp * 32 + lane;  // TMEM lane of this thread = tile row
+  const int quarter = warp & 3, cg = warp >> 2;  // TMEM lane quarter, column group
+  const int row = quarter * 32 + lane;          // TMEM lane of this thread = tile row
   bool failed = false;
   for (int w = blockIdx.x; w < total && !failed; w += gridDim.x) {
     const WorkItem it = items[w];
@@ -844,10 +846,10 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       tmap_acquire(mb);
     }
     const int m = m0 + row;
-    // double-float result of the thread's row, one per column
-    float hi[LBN], lo[LBN];
+    // double-float result of the thread's row, one per column of its group
+    float hi[kLowCols], lo[kLowCols];
 #pragma unroll
-    for (int c = 0; c < LBN; ++c) {
+    for (int c = 0; c < kLowCols; ++c) {
       hi[c] = 0.f;
       lo[c] = 0.f;
     }
@@ -898,32 +900,29 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       if (KIND == 0) ea = S.tc_e[0][static_cast<size_t>(min(m, S.nyp - 1)) * (S.nxp / 128) + kb];
       else ea = S.low_jt_e[min(m, S.nxp - 1)];
       // 2^(E_A + E_B - 16) of every column (exact products of powers of two)
-      float scl[LBN];
+      float scl[kLowCols];
 #pragma unroll
-      for (int c = 0; c < LBN; ++c) {
-        const int eb = KIND == 0 ? S.low_qxt_e[static_cast<size_t>(c) * (S.nxp / 128) + kb]
-                                 : S.low_qy_e[min(n0 + c, S.nyp - 1)];
+      for (int c = 0; c < kLowCols; ++c) {
+        const int cc = cg * kLowCols + c;
+        const int eb = KIND == 0 ? S.low_qxt_e[static_cast<size_t>(cc) * (S.nxp / 128) + kb]
+                                 : S.low_qy_e[min(n0 + cc, S.nyp - 1)];
         scl[c] = pow2f(ea - 16) * pow2f(eb);
       }
-#pragma unroll 1
+#pragma unroll
       for (int d = 0; d < kLowNS; ++d) {
         const float od = pow2f(-8 * d);
-        uint32_t v[16];
+        uint32_t v[kLowCols];
+        tmem_ld8(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + d * LBN + cg * kLowCols, v);
+        tmem_wait_ld();
 #pragma unroll
-        for (int h = 0; h < LBN / 16; ++h) {
-          tmem_ld16(tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + d * LBN + h * 16, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int c0 = 0; c0 < 16; ++c0) {
-            const int c = h * 16 + c0;
-            const float t = __uint_as_float(v[c0]) * scl[c] * od;
-            if (d <= 2) {
-              float e;
-              two_sum(hi[c], t, hi[c], e);
-              lo[c] = __fadd_rn(lo[c], e);
-            } else {
-              lo[c] = __fadd_rn(lo[c], t);
-            }
+        for (int c = 0; c < kLowCols; ++c) {
+          const float t = __uint_as_float(v[c]) * scl[c] * od;
+          if (d <= 2) {
+            float e;
+            two_sum(hi[c], t, hi[c], e);
+            lo[c] = __fadd_rn(lo[c], e);
+          } else {
+            lo[c] = __fadd_rn(lo[c], t);
           }
         }
       }
@@ -934,10 +933,10 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
     // the tile's double-float results
     if (KIND == 0) {
       if (m < S.ny) {
-        float* hh = S.low_h + static_cast<size_t>(m) * kLowM;
-        float* hl = S.low_h + static_cast<size_t>(S.ny) * kLowM + static_cast<size_t>(m) * kLowM;
+        float* hh = S.low_h + static_cast<size_t>(m) * kLowM + cg * kLowCols;
+        float* hl = S.low_h + static_cast<size_t>(S.ny) * kLowM + static_cast<size_t>(m) * kLowM + cg * kLowCols;
 #pragma unroll
-        for (int c = 0; c < LBN; ++c) {
+        for (int c = 0; c < kLowCols; ++c) {
           const f2 v = df_norm(hi[c], lo[c]);
           hh[c] = v.hi;
           hl[c] = v.lo;
@@ -947,8 +946,8 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       const size_t nn = static_cast<size_t>(S.nx) * S.ny;
       if (m < S.nx) {
 #pragma unroll
-        for (int c = 0; c < LBN; ++c) {
-          const int n = n0 + c;
+        for (int c = 0; c < kLowCols; ++c) {
+          const int n = n0 + cg * kLowCols + c;
           if (n < S.ny) {
             const f2 v = df_norm(hi[c], lo[c]);
             const size_t g = static_cast<size_t>(n) * S.nx + m;
@@ -994,11 +993,13 @@ struct LowInvCtl {
   int abort_flag;
 };
 constexpr int kLowInvSmem = kLowNS * LA_PLANE + 2 * kLowNS * LB_PLANE + 1024 + 256;
+constexpr int kLowInvThreads = 512;            // 16 warps: four per TMEM lane quarter
+constexpr int kLowInvCols = LBN / 4;           // columns per warp
 constexpr int kLowInvTmemCols = 512;  // two sets of kLowNS * LBN columns, at 0 and 256
 static_assert(kLowNS * LBN <= 256, "low-mode TMEM set");
 
 template <bool BF16>
-__global__ void __launch_bounds__(kLowThreads, 1)
+__global__ void __launch_bounds__(kLowInvThreads, 1)
 k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int mode, int* __restrict__ err, long long wait_cycles) {
   extern __shared__ unsigned char smem_raw[];
@@ -1033,7 +1034,8 @@ k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   // thread 0's barrier bookkeeping: phases and the waits still owed
   uint32_t ph_fa = 0, ph_fb[2] = {0, 0}, ph_md[2] = {0, 0};
   int owe_fa = 0, owe_fb[2] = {0, 0}, owe_md[2] = {0, 0};
-  const int row = warp * 32 + lane;
+  const int quarter = warp & 3, cg = warp >> 2;   // TMEM lane quarter, column group
+  const int row = quarter * 32 + lane;
   bool failed = false;
   for (int w = blockIdx.x; w < total && !failed; w += gridDim.x) {
     const WorkItem it = items[w];
@@ -1106,40 +1108,37 @@ k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         break;
       }
       tc_fence_after();
-      const int n0 = j * LBN;
-      float hi[LBN], lo[LBN], scl[LBN];
+      const int n0 = j * LBN + cg * kLowInvCols;  // the warp's columns
+      float hi[kLowInvCols], lo[kLowInvCols], scl[kLowInvCols];
 #pragma unroll
-      for (int c = 0; c < LBN; ++c) {
+      for (int c = 0; c < kLowInvCols; ++c) {
         hi[c] = 0.f;
         lo[c] = 0.f;
         scl[c] = sa * pow2f(S.low_qy_e[n0 + c]);
       }
-#pragma unroll 1
+#pragma unroll
       for (int d = 0; d < kLowNS; ++d) {
         const float od = pow2f(-8 * d);
-        uint32_t v[16];
+        uint32_t v[kLowInvCols];
+        tmem_ld8(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + b * 256 + d * LBN +
+                     cg * kLowInvCols, v);
+        tmem_wait_ld();
 #pragma unroll
-        for (int h = 0; h < LBN / 16; ++h) {
-          tmem_ld16(tmem_base + (static_cast<uint32_t>(warp * 32) << 16) + b * 256 + d * LBN + h * 16, v);
-          tmem_wait_ld();
-#pragma unroll
-          for (int c0 = 0; c0 < 16; ++c0) {
-            const int c = h * 16 + c0;
-            const float t = __uint_as_float(v[c0]) * scl[c] * od;
-            if (d <= 2) {
-              float e;
-              two_sum(hi[c], t, hi[c], e);
-              lo[c] = __fadd_rn(lo[c], e);
-            } else {
-              lo[c] = __fadd_rn(lo[c], t);
-            }
+        for (int c = 0; c < kLowInvCols; ++c) {
+          const float t = __uint_as_float(v[c]) * scl[c] * od;
+          if (d <= 2) {
+            float e;
+            two_sum(hi[c], t, hi[c], e);
+            lo[c] = __fadd_rn(lo[c], e);
+          } else {
+            lo[c] = __fadd_rn(lo[c], t);
           }
         }
       }
       tc_fence_before();
       if (m < S.nx) {
 #pragma unroll
-        for (int c = 0; c < LBN; ++c) {
+        for (int c = 0; c < kLowInvCols; ++c) {
           const int y = n0 + c;
           if (y < S.ny) {
             const f2 v = df_norm(hi[c], lo[c]);
@@ -1249,23 +1248,38 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       gr_h[kx] = gh[lane][kx];
       gr_l[kx] = gl[lane][kx];
     }
-    for (int x = warp; x < S.nxp; x += 8) {
-      const size_t a = static_cast<size_t>(x) * kLowM;
-      const float qh = __ldg(qx_h + a + lane), ql = __ldg(qx_l + a + lane);
-      CompDotDF acc2;
+    // four rows of J^T per warp at a time: four independent dot-product chains per lane
+    constexpr int kRowsPerWarp = 4;
+    for (int x0 = warp * kRowsPerWarp; x0 < S.nxp; x0 += 8 * kRowsPerWarp) {
+      float qh[kRowsPerWarp], ql[kRowsPerWarp];
 #pragma unroll
-      for (int kx = 0; kx < kLowM; ++kx)
-        acc2.add(gr_h[kx], gr_l[kx], __shfl_sync(0xffffffffu, qh, kx), __shfl_sync(0xffffffffu, ql, kx));
-      const f2 j = df_norm(acc2.s, acc2.c);
-      const int E = low_block_exp(warp_max(fabsf(j.hi)));
-      uint16_t code[kLowNS];
-      slice_codes_df<BF16>(j.hi, j.lo, pow2f(8 - E), pow2f(E - 8), code);
-#pragma unroll
-      for (int p = 0; p < kLowNS; ++p) {
-        jt[p * plane + static_cast<size_t>(x) * kLowK3 + lane] = code[p];
-        jt[p * plane + static_cast<size_t>(x) * kLowK3 + kLowM + lane] = 0;  // padding columns
+      for (int r = 0; r < kRowsPerWarp; ++r) {
+        const size_t a = static_cast<size_t>(x0 + r) * kLowM;
+        qh[r] = __ldg(qx_h + a + lane);
+        ql[r] = __ldg(qx_l + a + lane);
       }
-      if (lane == 0) S.low_jt_e[x] = static_cast<int8_t>(E);
+      CompDotDF acc2[kRowsPerWarp];
+#pragma unroll
+      for (int kx = 0; kx < kLowM; ++kx) {
+#pragma unroll
+        for (int r = 0; r < kRowsPerWarp; ++r)
+          acc2[r].add(gr_h[kx], gr_l[kx], __shfl_sync(0xffffffffu, qh[r], kx),
+                      __shfl_sync(0xffffffffu, ql[r], kx));
+      }
+#pragma unroll
+      for (int r = 0; r < kRowsPerWarp; ++r) {
+        const int x = x0 + r;
+        const f2 j = df_norm(acc2[r].s, acc2[r].c);
+        const int E = low_block_exp(warp_max(fabsf(j.hi)));
+        uint16_t code[kLowNS];
+        slice_codes_df<BF16>(j.hi, j.lo, pow2f(8 - E), pow2f(E - 8), code);
+#pragma unroll
+        for (int p = 0; p < kLowNS; ++p) {
+          jt[p * plane + static_cast<size_t>(x) * kLowK3 + lane] = code[p];
+          jt[p * plane + static_cast<size_t>(x) * kLowK3 + kLowM + lane] = 0;  // padding columns
+        }
+        if (lane == 0) S.low_jt_e[x] = static_cast<int8_t>(E);
+      }
     }
     __syncthreads();
   }
@@ -1334,10 +1348,10 @@ void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* 
   const long long wc = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
   if (split_kind == 0) {
     if (kind == 0) k_low_tc<false, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
-    else k_low_inv<false><<<c.grid, kLowThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    else k_low_inv<false><<<c.grid, kLowInvThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
   } else {
     if (kind == 0) k_low_tc<true, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
-    else k_low_inv<true><<<c.grid, kLowThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    else k_low_inv<true><<<c.grid, kLowInvThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
   }
 }
 
