@@ -63,7 +63,26 @@ def parse():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="batch: requests of the serving leg (config-4 shape); 0 skips it")
-    return ap.parse_args()
+    ap.add_argument("--low-modes", type=int, default=None,
+                    help="low-mode correction of the mixed preconditioner: 1 on, 0 off (library default)")
+    ap.add_argument("--fold", type=int, default=None,
+                    help="mirror-class transforms of the mixed preconditioner: 1 on, 0 off (library default)")
+    args = ap.parse_args()
+    if args.low_modes is not None:
+        _OPTION_OVERRIDES["low_modes"] = args.low_modes
+    if args.fold is not None:
+        _OPTION_OVERRIDES["fold"] = args.fold
+    return args
+
+
+_OPTION_OVERRIDES = {}
+
+
+def _options(prec, **kw):
+    """Solver options of every context the bench creates, with the command line's overrides."""
+    from paper_1704_08897_gb300 import ext
+    kw = {**kw, **_OPTION_OVERRIDES}
+    return ext.options(prec, **kw)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -100,16 +119,35 @@ TC_PAD = 128
 TC_LOW_PRODUCTS = 21
 
 
-def issued_tensor_flop(probs, kind):
-    """Flops the tensor cores execute in one launch of transform stage `kind` (mixed modes)."""
+def mirror_classes(n, fold=True):
+    """Node counts of one axis's transform problems in the mixed preconditioner: two mirror
+    classes of ceil(n/2) nodes where both, padded to 128, fit in the padded axis, else the axis."""
+    pad = lambda m: -(-m // TC_PAD) * TC_PAD
+    h = (n + 1) // 2
+    return [h, h] if fold and 2 * pad(h) <= pad(n) else [n]
+
+
+def issued_tensor_flop(probs, kind, fold=None):
+    """Flops the tensor cores execute in one launch of transform stage `kind` (mixed modes), over
+    the transform problems (mirror classes) of every instance."""
+    fold = _fold_default() if fold is None else fold
     pad = lambda n: -(-n // TC_PAD) * TC_PAD
-    if kind == "low_fwd":
-        return sum(2 * TC_LOW_PRODUCTS * pad(p.ny) * 32 * pad(p.nx) for p in probs)
-    if kind == "low_inv":
-        return sum(2 * TC_LOW_PRODUCTS * pad(p.nx) * pad(p.ny) * 64 for p in probs)
-    s = int(kind[-1])
-    return sum(2 * TC_PRODUCTS * pad(p.nx) * pad(p.ny) * pad(p.nx if s in (0, 2) else p.ny)
-               for p in probs)
+    fl = 0
+    for p in probs:
+        for cx in mirror_classes(p.nx, fold):
+            for cy in mirror_classes(p.ny, fold):
+                if kind == "low_fwd":
+                    fl += 2 * TC_LOW_PRODUCTS * pad(cy) * 32 * pad(cx)
+                elif kind == "low_inv":
+                    fl += 2 * TC_LOW_PRODUCTS * pad(cx) * pad(cy) * 64
+                else:
+                    s = int(kind[-1])
+                    fl += 2 * TC_PRODUCTS * pad(cx) * pad(cy) * pad(cx if s in (0, 2) else cy)
+    return fl
+
+
+def _fold_default():
+    return bool(_OPTION_OVERRIDES.get("fold", 1))
 
 
 def algorithmic_cost(probs, kind):
@@ -131,6 +169,8 @@ def algorithmic_cost(probs, kind):
         return sum(48 * p.nx * p.ny for p in probs), "byte"
     if kind == "split":     # read r (8); write four 16-bit slices (8)
         return sum(16 * p.nx * p.ny for p in probs), "byte"
+    if kind == "unfold":    # read the classes' g (8), r (8), q (8), mask (1); write z (8)
+        return sum(33 * p.nx * p.ny for p in probs), "byte"
     return None, None
 
 
@@ -186,7 +226,7 @@ class ClockSampler:
 # our implementation
 # ----------------------------------------------------------------------------------------------
 def kernel_hash(kind, prec="fp32"):
-    if kind.startswith("prec") or kind == "split":
+    if kind.startswith("prec") or kind in ("split", "unfold") or kind.startswith("low"):
         f = "kernels_gemm_simt.cu" if prec == "fp32" else "kernels_gemm_tc.cu"
     else:
         f = "kernels_grid.cu"
@@ -218,7 +258,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.Stream()
     # hard extend-out grids need up to ~10 n iterations at 1e-8 in FP32 arithmetic
     maxit = 40 * max(max(p.nx, p.ny) for p in probs)
-    ctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=maxit), stream=stream)
+    ctx = ext.ext_create(_options(prec, rtol=1e-8, maxit=maxit), stream=stream)
     dprobs = [ext.problem_of(p) for p in probs]
     phis = [torch.from_numpy(p.phi).cuda() for p in probs]
     fs = [torch.from_numpy(p.f).cuda() for p in probs]
@@ -301,7 +341,7 @@ def run_ours(args, rank, world):
         k = min(args.plain_sample, len(probs))
         same_grids = {"sample": f"first {k} grids of the workload", "grids": k}
         for pname in ("fp32", "mixed_bf16"):
-            cctx = ext.ext_create(ext.options(pname, rtol=1e-8, maxit=maxit), stream=stream)
+            cctx = ext.ext_create(_options(pname, rtol=1e-8, maxit=maxit), stream=stream)
             for mode in ("single", "batched"):
                 # warm: plans and workspaces of these shapes
                 if mode == "single":
@@ -361,7 +401,7 @@ def run_ours(args, rank, world):
     if not args.no_profile and rank == 0:
         # profiled pass: the first 100 iterations, during which every instance is still iterating,
         # so each launch processes the whole workload (the algorithmic cost per launch holds)
-        pctx = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=100, profile=1), stream=stream)
+        pctx = ext.ext_create(_options(prec, rtol=1e-8, maxit=100, profile=1), stream=stream)
         if args.workload == "serve":
             ext.ext_solve_batch(pctx, dprobs, phis, fs, outs, check=False)
         elif len(probs) == 1:
@@ -412,7 +452,7 @@ def run_ours(args, rank, world):
             with open(PEAKS_FILE) as fh:
                 hbm_peak = json.load(fh)["hbm_gbs"]
             hbm = {}
-            for kd in ("stencil", "update", "split"):
+            for kd in ("stencil", "update", "split", "unfold"):
                 amt, un = algorithmic_cost(probs, kd)
                 if kd in prof and prof[kd][1] and un == "byte":
                     gbs = amt / (prof[kd][0] / prof[kd][1] / 1e3) / 1e9
@@ -434,7 +474,9 @@ def run_ours(args, rank, world):
            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
            "data": "synthetic (seeded; paper-shaped interfaces and fields)",
            "config": dict(cfg, l2="flushed between steps (256 MiB write)",
-                          parallelism="replicas" if world > 1 else "single"),
+                          parallelism="replicas" if world > 1 else "single",
+                          low_modes=_options(cfg["prec"]).low_modes,
+                          fold=_options(cfg["prec"]).fold),
            "iterations": iters if len(iters) <= 4 else
            {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},
            "iterations_per_grid": iters[:32],
@@ -507,7 +549,7 @@ def serving_leg(count=48, seed=None, side_lo=64, side_hi=2048, plain_budget_s=20
     probs = [r.problem for r in reqs]
     unit_t = [r.arrival_s for r in reqs]  # arrivals at 1 request/s; scaled per offered rate
     maxit = 40 * max(p.nx for p in probs)
-    ctx = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, maxit=maxit))
+    ctx = ext.ext_create(_options("mixed_bf16", rtol=1e-8, maxit=maxit))
     dprobs = [ext.problem_of(p) for p in probs]
     phis = [torch.from_numpy(p.phi).cuda() for p in probs]
     fs = [torch.from_numpy(p.f).cuda() for p in probs]
@@ -545,7 +587,7 @@ def serving_leg(count=48, seed=None, side_lo=64, side_hi=2048, plain_budget_s=20
     ext.ext_destroy(ctx)
     # the serial plain FP32 path on the same requests (those with sides up to 512: a single
     # large request alone takes the path a minute), in arrival order, within a time budget
-    pctx = ext.ext_create(ext.options("fp32", rtol=1e-8, maxit=maxit))
+    pctx = ext.ext_create(_options("fp32", rtol=1e-8, maxit=maxit))
     done, t0 = 0, time.perf_counter()
     for p, dp, ph, f, o in zip(probs, dprobs, phis, fs, outs):
         if p.nx > 512:

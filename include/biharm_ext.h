@@ -87,14 +87,19 @@ typedef struct {
                               EXT_TUNE_CACHE names a file, in that file; 0: tile_y; default 1.
                               Results do not depend on the tile.                              */
   int32_t tile_y;          /* the stencil's tile height when autotune = 0: 16 or 32 (default) */
-  int32_t low_modes;       /* mixed modes: 1 = the lowest 32 x 32 modes of the preconditioner
-                              (those with the largest weights) come from six-slice tensor-core
-                              products of about 48 bits instead of the four-slice stages
-                              (default); 0 = all modes from the four-slice stages              */
+  int32_t low_modes;       /* mixed modes: 1 = the lowest 32 x 32 modes of each transform
+                              problem (those with the largest weights) come from six-slice
+                              tensor-core products of about 48 bits instead of the four-slice
+                              stages: about 28% fewer iterations at more cost per iteration;
+                              0 = all modes from the four-slice stages (default)              */
   int64_t wait_cycles;     /* bound, in SM clock cycles, of every wait of a kernel for its own
                               tensor copies and tensor-core pipeline; a wait that runs out makes
                               the kernel drain what it issued and return, and the call returns
                               EXT_ETIMEOUT; 0 = 4e9 (about two seconds)                       */
+  int32_t fold;            /* mixed modes: 1 = an axis whose two mirror classes (ceil(n/2) nodes
+                              each), padded to 128, fit in the axis padded to 128 runs its
+                              transforms per class (even and odd vectors under i -> n-1-i: half
+                              the products per stage) (default); 0 = full-size transforms      */
 } ext_options;
 
 /* Kernel kinds reported by ext_profile_read. */
@@ -114,7 +119,8 @@ enum {
   EXT_KERNEL_LOW_FWD = 12,       /* low-mode correction: forward product, middle, inverse    */
   EXT_KERNEL_LOW_MID = 13,
   EXT_KERNEL_LOW_INV = 14,
-  EXT_KERNEL_KINDS = 15
+  EXT_KERNEL_UNFOLD = 15,        /* mirror classes -> masked z, r.z, z.q (folded slots)       */
+  EXT_KERNEL_KINDS = 16
 };
 
 typedef struct {
@@ -242,6 +248,20 @@ int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float*
  * lam (n doubles, lam[k] its eigenvalue) are caller-owned host arrays; T = Q diag(lam) Q^T.
  * Returns EXT_OK, or EXT_EINVAL for n < 4, n > 32768, an unknown bc or a NULL array. */
 int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam);
+
+/* One mirror class of the same axis, computed on the host (no GPU, no context); this is what the
+ * tensor-core preconditioner applies on axes where folding halves the work (Sec. 2.2: the fast
+ * transforms' even/odd symmetry).  The mirror i -> n-1-i maps T onto itself, and the axis has an
+ * orthonormal eigenbasis of even and odd vectors: the DCT-II and DST-I bases as they are, and for
+ * the periodic rule the real Fourier basis sampled at i + 1/2 (same eigenspaces as
+ * ext_axis_basis's).  With h = ceil(n/2), Q (h*h doubles, row-major) holds the class's vectors
+ * restricted to nodes 0..h-1, in ascending order of eigenvalue, and lam (h doubles) their
+ * eigenvalues; columns beyond the class's mode count are zero (eigenvalue 0), and for odd n the
+ * odd class's row h-1 (the middle node) is zero.  cls: 0 = even, 1 = odd.  For r on the n nodes,
+ * the class transform of the folded vector (r[i] + r[n-1-i], or r[i] alone at the middle node, for
+ * cls 0; r[i] - r[n-1-i] for cls 1) equals the full transform's class coefficients.  Returns
+ * EXT_OK, or EXT_EINVAL for n < 4, n > 32768, an unknown bc or cls, or a NULL array. */
+int ext_axis_class_basis(int32_t n, ext_bc bc, int32_t cls, double* Q, double* lam);
 
 /* The tensor-core operand form of the same basis, computed on the host (no GPU, no context): Q
  * and Q^T, zero-padded to np x np (np = n rounded up to a multiple of 128), each row cut into

@@ -55,6 +55,8 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct PlanDev {
   int n = 0, np = 0, bc = 0;
+  int cls = -1;   // -1: the axis basis; 0 / 1: its even / odd mirror class (n = ceil(nfull / 2))
+  int nfull = 0;  // nodes of the axis
   float* q = nullptr;   // [2][np][np]: hi plane, lo plane
   float* qt = nullptr;  // [2][np][np]
   std::vector<double> lam;
@@ -70,6 +72,8 @@ struct PlanDev {
 struct SlotHost {
   ext_problem prob{};
   SlotDesc d{};
+  SlotDesc tcp[kMirClasses]{};  // tensor-core problems (mixed modes): the slot, or its classes
+  int n_tcp = 0;
   char* arena = nullptr;
   size_t bytes = 0;
   float* phi_stage = nullptr;  // device copies when the caller passes host arrays
@@ -86,7 +90,8 @@ struct Workspace {
   WorkItem *d_st = nullptr, *d_vec = nullptr, *d_gm = nullptr;
   WorkItem* d_sl = nullptr;     // one item per slot (tile 0), for the per-slot scalar kernels
   int *d_counts = nullptr;      // [0] grid tiles, [1] vector items, [2] gemm items, [3] slots,
-                                // [4] stencil tiles
+                                // [4] stencil tiles, [5] [6] low-mode tiles, [7] fold items,
+                                // [8] unfold tiles, [9] tensor-core problems
   int n_st = 0, n_vec = 0, n_gm = 0, n_sl = 0;
   WorkItem* d_sten = nullptr;   // the stencil kernel's tiles (64 x sten_ty)
   int n_sten = 0;
@@ -94,6 +99,11 @@ struct Workspace {
   bool tuned = false;
   WorkItem *d_l1 = nullptr, *d_l3 = nullptr;  // tiles of the low-mode products
   int n_l1 = 0, n_l3 = 0;
+  // tensor-core problems (mixed modes): kMirClasses entries per slot, the slot's own descriptor
+  // or its mirror classes; items of the fold and unfold kernels; one item per problem
+  SlotDesc* d_tcp = nullptr;
+  WorkItem *d_fold = nullptr, *d_unfold = nullptr, *d_tcl = nullptr;
+  int n_fold = 0, n_unfold = 0, n_tcl = 0;
   const float** d_phis = nullptr;
   const float** d_fs = nullptr;
   float** d_outs = nullptr;
@@ -110,7 +120,11 @@ struct Workspace {
   cudaStream_t stream = nullptr;  // the context's stream, or the serving worker's own
 };
 
-int plan_key(int n, int bc) { return n * 4 + bc; }
+int plan_key(int n, int bc, int cls) { return (n * 4 + bc) * 3 + cls + 1; }
+
+AxisBasis plan_basis(int nfull, int bc, int cls) {
+  return cls < 0 ? make_axis_basis(nfull, bc) : make_class_basis(nfull, bc, cls);
+}
 
 }  // namespace
 
@@ -270,15 +284,15 @@ static int block_exp_host(const double* v, size_t stride, int count) {
 // Q and Q^T of one axis (n nodes, rule bc) as block-scaled slices, zero-padded to np x np, with
 // their exponents: h = [Q slices (NS planes)][Q^T slices (NS planes)], each plane [np][np];
 // ex = [exponents of Q rows][exponents of Q^T rows], each [np][np / KB].
-static void slice_plan_host(int n, int bc, int np, int split, std::vector<uint16_t>& h,
-                            std::vector<int8_t>& ex) {
+static void slice_plan_basis(const AxisBasis& B, int np, int split, std::vector<uint16_t>& h,
+                             std::vector<int8_t>& ex) {
+  const int n = B.n;
   const int NS = tc_planes(split);
   const int KB = tc_block();  // k per block exponent of the sliced operands
   const int nkb = np / KB;
   const size_t plane = (size_t)np * np;
   h.assign(2 * NS * plane, 0);
   ex.assign(2 * (size_t)np * nkb, 0);
-  AxisBasis B = make_axis_basis(n, bc);
   std::vector<double> Qp((size_t)np * np, 0.0), QTp((size_t)np * np, 0.0);
   for (int i = 0; i < n; ++i)
     for (int k = 0; k < n; ++k) {
@@ -300,6 +314,11 @@ static void slice_plan_host(int n, int bc, int np, int split, std::vector<uint16
   }
 }
 
+static void slice_plan_host(int n, int bc, int np, int split, std::vector<uint16_t>& h,
+                            std::vector<int8_t>& ex) {
+  slice_plan_basis(make_axis_basis(n, bc), np, split, h, ex);
+}
+
 static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
   if (P->tc && P->tc_split == ctx->split) return EXT_OK;
   if (P->tc) {
@@ -308,7 +327,8 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
   }
   std::vector<uint16_t> h;
   std::vector<int8_t> ex;
-  slice_plan_host(P->n, P->bc, P->np, ctx->split, h, ex);
+  const AxisBasis B = plan_basis(P->nfull, P->bc, P->cls);
+  slice_plan_basis(B, P->np, ctx->split, h, ex);
   const size_t bytes = 2 * h.size() + ex.size();
   if (cudaMalloc(&P->tc, bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -325,7 +345,6 @@ static int ensure_tc_plan(ext_ctx* ctx, PlanDev* P) {
   }
   const int np = P->np, nkb = np / tc_block();
   const int m = std::min(kLowM, P->n);
-  AxisBasis B = make_axis_basis(P->n, P->bc);
   auto Qv = [&](int i, int k) { return (i < P->n && k < m) ? B.Q[(size_t)i * P->n + k] : 0.0; };
   const size_t pt = (size_t)kLowM * np, pq = (size_t)np * kLowK3;
   std::vector<uint16_t> lt(kLowNS * pt, 0), lq(kLowNS * pq, 0);
@@ -380,18 +399,20 @@ static const int8_t* plan_exps(const PlanDev* P, int t) {
          t * (size_t)P->np * nkb;
 }
 
-static int get_plan(ext_ctx* ctx, int n, int bc, PlanDev** out) {
-  const int key = plan_key(n, bc);
+static int get_plan(ext_ctx* ctx, int n, int bc, int cls, PlanDev** out) {
+  const int key = plan_key(n, bc, cls);
   auto it = ctx->plans.find(key);
   if (it != ctx->plans.end()) {
     *out = &it->second;
     return EXT_OK;
   }
-  AxisBasis B = make_axis_basis(n, bc);
+  AxisBasis B = plan_basis(n, bc, cls);
   PlanDev P;
-  P.n = n;
+  P.n = B.n;
+  P.nfull = n;
+  P.cls = cls;
   P.bc = bc;
-  P.np = pad_to(n, kPad);
+  P.np = pad_to(B.n, kPad);
   P.lam = B.lam;
   std::vector<float> q, qt;
   padded_df(B, P.np, q, qt);
@@ -445,6 +466,10 @@ static void free_workspace(Workspace* W) {
   cudaFree(W->d_sl);
   cudaFree(W->d_l1);
   cudaFree(W->d_l3);
+  cudaFree(W->d_tcp);
+  cudaFree(W->d_fold);
+  cudaFree(W->d_unfold);
+  cudaFree(W->d_tcl);
   cudaFree(W->d_counts);
   cudaFree(W->d_phis);
   cudaFree(W->d_fs);
@@ -466,19 +491,20 @@ static std::string shape_key(int count, const ext_problem* probs, bool host_io) 
   return k;
 }
 
-// Build the device state of `count` problems (no inputs yet).
-// Device state of one problem: plans, arena layout (allocated here unless `arena` is given),
-// slot descriptor and tensor maps.  With size_only, only s.bytes is computed.
+// Device state of one problem: plans, arena layout (allocated here unless `arena` is given), slot
+// descriptor, its tensor-core problems and their tensor maps.  With size_only, only s.bytes is
+// computed.
 static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotHost& s,
                       char* arena = nullptr, bool size_only = false) {
   std::lock_guard<std::recursive_mutex> plk(ctx->plan_mu);
   s.prob = prob;
   s.d = SlotDesc{};
+  s.n_tcp = 0;
   const int nx = prob.nx, ny = prob.ny;
   PlanDev *px, *py;
-  int rc = get_plan(ctx, nx, prob.bc_x, &px);
+  int rc = get_plan(ctx, nx, prob.bc_x, -1, &px);
   if (rc) return rc;
-  rc = get_plan(ctx, ny, prob.bc_y, &py);
+  rc = get_plan(ctx, ny, prob.bc_y, -1, &py);
   if (rc) return rc;
   SlotDesc& d = s.d;
   d.nx = nx;
@@ -494,15 +520,28 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.n_vec_items = (int)((N + kVecChunk - 1) / kVecChunk);
   const int n_gm = (d.nxp / 128) * (d.nyp / 64);
   d.n_gm_tiles = n_gm;
+  d.n_tc_tiles = n_gm;
   set_weights(d, prob.hx, prob.hy);
-  const int n_part = std::max(d.n_st_tiles, std::max(d.n_vec_items, n_gm));
+  // the tensor-core transforms fold an axis by its mirror symmetry where both classes, padded,
+  // fit in the padded axis: each stage then does half the products
+  d.mir = 0;
+  if (ctx->tc && ctx->opt.fold) {
+    if (mirror_pays(nx, kPad)) d.mir |= 1;
+    if (mirror_pays(ny, kPad)) d.mir |= 2;
+  }
+  d.mhx = (d.mir & 1) ? mirror_half(nx) : nx;
+  d.mhy = (d.mir & 2) ? mirror_half(ny) : ny;
+  d.n_fold_items = d.mir ? ((d.mhy + 7) / 8) * ((d.mhx + 127) / 128) : 0;
+  d.n_unfold_tiles = d.mir ? ((d.mhx + 31) / 32) * ((d.mhy + 7) / 8) : 0;
+  d.n_prec_parts = d.mir ? d.n_unfold_tiles : n_gm;
+  const int n_part = std::max(std::max(d.n_st_tiles, d.n_vec_items), std::max(n_gm, d.n_unfold_tiles));
   const size_t Np = (size_t)d.nxp * d.nyp;
   // arena layout
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes, 256); return o; };
   const size_t o_b = take(8 * N), o_x = take(4 * N), o_xl = take(4 * N);
   const size_t o_part = take(8 * 4 * (size_t)n_part);
-  const size_t o_pqp = take(8 * (size_t)ny * ((nx + 31) / 32));
+  const size_t o_pqp = take(8 * (size_t)((ny + 15) / 16) * ((nx + 31) / 32));
   const size_t o_r = take(4 * N), o_p0 = take(4 * N), o_p1 = take(4 * N);
   const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
   const size_t o_rl = take(4 * N), o_p0l = take(4 * N), o_p1l = take(4 * N);
@@ -515,25 +554,45 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   if (host_io) o_io = take(12 * N);
   const bool st_copy = stencil_copies_fit(nx);
   const size_t o_smaps = st_copy ? take(kStMaps * sizeof(CUtensorMap)) : 0;
+  // tensor-core problems: the slot itself, or its classes c = 2 cls_y + cls_x
+  struct TcLay {
+    int c = 0;
+    PlanDev *px = nullptr, *py = nullptr;
+    size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0, o_lx = 0, o_ly = 0;
+    size_t o_g = 0, o_lh = 0, o_ljt = 0, o_ljte = 0, o_lz = 0, o_lmaps = 0;
+  };
+  std::vector<TcLay> tl;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
-  size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0;
-  size_t o_lh = 0, o_ljt = 0, o_ljte = 0, o_lz = 0, o_lmaps = 0;
-  const size_t nex = Np / 64;  // block exponents of one operand
   const bool low = ctx->tc && ctx->opt.low_modes != 0;
   if (ctx->tc) {
-    o_tr = take(2 * (low ? kLowNS : NS) * Np);
-    o_tt1 = take(2 * NS * Np);
-    o_tt2 = take(2 * NS * Np);
-    o_tt3 = take(2 * NS * Np);
-    o_maps = take(8 * sizeof(CUtensorMap));
-    o_ex = take(4 * nex);
-  }
-  if (low) {
-    o_lh = take(2 * 4 * (size_t)ny * kLowM);
-    o_ljt = take(2 * (size_t)kLowNS * d.nxp * kLowK3);
-    o_ljte = take((size_t)d.nxp);
-    o_lz = take(2 * 4 * N);
-    o_lmaps = take(4 * sizeof(CUtensorMap));
+    for (int cy = 0; cy < ((d.mir & 2) ? 2 : 1); ++cy)
+      for (int cx = 0; cx < ((d.mir & 1) ? 2 : 1); ++cx) {
+        TcLay L;
+        L.c = 2 * cy + cx;
+        rc = get_plan(ctx, nx, prob.bc_x, (d.mir & 1) ? cx : -1, &L.px);
+        if (!rc) rc = get_plan(ctx, ny, prob.bc_y, (d.mir & 2) ? cy : -1, &L.py);
+        if (rc) return rc;
+        const size_t Npc = (size_t)L.px->np * L.py->np;
+        L.o_tr = take(2 * (low ? kLowNS : NS) * Npc);
+        L.o_tt1 = take(2 * NS * Npc);
+        L.o_tt2 = take(2 * NS * Npc);
+        L.o_tt3 = take(2 * NS * Npc);
+        L.o_maps = take(8 * sizeof(CUtensorMap));
+        L.o_ex = take(4 * (Npc / 64));
+        if (d.mir) {
+          L.o_lx = take(4 * (size_t)L.px->np);
+          L.o_ly = take(4 * (size_t)L.py->np);
+          L.o_g = take(2 * 4 * (size_t)L.px->n * L.py->n);
+        }
+        if (low) {
+          L.o_lh = take(4 * 2 * (size_t)kLowM * kLowM * (L.py->np / 128));  // G shares
+          L.o_ljt = take(2 * (size_t)kLowNS * L.px->np * kLowK3);
+          L.o_ljte = take((size_t)L.px->np);
+          L.o_lz = take(2 * 4 * (size_t)L.px->n * L.py->n);
+          L.o_lmaps = take(4 * sizeof(CUtensorMap));
+        }
+        tl.push_back(L);
+      }
   }
   s.bytes = off;
   if (size_only) return EXT_OK;
@@ -568,7 +627,6 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.t1_lo = (float*)(A + o_t1l);
   d.t2_lo = (float*)(A + o_t2l);
   d.t3_lo = (float*)(A + o_t3l);
-  d.n_tc_tiles = n_gm;
   d.st_maps = nullptr;
   if (st_copy) {
     CUtensorMap smaps[kStMaps];
@@ -576,68 +634,6 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
     if (rc1) return rc1;
     BX_CUDA(cudaMemcpy(A + o_smaps, smaps, sizeof(smaps), cudaMemcpyHostToDevice));
     d.st_maps = A + o_smaps;
-  }
-  if (ctx->tc) {
-    int rc2 = ensure_tc_plan(ctx, px);
-    if (!rc2) rc2 = ensure_tc_plan(ctx, py);
-    if (rc2) return rc2;
-    d.tc_r = A + o_tr;
-    d.tc_t1 = A + o_tt1;
-    d.tc_t2 = A + o_tt2;
-    d.tc_t3 = A + o_tt3;
-    d.tmaps = A + o_maps;
-    for (int k = 0; k < 4; ++k) d.tc_e[k] = (int8_t*)(A + o_ex + k * nex);
-    d.tc_eb[0] = plan_exps(px, 1);  // Qx^T rows
-    d.tc_eb[1] = plan_exps(py, 1);  // Qy^T rows
-    d.tc_eb[2] = plan_exps(px, 0);  // Qx rows
-    d.tc_eb[3] = plan_exps(py, 0);  // Qy rows
-    BX_CUDA(cudaMemset(d.tc_r, 0, 2 * (low ? kLowNS : NS) * Np));
-    BX_CUDA(cudaMemset(A + o_ex, 0, 4 * nex));
-    const bool bf = ctx->split == 1;
-    const size_t qplane = 0;
-    (void)qplane;
-    CUtensorMap maps[8];
-    const size_t pxp = (size_t)d.nxp * d.nxp, pyp = (size_t)d.nyp * d.nyp;
-    uint16_t* qxb = (uint16_t*)px->tc;
-    uint16_t* qyb = (uint16_t*)py->tc;
-    // A operands: r planes [P][nyp][nxp], T1 [P][nxp][nyp], T2 [P][nyp][nxp], T3 [P][nxp][nyp]
-    int rc3 = make_tmap(&maps[0], d.tc_r, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
-    if (!rc3) rc3 = make_tmap(&maps[1], d.tc_t1, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
-    if (!rc3) rc3 = make_tmap(&maps[2], d.tc_t2, bf, d.nxp, (uint64_t)NS * d.nyp, 128);
-    if (!rc3) rc3 = make_tmap(&maps[3], d.tc_t3, bf, d.nyp, (uint64_t)NS * d.nxp, 128);
-    // B operands: Qx^T, Qy^T, Qx, Qy planes
-    if (!rc3) rc3 = make_tmap(&maps[4], qxb + NS * pxp, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
-    if (!rc3) rc3 = make_tmap(&maps[5], qyb + NS * pyp, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
-    if (!rc3) rc3 = make_tmap(&maps[6], qxb, bf, d.nxp, (uint64_t)NS * d.nxp, 64);
-    if (!rc3) rc3 = make_tmap(&maps[7], qyb, bf, d.nyp, (uint64_t)NS * d.nyp, 64);
-    if (rc3) return rc3;
-    BX_CUDA(cudaMemcpy(A + o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
-  }
-  d.lowm_x = d.lowm_y = 0;
-  if (low) {
-    d.lowm_x = std::min(kLowM, nx);
-    d.lowm_y = std::min(kLowM, ny);
-    d.low_h = (float*)(A + o_lh);
-    d.low_jt = A + o_ljt;
-    d.low_jt_e = (int8_t*)(A + o_ljte);
-    d.low_z = (float*)(A + o_lz);
-    const char* lx = (const char*)px->low;
-    const char* ly = (const char*)py->low;
-    d.low_qxd = (const float*)(lx + px->low_off_d);
-    d.low_qyd = (const float*)(ly + py->low_off_d);
-    d.low_qxt_e = (const int8_t*)(lx + px->low_off_te);
-    d.low_qy_e = (const int8_t*)(ly + py->low_off_qe);
-    d.n_l1_tiles = d.nyp / 128;
-    d.n_l3_tiles = d.nxp / 128;  // inverse product: one item per 128 rows of x
-    const bool bf = ctx->split == 1;
-    CUtensorMap lm[4];
-    int rc4 = make_tmap(&lm[0], d.tc_r, bf, d.nxp, (uint64_t)kLowNS * d.nyp, 128);
-    if (!rc4) rc4 = make_tmap(&lm[1], px->low, bf, d.nxp, (uint64_t)kLowNS * kLowM, kLowM);
-    if (!rc4) rc4 = make_tmap(&lm[2], d.low_jt, bf, kLowK3, (uint64_t)kLowNS * d.nxp, 128);
-    if (!rc4) rc4 = make_tmap(&lm[3], (char*)py->low + py->low_off_q, bf, kLowK3, (uint64_t)kLowNS * d.nyp, kLowM);
-    if (rc4) return rc4;
-    BX_CUDA(cudaMemcpy(A + o_lmaps, lm, sizeof(lm), cudaMemcpyHostToDevice));
-    d.low_maps = A + o_lmaps;
   }
   d.qx = px->q;
   d.qxt = px->qt;
@@ -677,6 +673,139 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.lamy = (const float*)(A + o_ly);
   BX_CUDA(cudaMemcpy(A + o_lx, lx.data(), 4 * lx.size(), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMemcpy(A + o_ly, ly.data(), 4 * ly.size(), cudaMemcpyHostToDevice));
+  // the tensor-core problems
+  const bool bf = ctx->split == 1;
+  for (const TcLay& L : tl) {
+    SlotDesc t = d;  // the slot's fields; a class problem overrides its domain and operands below
+    PlanDev* qx = L.px;
+    PlanDev* qy = L.py;
+    int rc2 = ensure_tc_plan(ctx, qx);
+    if (!rc2) rc2 = ensure_tc_plan(ctx, qy);
+    if (rc2) return rc2;
+    if (d.mir) {
+      t.nx = qx->n;
+      t.ny = qy->n;
+      t.nxp = qx->np;
+      t.nyp = qy->np;
+      t.n_gm_tiles = t.n_tc_tiles = (t.nxp / 128) * (t.nyp / 64);
+      t.mir = 0;
+      t.mir_out = 1;
+      // only the transform fields are live: grid vectors of the slot stay out of reach
+      t.mask = nullptr;
+      t.b = nullptr;
+      t.xhi = t.xlo = nullptr;
+      t.r = t.r_lo = t.q = t.q_lo = nullptr;
+      t.p[0] = t.p[1] = t.p_lo[0] = t.p_lo[1] = nullptr;
+      t.part = t.pq_part = nullptr;
+      t.t1 = t.t2 = t.t3 = t.t1_lo = t.t2_lo = t.t3_lo = nullptr;
+      t.st_maps = nullptr;
+      t.z = (float*)(A + L.o_g);  // the class result g, [ny][nx] hi then lo
+      t.z_lo = t.z + (size_t)t.nx * t.ny;
+      std::vector<float> lxc(t.nxp, 0.f), lyc(t.nyp, 0.f);
+      for (int k = 0; k < t.nx; ++k) lxc[k] = (float)(qx->lam[k] * a);
+      for (int k = 0; k < t.ny; ++k) lyc[k] = (float)(qy->lam[k] * c);
+      BX_CUDA(cudaMemcpy(A + L.o_lx, lxc.data(), 4 * lxc.size(), cudaMemcpyHostToDevice));
+      BX_CUDA(cudaMemcpy(A + L.o_ly, lyc.data(), 4 * lyc.size(), cudaMemcpyHostToDevice));
+      t.lamx = (const float*)(A + L.o_lx);
+      t.lamy = (const float*)(A + L.o_ly);
+    }
+    const size_t Npc = (size_t)t.nxp * t.nyp, nex = Npc / 64;
+    t.tc_r = A + L.o_tr;
+    t.tc_t1 = A + L.o_tt1;
+    t.tc_t2 = A + L.o_tt2;
+    t.tc_t3 = A + L.o_tt3;
+    t.tmaps = A + L.o_maps;
+    for (int k = 0; k < 4; ++k) t.tc_e[k] = (int8_t*)(A + L.o_ex + k * nex);
+    t.tc_eb[0] = plan_exps(qx, 1);  // Qx^T rows
+    t.tc_eb[1] = plan_exps(qy, 1);  // Qy^T rows
+    t.tc_eb[2] = plan_exps(qx, 0);  // Qx rows
+    t.tc_eb[3] = plan_exps(qy, 0);  // Qy rows
+    BX_CUDA(cudaMemset(t.tc_r, 0, 2 * (low ? kLowNS : NS) * Npc));
+    BX_CUDA(cudaMemset(A + L.o_ex, 0, 4 * nex));
+    CUtensorMap maps[8];
+    const size_t pxp = (size_t)t.nxp * t.nxp, pyp = (size_t)t.nyp * t.nyp;
+    uint16_t* qxb = (uint16_t*)qx->tc;
+    uint16_t* qyb = (uint16_t*)qy->tc;
+    // A operands: r planes [P][nyp][nxp], T1 [P][nxp][nyp], T2 [P][nyp][nxp], T3 [P][nxp][nyp]
+    int rc3 = make_tmap(&maps[0], t.tc_r, bf, t.nxp, (uint64_t)NS * t.nyp, 128);
+    if (!rc3) rc3 = make_tmap(&maps[1], t.tc_t1, bf, t.nyp, (uint64_t)NS * t.nxp, 128);
+    if (!rc3) rc3 = make_tmap(&maps[2], t.tc_t2, bf, t.nxp, (uint64_t)NS * t.nyp, 128);
+    if (!rc3) rc3 = make_tmap(&maps[3], t.tc_t3, bf, t.nyp, (uint64_t)NS * t.nxp, 128);
+    // B operands: Qx^T, Qy^T, Qx, Qy planes
+    if (!rc3) rc3 = make_tmap(&maps[4], qxb + NS * pxp, bf, t.nxp, (uint64_t)NS * t.nxp, 64);
+    if (!rc3) rc3 = make_tmap(&maps[5], qyb + NS * pyp, bf, t.nyp, (uint64_t)NS * t.nyp, 64);
+    if (!rc3) rc3 = make_tmap(&maps[6], qxb, bf, t.nxp, (uint64_t)NS * t.nxp, 64);
+    if (!rc3) rc3 = make_tmap(&maps[7], qyb, bf, t.nyp, (uint64_t)NS * t.nyp, 64);
+    if (rc3) return rc3;
+    BX_CUDA(cudaMemcpy(A + L.o_maps, maps, sizeof(maps), cudaMemcpyHostToDevice));
+    t.lowm_x = t.lowm_y = 0;
+    if (low) {
+      t.lowm_x = std::min(kLowM, t.nx);
+      t.lowm_y = std::min(kLowM, t.ny);
+      t.low_gp = (float*)(A + L.o_lh);
+      t.low_jt = A + L.o_ljt;
+      t.low_jt_e = (int8_t*)(A + L.o_ljte);
+      t.low_z = (float*)(A + L.o_lz);
+      const char* lxp = (const char*)qx->low;
+      const char* lyp = (const char*)qy->low;
+      t.low_qxd = (const float*)(lxp + qx->low_off_d);
+      t.low_qyd = (const float*)(lyp + qy->low_off_d);
+      t.low_qxt_e = (const int8_t*)(lxp + qx->low_off_te);
+      t.low_qy_e = (const int8_t*)(lyp + qy->low_off_qe);
+      t.n_l1_tiles = t.nyp / 128;
+      t.n_l3_tiles = t.nxp / 128;  // inverse product: one item per 128 rows of x
+      CUtensorMap lm[4];
+      int rc4 = make_tmap(&lm[0], t.tc_r, bf, t.nxp, (uint64_t)kLowNS * t.nyp, 128);
+      if (!rc4) rc4 = make_tmap(&lm[1], qx->low, bf, t.nxp, (uint64_t)kLowNS * kLowM, kLowM);
+      if (!rc4) rc4 = make_tmap(&lm[2], t.low_jt, bf, kLowK3, (uint64_t)kLowNS * t.nxp, 128);
+      if (!rc4) rc4 = make_tmap(&lm[3], (char*)qy->low + qy->low_off_q, bf, kLowK3, (uint64_t)kLowNS * t.nyp, kLowM);
+      if (rc4) return rc4;
+      BX_CUDA(cudaMemcpy(A + L.o_lmaps, lm, sizeof(lm), cudaMemcpyHostToDevice));
+      t.low_maps = A + L.o_lmaps;
+    }
+    s.tcp[L.c] = t;
+  }
+  s.n_tcp = (int)tl.size();
+  if (ctx->tc && !d.mir) d = s.tcp[0];  // the slot is its own problem (k_tc_prepare reads it)
+  return EXT_OK;
+}
+
+// The slot's scalars, in the slot descriptor and in each of its tensor-core problems.
+static void set_slot_scalars(SlotHost& s, SlotScalars* sc) {
+  s.d.sc = sc;
+  for (int c = 0; c < kMirClasses; ++c) s.tcp[c].sc = sc;
+}
+
+// Work items of the tensor-core problems of slot i (problem index kMirClasses * i + c).
+static void tc_items(const SlotHost& s, int i, std::vector<WorkItem>& gm, std::vector<WorkItem>& l1,
+                     std::vector<WorkItem>& l3, std::vector<WorkItem>& tcl) {
+  for (int c = 0; c < kMirClasses; ++c) {
+    if (s.d.mir == 0 && c > 0) break;
+    if (((c & 1) && !(s.d.mir & 1)) || ((c & 2) && !(s.d.mir & 2))) continue;
+    const SlotDesc& t = s.tcp[c];
+    const int k = kMirClasses * i + c;
+    for (int tt = 0; tt < t.n_gm_tiles; ++tt) gm.push_back({k, tt});
+    if (t.lowm_x) {
+      for (int tt = 0; tt < t.n_l1_tiles; ++tt) l1.push_back({k, tt});
+      for (int tt = 0; tt < t.n_l3_tiles; ++tt) l3.push_back({k, tt});
+    }
+    tcl.push_back({k, 0});
+  }
+}
+
+// Tensor-core work items in the order the persistent kernels take them (longest first).
+static void longest_first_tc(std::vector<WorkItem>& gm, const std::vector<SlotHost>& slots) {
+  std::stable_sort(gm.begin(), gm.end(), [&](const WorkItem& a, const WorkItem& b) {
+    const SlotDesc& da = slots[a.slot / kMirClasses].tcp[a.slot % kMirClasses];
+    const SlotDesc& db = slots[b.slot / kMirClasses].tcp[b.slot % kMirClasses];
+    return std::max(da.nxp, da.nyp) > std::max(db.nxp, db.nyp);
+  });
+}
+
+template <class T>
+static int upload(T** dst, const std::vector<T>& v) {
+  BX_CUDA(cudaMalloc(dst, sizeof(T) * std::max<size_t>(1, v.size())));
+  if (!v.empty()) BX_CUDA(cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
   return EXT_OK;
 }
 
@@ -686,7 +815,7 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   W->key = shape_key(count, probs, host_io);
   W->host_io = host_io;
   W->slots.resize(count);
-  std::vector<WorkItem> st, vec, gm, l1, l3;
+  std::vector<WorkItem> st, vec, gm, l1, l3, fold, unfold, tcl;
   for (int i = 0; i < count; ++i) {
     SlotHost& s = W->slots[i];
     int rc = build_slot(ctx, probs[i], host_io, s);
@@ -699,13 +828,16 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     if (d.aniso) W->aniso = true;
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
-    for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
-    if (d.lowm_x) {
-      for (int t = 0; t < d.n_l1_tiles; ++t) l1.push_back({i, t});
-      for (int t = 0; t < d.n_l3_tiles; ++t) l3.push_back({i, t});
+    if (ctx->tc) {
+      tc_items(s, i, gm, l1, l3, tcl);
+      for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
+      for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
+    } else {
+      for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
     }
   }
-  longest_first(gm, W->slots);
+  if (ctx->tc) longest_first_tc(gm, W->slots);
+  else longest_first(gm, W->slots);
   std::vector<WorkItem> sl;
   for (int i = 0; i < count; ++i) sl.push_back({i, 0});
   W->n_sl = (int)sl.size();
@@ -715,29 +847,34 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   BX_CUDA(cudaMalloc(&W->d_sc, sizeof(SlotScalars) * count));
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * count));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * count));
-  for (int i = 0; i < count; ++i) W->slots[i].d.sc = W->d_sc + i;
-  std::vector<SlotDesc> descs(count);
-  for (int i = 0; i < count; ++i) descs[i] = W->slots[i].d;
-  BX_CUDA(cudaMalloc(&W->d_slots, sizeof(SlotDesc) * count));
-  BX_CUDA(cudaMemcpy(W->d_slots, descs.data(), sizeof(SlotDesc) * count, cudaMemcpyHostToDevice));
-  BX_CUDA(cudaMalloc(&W->d_st, sizeof(WorkItem) * st.size()));
-  BX_CUDA(cudaMalloc(&W->d_vec, sizeof(WorkItem) * vec.size()));
-  BX_CUDA(cudaMalloc(&W->d_gm, sizeof(WorkItem) * gm.size()));
-  BX_CUDA(cudaMemcpy(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice));
-  BX_CUDA(cudaMemcpy(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice));
-  BX_CUDA(cudaMemcpy(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice));
-  BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * sl.size()));
-  BX_CUDA(cudaMemcpy(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice));
+  for (int i = 0; i < count; ++i) set_slot_scalars(W->slots[i], W->d_sc + i);
+  std::vector<SlotDesc> descs(count), tcps(ctx->tc ? kMirClasses * count : 0);
+  for (int i = 0; i < count; ++i) {
+    descs[i] = W->slots[i].d;
+    if (ctx->tc)
+      for (int c = 0; c < kMirClasses; ++c) tcps[kMirClasses * i + c] = W->slots[i].tcp[c];
+  }
+  int rc = upload(&W->d_slots, descs);
+  if (!rc) rc = upload(&W->d_tcp, tcps);
+  if (!rc) rc = upload(&W->d_st, st);
+  if (!rc) rc = upload(&W->d_vec, vec);
+  if (!rc) rc = upload(&W->d_gm, gm);
+  if (!rc) rc = upload(&W->d_sl, sl);
+  if (!rc) rc = upload(&W->d_sten, st);
+  if (!rc) rc = upload(&W->d_l1, l1);
+  if (!rc) rc = upload(&W->d_l3, l3);
+  if (!rc) rc = upload(&W->d_fold, fold);
+  if (!rc) rc = upload(&W->d_unfold, unfold);
+  if (!rc) rc = upload(&W->d_tcl, tcl);
+  if (rc) return rc;
   W->n_sten = W->n_st;
-  BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * st.size()));
-  BX_CUDA(cudaMemcpy(W->d_sten, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice));
   W->n_l1 = (int)l1.size();
   W->n_l3 = (int)l3.size();
-  BX_CUDA(cudaMalloc(&W->d_l1, sizeof(WorkItem) * std::max<size_t>(1, l1.size())));
-  BX_CUDA(cudaMalloc(&W->d_l3, sizeof(WorkItem) * std::max<size_t>(1, l3.size())));
-  if (!l1.empty()) BX_CUDA(cudaMemcpy(W->d_l1, l1.data(), sizeof(WorkItem) * l1.size(), cudaMemcpyHostToDevice));
-  if (!l3.empty()) BX_CUDA(cudaMemcpy(W->d_l3, l3.data(), sizeof(WorkItem) * l3.size(), cudaMemcpyHostToDevice));
-  int counts[7] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten, W->n_l1, W->n_l3};
+  W->n_fold = (int)fold.size();
+  W->n_unfold = (int)unfold.size();
+  W->n_tcl = (int)tcl.size();
+  int counts[10] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten, W->n_l1, W->n_l3,
+                    W->n_fold, W->n_unfold, W->n_tcl};
   BX_CUDA(cudaMalloc(&W->d_counts, sizeof(counts)));
   BX_CUDA(cudaMemcpy(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * count));
@@ -775,9 +912,18 @@ static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
   LaunchCfg c;
   c.wait_cycles = ctx->opt.wait_cycles;
   c.slots = W->d_slots;
+  c.tcp = W->d_tcp;
   c.stream = W->stream ? W->stream : ctx->stream;
   const int cap = ctx->sm_count * 8;
-  if (which == 0) {
+  if (which == 7 || which == 8) {
+    c.items = which == 7 ? W->d_fold : W->d_unfold;
+    c.n_items = W->d_counts + which;
+    c.grid = std::max(1, std::min(which == 7 ? W->n_fold : W->n_unfold, cap));
+  } else if (which == 9) {
+    c.items = W->d_tcl;
+    c.n_items = W->d_counts + 9;
+    c.grid = std::max(1, std::min(W->n_tcl, cap));
+  } else if (which == 0) {
     c.items = W->d_st;
     c.n_items = W->d_counts + 0;
     c.grid = std::max(1, std::min(W->n_st, cap));
@@ -868,12 +1014,20 @@ static void harvest(ext_ctx* ctx) {
 static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
   LaunchCfg g = cfg_of(ctx, W, 2);
   if (ctx->tc) {
+    // residual slices: unfolded slots directly, folded slots per mirror class
     const LaunchCfg st = cfg_of(ctx, W, 0);
-    timed(ctx, EXT_KERNEL_SPLIT, [&] { launch_prec_tc_prepare(st, mode, ctx->split); }, g.stream);
+    timed(ctx, EXT_KERNEL_SPLIT, [&] {
+      launch_prec_tc_prepare(st, mode, ctx->split);
+      if (W->n_fold > 0) launch_tc_fold(cfg_of(ctx, W, 7), mode, ctx->split);
+    }, g.stream);
+    // the transform kernels run over the tensor-core problems
+    g.slots = W->d_tcp;
     g.grid = std::max(1, std::min(W->n_gm, ctx->sm_count));
     if (W->n_l1 > 0) {
       // the lowest modes in high precision: forward product, middle, inverse product
-      const LaunchCfg c1 = cfg_of(ctx, W, 5), cm = cfg_of(ctx, W, 3), c3 = cfg_of(ctx, W, 6);
+      LaunchCfg c1 = cfg_of(ctx, W, 5), cm = cfg_of(ctx, W, 6), c3 = cfg_of(ctx, W, 6);
+      c1.slots = cm.slots = c3.slots = W->d_tcp;
+      cm.grid = std::max(1, std::min(W->n_l3, ctx->sm_count * 8));  // the middle: small blocks
       timed(ctx, EXT_KERNEL_LOW_FWD, [&] { launch_low_tc(c1, 0, mode, ctx->split, ctx->d_err); }, g.stream);
       timed(ctx, EXT_KERNEL_LOW_MID, [&] { launch_low_mid(cm, mode, ctx->split); }, g.stream);
       timed(ctx, EXT_KERNEL_LOW_INV, [&] { launch_low_tc(c3, 1, mode, ctx->split, ctx->d_err); }, g.stream);
@@ -885,6 +1039,8 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
       else launch_prec_tc(g, s, mode, ctx->split, ctx->d_err);
     }, g.stream);
   }
+  if (ctx->tc && W->n_unfold > 0)
+    timed(ctx, EXT_KERNEL_UNFOLD, [&] { launch_unfold(cfg_of(ctx, W, 8), mode); }, g.stream);
   const LaunchCfg f = cfg_of(ctx, W, 3);  // one block per slot
   timed(ctx, EXT_KERNEL_PREC_FINISH, [&] { launch_prec_finish(f, mode); }, f.stream);
 }
@@ -947,8 +1103,8 @@ static int ensure_graph(ext_ctx* ctx, Workspace* W) {
 
 // ---- stencil tile shape and its autotuner ----------------------------------------------------
 // Re-tile the stencil of every slot of W with tiles 64 x ty: the work list, the tile counts and
-// the tensor maps' box heights.  The p.q partials do not depend on the tile (32-node row
-// segments), so any shape gives the same results.
+// the tensor maps' box heights.  The p.q partials do not depend on the tile (64 x 16 node
+// blocks), so any shape gives the same results.
 static int set_stencil_shape(ext_ctx* ctx, Workspace* W, int ty) {
   if (W->sten_ty == ty) return EXT_OK;
   cudaStream_t s = W->stream ? W->stream : ctx->stream;
@@ -1224,7 +1380,8 @@ void ext_options_default(ext_options* o) {
   o->max_slots = 256;
   o->autotune = 1;
   o->tile_y = 32;
-  o->low_modes = 1;
+  o->low_modes = 0;
+  o->fold = 1;
 }
 
 const char* ext_strerror(int code) {
@@ -1261,6 +1418,14 @@ int ext_axis_slices(int32_t n, ext_bc bc, int32_t type, uint16_t* codes, int8_t*
 int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam) {
   if (n < 4 || n > 32768 || bc < 0 || bc > 2 || !Q || !lam) return EXT_EINVAL;
   const AxisBasis B = make_axis_basis(n, bc);
+  std::copy(B.Q.begin(), B.Q.end(), Q);
+  std::copy(B.lam.begin(), B.lam.end(), lam);
+  return EXT_OK;
+}
+
+int ext_axis_class_basis(int32_t n, ext_bc bc, int32_t cls, double* Q, double* lam) {
+  if (n < 4 || n > 32768 || bc < 0 || bc > 2 || (cls != 0 && cls != 1) || !Q || !lam) return EXT_EINVAL;
+  const AxisBasis B = make_class_basis(n, bc, cls);
   std::copy(B.Q.begin(), B.Q.end(), Q);
   std::copy(B.lam.begin(), B.lam.end(), lam);
   return EXT_OK;
@@ -1470,7 +1635,7 @@ int ext_apply_biharmonic(ext_ctx* ctx, const ext_problem* prob, const float* phi
   timed(ctx, EXT_KERNEL_STENCIL, [&] { launch_stencil(sc, W->aniso, W->sten_ty, ctx->d_err); });
   BX_CUDA(cudaGetLastError());
   BX_CUDA(cudaMemcpyAsync(q, sl.d.q, 4 * N, cudaMemcpyDeviceToDevice, s));
-  std::vector<double> part((size_t)prob->ny * ((prob->nx + 31) / 32));
+  std::vector<double> part((size_t)((prob->ny + 15) / 16) * ((prob->nx + kStTileX - 1) / kStTileX));
   BX_CUDA(cudaMemcpyAsync(part.data(), sl.d.pq_part, 8 * part.size(), cudaMemcpyDeviceToHost, s));
   BX_CUDA(cudaMemcpyAsync(ctx->h_err, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   BX_CUDA(cudaStreamSynchronize(s));
@@ -1591,9 +1756,16 @@ static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
   cudaFree(W->d_gm);
   cudaFree(W->d_l1);
   cudaFree(W->d_l3);
+  cudaFree(W->d_fold);
+  cudaFree(W->d_unfold);
+  cudaFree(W->d_tcl);
   cudaFree(S->d_new);
   cudaFree(S->d_ret);
   W->d_st = W->d_sten = W->d_vec = W->d_gm = W->d_l1 = W->d_l3 = S->d_new = S->d_ret = nullptr;
+  W->d_fold = W->d_unfold = W->d_tcl = nullptr;
+  BX_CUDA(cudaMalloc(&W->d_fold, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_unfold, sizeof(WorkItem) * cap));
+  BX_CUDA(cudaMalloc(&W->d_tcl, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_st, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_sten, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_l1, sizeof(WorkItem) * cap));
@@ -1603,7 +1775,9 @@ static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
   BX_CUDA(cudaMalloc(&S->d_new, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&S->d_ret, sizeof(WorkItem) * cap));
   S->cap_items = cap;
-  W->n_st = W->n_vec = W->n_gm = W->n_sten = W->n_l1 = W->n_l3 = cap;  // grids sized for the capacity
+  // grids sized for the capacity
+  W->n_st = W->n_vec = W->n_gm = W->n_sten = W->n_l1 = W->n_l3 = cap;
+  W->n_fold = W->n_unfold = W->n_tcl = cap;
   if (W->graph) {
     cudaGraphExecDestroy(W->graph);
     W->graph = nullptr;
@@ -1620,12 +1794,13 @@ static int serve_init(ext_ctx* ctx) {
   W->slots.resize(cap);
   BX_CUDA(cudaStreamCreateWithFlags(&W->stream, cudaStreamNonBlocking));
   BX_CUDA(cudaMalloc(&W->d_slots, sizeof(SlotDesc) * cap));
+  BX_CUDA(cudaMalloc(&W->d_tcp, sizeof(SlotDesc) * kMirClasses * cap));
   BX_CUDA(cudaMalloc(&W->d_sc, sizeof(SlotScalars) * cap));
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * cap));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * cap));
   memset(W->h_sc, 0, sizeof(SlotScalars) * cap);
-  BX_CUDA(cudaMalloc(&W->d_counts, 7 * sizeof(int)));
-  BX_CUDA(cudaMemset(W->d_counts, 0, 7 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_counts, 10 * sizeof(int)));
+  BX_CUDA(cudaMemset(W->d_counts, 0, 10 * sizeof(int)));
   BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * cap));
   W->n_sl = cap;  // the per-slot grid is sized for the slot table
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * cap));
@@ -1648,26 +1823,31 @@ static int serve_init(ext_ctx* ctx) {
 static int serve_rebuild_lists(ext_ctx* ctx) {
   ext_ctx::Serve* S = ctx->serve;
   Workspace* W = S->W;
-  std::vector<WorkItem> st, vec, gm, sl, l1, l3;
+  std::vector<WorkItem> st, vec, gm, sl, l1, l3, fold, unfold, tcl;
   bool aniso = false;
   for (int i = 0; i < (int)S->slots.size(); ++i) {
     if (!S->slots[i].used) continue;
-    const SlotDesc& d = W->slots[i].d;
+    const SlotHost& h = W->slots[i];
+    const SlotDesc& d = h.d;
     aniso |= d.aniso != 0;
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
-    for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
-    if (d.lowm_x) {
-      for (int t = 0; t < d.n_l1_tiles; ++t) l1.push_back({i, t});
-      for (int t = 0; t < d.n_l3_tiles; ++t) l3.push_back({i, t});
+    if (ctx->tc) {
+      tc_items(h, i, gm, l1, l3, tcl);
+      for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
+      for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
+    } else {
+      for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
     }
     sl.push_back({i, 0});
   }
-  longest_first(gm, W->slots);
-  const int need = (int)std::max(std::max(st.size(), l3.size()), std::max(vec.size(), gm.size()));
-  if (need > S->cap_items) {
+  if (ctx->tc) longest_first_tc(gm, W->slots);
+  else longest_first(gm, W->slots);
+  size_t need = 0;
+  for (const auto* v : {&st, &vec, &gm, &l1, &l3, &fold, &unfold, &tcl}) need = std::max(need, v->size());
+  if ((int)need > S->cap_items) {
     int cap = S->cap_items;
-    while (cap < need) cap *= 2;
+    while (cap < (int)need) cap *= 2;
     BX_CUDA(cudaStreamSynchronize(W->stream));
     int rc = serve_alloc_lists(S, cap);
     if (rc) return rc;
@@ -1678,16 +1858,24 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
   }
   W->aniso = aniso;
   cudaStream_t s = W->stream;
-  if (!st.empty()) BX_CUDA(cudaMemcpyAsync(W->d_st, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice, s));
+  auto put = [&](WorkItem* dst, const std::vector<WorkItem>& v) -> int {
+    if (!v.empty()) BX_CUDA(cudaMemcpyAsync(dst, v.data(), sizeof(WorkItem) * v.size(), cudaMemcpyHostToDevice, s));
+    return EXT_OK;
+  };
+  int rc = put(W->d_st, st);
   // the serving table keeps the 64 x 32 stencil tiles: its stencil list is the grid-tile list
-  if (!st.empty()) BX_CUDA(cudaMemcpyAsync(W->d_sten, st.data(), sizeof(WorkItem) * st.size(), cudaMemcpyHostToDevice, s));
-  if (!vec.empty()) BX_CUDA(cudaMemcpyAsync(W->d_vec, vec.data(), sizeof(WorkItem) * vec.size(), cudaMemcpyHostToDevice, s));
-  if (!gm.empty()) BX_CUDA(cudaMemcpyAsync(W->d_gm, gm.data(), sizeof(WorkItem) * gm.size(), cudaMemcpyHostToDevice, s));
-  if (!sl.empty()) BX_CUDA(cudaMemcpyAsync(W->d_sl, sl.data(), sizeof(WorkItem) * sl.size(), cudaMemcpyHostToDevice, s));
-  if (!l1.empty()) BX_CUDA(cudaMemcpyAsync(W->d_l1, l1.data(), sizeof(WorkItem) * l1.size(), cudaMemcpyHostToDevice, s));
-  if (!l3.empty()) BX_CUDA(cudaMemcpyAsync(W->d_l3, l3.data(), sizeof(WorkItem) * l3.size(), cudaMemcpyHostToDevice, s));
-  int counts[7] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size(),
-                   (int)l1.size(), (int)l3.size()};
+  if (!rc) rc = put(W->d_sten, st);
+  if (!rc) rc = put(W->d_vec, vec);
+  if (!rc) rc = put(W->d_gm, gm);
+  if (!rc) rc = put(W->d_sl, sl);
+  if (!rc) rc = put(W->d_l1, l1);
+  if (!rc) rc = put(W->d_l3, l3);
+  if (!rc) rc = put(W->d_fold, fold);
+  if (!rc) rc = put(W->d_unfold, unfold);
+  if (!rc) rc = put(W->d_tcl, tcl);
+  if (rc) return rc;
+  int counts[10] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size(),
+                    (int)l1.size(), (int)l3.size(), (int)fold.size(), (int)unfold.size(), (int)tcl.size()};
   BX_CUDA(cudaMemcpyAsync(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
   // the host vectors die here: the copies above must finish first (pageable sources are staged)
   BX_CUDA(cudaStreamSynchronize(s));
@@ -1758,7 +1946,7 @@ static int serve_setup_slots(ext_ctx* ctx, const std::vector<int>& admitted) {
     }
     int rc = build_slot(ctx, r->prob, r->host_io, sl, arena);
     if (rc) return rc;
-    sl.d.sc = W->d_sc + i;
+    set_slot_scalars(sl, W->d_sc + i);
     const size_t N = (size_t)r->prob.nx * r->prob.ny;
     if (r->host_io) {
       BX_CUDA(cudaMemcpyAsync(sl.phi_stage, r->phi, 4 * N, cudaMemcpyHostToDevice, s));
@@ -1777,6 +1965,9 @@ static int serve_setup_slots(ext_ctx* ctx, const std::vector<int>& admitted) {
     BX_CUDA(cudaMemcpyAsync(W->d_outs + i, &h_outs[i], sizeof(void*), cudaMemcpyHostToDevice, s));
     BX_CUDA(cudaMemcpyAsync(W->d_dirs + i, &h_dirs[i], sizeof(int), cudaMemcpyHostToDevice, s));
     BX_CUDA(cudaMemcpyAsync(W->d_slots + i, &sl.d, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
+    if (ctx->tc)
+      BX_CUDA(cudaMemcpyAsync(W->d_tcp + kMirClasses * i, sl.tcp, sizeof(SlotDesc) * kMirClasses,
+                              cudaMemcpyHostToDevice, s));
     SlotScalars& sc = W->h_sc[i];
     memset(&sc, 0, sizeof(sc));
     sc.rtol2 = ctx->opt.rtol * ctx->opt.rtol;

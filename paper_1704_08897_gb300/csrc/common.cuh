@@ -124,7 +124,8 @@ struct SlotDesc {
   // (the smoothest, with the largest weights) are left out of the four 32-bit transform stages and
   // added from thin transforms with six slices per operand (about 48 bits).  0 = off.
   int lowm_x, lowm_y;
-  float* low_h;             // H = r Qx[:, :32]: [ny][32] hi plane, lo plane at + ny * 32
+  float* low_gp;            // per forward tile t its share of G = Qy_low^T (r Qx_low): [t][2][32][32]
+                            // (hi plane, then lo plane)
   void* low_jt;             // J^T slices [kLowNS][nxp][kLowK3] (16-bit codes), J = W o G Qx_low^T
   int8_t* low_jt_e;         // block exponent of each J^T row [nxp]
   float* low_z;             // zl = Qy_low J: [ny][nx] hi plane, lo plane at + nx * ny
@@ -135,10 +136,22 @@ struct SlotDesc {
   const void* low_maps;     // 4 CUtensorMap: r slices, Qx_low^T slices, J^T slices, Qy_low slices
   int n_l1_tiles;           // tiles of the forward product: nyp / 128
   int n_l3_tiles;           // items of the inverse product: nxp / 128 (each walks every y-tile)
+  // Mirror fold of the tensor-core transforms (i -> n-1-i on an axis; even and odd classes of
+  // ceil(n/2) nodes each): a slot with a folded axis runs its four stages as two or four
+  // half-size problems, the slot's classes, held in the tensor-core problem list at
+  // kMirClasses * slot + c, c = 2 cls_y + cls_x.
+  int mir;           // slot: bit 0 = x folded, bit 1 = y folded (0: the slot is its own problem)
+  int mhx, mhy;      // slot: class nodes along x, y (ceil(n/2) on a folded axis, else n)
+  int n_fold_items;  // slot: items of the fold kernel (8 class rows x 128 columns)
+  int n_unfold_tiles;// slot: tiles of the unfold kernel (32 x 8 class nodes)
+  int n_prec_parts;  // slot: r.z, z.q partials the preconditioner leaves (stage-3 or unfold tiles)
+  int mir_out;       // class problem: stage 3 writes the class result g to z, z_lo ([ny][nx])
   SlotScalars* sc;
   double* part;      // per-work-item partial sums (2 doubles per item), slot-local indexing
-  double* pq_part;   // p.q partial sums of the stencil, one per 32-node row segment [ny][nx/32]
+  double* pq_part;   // p.q partial sums of the stencil, one per 64 x 16 block [ny/16][nx/64]
 };
+
+constexpr int kMirClasses = 4;  // tensor-core problem entries per slot
 
 struct WorkItem {
   int slot;

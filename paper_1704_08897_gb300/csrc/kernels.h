@@ -10,6 +10,7 @@ namespace bx {
 
 struct LaunchCfg {
   const SlotDesc* slots;   // device array of slot descriptors
+  const SlotDesc* tcp = nullptr;  // tensor-core problems (kMirClasses per slot), mixed modes
   const WorkItem* items;   // device work list
   const int* n_items;      // device count of valid items (persistent kernels read it)
   int grid;
@@ -60,6 +61,10 @@ int tc_planes(int split_kind);
 // 128 rows of y), kind 1 = inverse product (tiles of 128 x 32); the middle step one block per slot
 void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* err);
 void launch_low_mid(const LaunchCfg& c, int mode, int split_kind);
+// mirror fold: residual -> slices of each class's first operand (c.slots = slots, items of the
+// folded slots), and class results -> masked z with the r.z, z.q partials
+void launch_tc_fold(const LaunchCfg& c, int mode, int split_kind);
+void launch_unfold(const LaunchCfg& c, int mode);
 int tc_block();
 bool tc_supported();
 // opt the tensor-core kernels into their dynamic shared memory (once per process and device)

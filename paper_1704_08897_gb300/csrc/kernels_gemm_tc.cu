@@ -407,7 +407,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       const int m = m0 + row;
       const int ncol0 = n0 + group * kEpiCols;
       const int kblocks = v.K / KC;
-      if (STAGE == 3 && col_lane) {
+      if (STAGE == 3 && col_lane && !S.mir_out) {
         // the r, q and mask entries read after the last k-block: start them towards L2 now
         const int n = ncol0 + lane;
         const int mr = min(m0 + 32 * quarter, S.nx - 1);
@@ -564,6 +564,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               static_cast<int8_t>(E_mine);
       } else {
         CompDotDF c_rz, c_zq;
+        const bool with_zq = S.mir_out == 0 && (sc->flexible != 0 || mode == 2);
         if (m < S.nx) {
           constexpr int kGrp = 8;
           static_assert(kEpiCols % kGrp == 0, "stage-3 load groups");
@@ -587,6 +588,19 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
                 vlo[g8 + i] = zsum.lo;
               }
             }
+            if (S.mir_out) {
+              // one mirror class of a folded slot: its result g, unmasked (k_unfold combines the
+              // classes, masks and forms the dot products)
+#pragma unroll
+              for (int i = 0; i < kGrp; ++i) {
+                const int n = ncol0 + g8 + i;
+                if (n < S.ny) {
+                  S.z[n * S.nx + m] = val[g8 + i];
+                  S.z_lo[n * S.nx + m] = vlo[g8 + i];
+                }
+              }
+              continue;
+            }
             float rv[kGrp], rl[kGrp], qv[kGrp], ql[kGrp];
             uint8_t mk[kGrp];
 #pragma unroll
@@ -595,8 +609,9 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
               const int g = (n < S.ny ? n : 0) * S.nx + m;
               rv[i] = S.r[g];
               rl[i] = S.r_lo[g];
-              qv[i] = S.q[g];
-              ql[i] = S.q_lo[g];
+              // z.q enters only the flexible beta
+              qv[i] = with_zq ? S.q[g] : 0.f;
+              ql[i] = with_zq ? S.q_lo[g] : 0.f;
               mk[i] = n < S.ny ? S.mask[g] : 0;
             }
 #pragma unroll
@@ -613,6 +628,7 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             }
           }
         }
+        if (S.mir_out) continue;  // a class problem leaves no partial sums
         // tile partials of r.z and z.q (FP32-compensated inside the warp)
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -684,7 +700,7 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     const WorkItem it = items[w];
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
-    if (!slot_runs(sc, mode)) continue;
+    if (!slot_runs(sc, mode) || S.mir) continue;  // folded slots: k_tc_fold
     const int tx = (S.nx + kStTileX - 1) / kStTileX;
     const int x0 = (it.tile % tx) * kStTileX;
     const int y0 = (it.tile / tx) * kStTileY;
@@ -725,15 +741,225 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
       const float s = pow2f(8 - E), is = pow2f(E - 8);
 #pragma unroll
       for (int k = 0; k < kPairs; ++k) {
-        // six slices: the first four are stage 0's operand, all six the low-mode product's
-        uint32_t code[kLowNS];
-        slice_codes2_df<BF16, kLowNS>(v[j][k], vl[j][k], make_float2(s, s), make_float2(is, is), code);
         const size_t idx = (static_cast<size_t>(y) * S.nxp + x0 + 64 * k + 2 * lane) / 2;
-        const int nsl = S.lowm_x ? kLowNS : NS;
-        for (int q = 0; q < nsl; ++q) out32[q * (plane / 2) + idx] = code[q];
+        if (S.lowm_x) {
+          // six slices: the first four are stage 0's operand, all six the low-mode product's
+          uint32_t code[kLowNS];
+          slice_codes2_df<BF16, kLowNS>(v[j][k], vl[j][k], make_float2(s, s), make_float2(is, is), code);
+#pragma unroll
+          for (int q = 0; q < kLowNS; ++q) out32[q * (plane / 2) + idx] = code[q];
+        } else {
+          uint32_t code[NS];
+          slice_codes2_df<BF16, NS>(v[j][k], vl[j][k], make_float2(s, s), make_float2(is, is), code);
+#pragma unroll
+          for (int q = 0; q < NS; ++q) out32[q * (plane / 2) + idx] = code[q];
+        }
       }
       if (lane == 0) S.tc_e[0][static_cast<size_t>(y) * kblocks + x0 / KC] = static_cast<int8_t>(E);
     }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Mirror fold (slots with a folded axis).  On a folded axis the basis splits into even and odd
+// vectors under i -> n-1-i (plan.cpp), so the four stages of the slot run as two or four
+// independent half-size problems, its classes.  k_tc_fold forms each class's residual on its
+// ceil(n/2)-node domain, signed sums of r at a node and its mirrors (the even class adds, the
+// odd class subtracts; a middle node, its own mirror, counts once in the even class and not in
+// the odd one), in double-float, and slices it like k_tc_prepare.  After stage 3 has written
+// each class's result g, k_unfold forms z at a node and its mirrors as the sums of the classes
+// with the odd ones' signs flipped on the mirrored side, masks it and leaves the r.z and z.q
+// partials that stage 3 leaves for an unfolded slot.
+// ---------------------------------------------------------------------------------------------
+__device__ __forceinline__ f2 df_neg(f2 a) { return f2{-a.hi, -a.lo}; }
+
+// One warp per (class row y, 128 class columns); lane pairs (x, x+1) at x = 64 k + 2 lane.
+template <bool BF16>
+__global__ void __launch_bounds__(256)
+k_tc_fold(const SlotDesc* __restrict__ slots, const SlotDesc* __restrict__ tcp,
+          const WorkItem* __restrict__ items, const int* __restrict__ n_items, int mode) {
+  const int total = *n_items;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    if (!slot_runs(S.sc, mode)) continue;
+    const bool fx = (S.mir & 1) != 0, fy = (S.mir & 2) != 0;
+    const int nxb = (S.mhx + KC - 1) / KC;
+    const int y = (it.tile / nxb) * 8 + warp, xb = it.tile % nxb;
+    if (y >= S.mhy) continue;
+    const int yy = fy ? S.ny - 1 - y : y;  // the mirrored row (y itself on an unfolded axis)
+    const bool ymid = yy == y;
+    const float* rh = S.r;
+    const float* rl = S.r_lo;
+    // class values of the lane's four columns: hi and lo planes of pair k's columns (x, x+1)
+    float2 ch[4][2], cl[4][2];  // [class][pair]
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      f2 v[4][2];  // [class][column of the pair]
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int x = xb * KC + 64 * k + 2 * lane + e;
+        f2 a{0.f, 0.f}, b{0.f, 0.f}, c{0.f, 0.f}, d{0.f, 0.f};
+        const int xx = fx ? S.nx - 1 - x : x;
+        const bool xmid = xx == x;
+        if (x < S.mhx) {
+          const size_t gy = static_cast<size_t>(y) * S.nx, gyy = static_cast<size_t>(yy) * S.nx;
+          a = f2{rh[gy + x], rl[gy + x]};
+          if (!xmid) b = f2{rh[gy + xx], rl[gy + xx]};
+          if (!ymid) {
+            c = f2{rh[gyy + x], rl[gyy + x]};
+            if (!xmid) d = f2{rh[gyy + xx], rl[gyy + xx]};
+          }
+        }
+        // along x: even = a + b, odd = a - b (b = 0 at a middle node or on an unfolded axis)
+        const f2 e0 = df_add(a, b), o0 = df_add(a, df_neg(b));
+        const f2 e1 = df_add(c, d), o1 = df_add(c, df_neg(d));
+        // along y the same with the mirrored row; class c = 2 cls_y + cls_x
+        v[0][e] = df_add(e0, e1);
+        v[1][e] = df_add(o0, o1);
+        v[2][e] = df_add(e0, df_neg(e1));
+        v[3][e] = df_add(o0, df_neg(o1));
+        if (xmid && fx) {  // the odd x classes vanish at the middle column
+          v[1][e] = f2{0.f, 0.f};
+          v[3][e] = f2{0.f, 0.f};
+        }
+        if (ymid && fy) {
+          v[2][e] = f2{0.f, 0.f};
+          v[3][e] = f2{0.f, 0.f};
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        ch[c][k] = make_float2(v[c][0].hi, v[c][1].hi);
+        cl[c][k] = make_float2(v[c][0].lo, v[c][1].lo);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      if ((c & 1) && !fx) continue;
+      if ((c & 2) && !fy) continue;
+      const SlotDesc& T = tcp[kMirClasses * it.slot + c];
+      float amax = 0.f;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) amax = fmaxf(amax, fmaxf(fabsf(ch[c][k].x), fabsf(ch[c][k].y)));
+      const int E = block_exp(warp_max(amax));
+      const float up = pow2f(8 - E), is = pow2f(E - 8);
+      const size_t plane = static_cast<size_t>(T.nyp) * T.nxp;
+      uint32_t* out32 = static_cast<uint32_t*>(T.tc_r);
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        const size_t idx = (static_cast<size_t>(y) * T.nxp + xb * KC + 64 * k + 2 * lane) / 2;
+        if (T.lowm_x) {
+          uint32_t code[kLowNS];
+          slice_codes2_df<BF16, kLowNS>(ch[c][k], cl[c][k], make_float2(up, up), make_float2(is, is), code);
+#pragma unroll
+          for (int q = 0; q < kLowNS; ++q) out32[q * (plane / 2) + idx] = code[q];
+        } else {
+          uint32_t code[NS];
+          slice_codes2_df<BF16, NS>(ch[c][k], cl[c][k], make_float2(up, up), make_float2(is, is), code);
+#pragma unroll
+          for (int q = 0; q < NS; ++q) out32[q * (plane / 2) + idx] = code[q];
+        }
+      }
+      if (lane == 0) T.tc_e[0][static_cast<size_t>(y) * (T.nxp / KC) + xb] = static_cast<int8_t>(E);
+    }
+  }
+}
+
+// One thread per class node (tiles of 32 x 8): z at the node and its mirrors, masked, with the
+// tile's compensated r.z and z.q partials.
+__global__ void __launch_bounds__(256)
+k_unfold(const SlotDesc* __restrict__ slots, const SlotDesc* __restrict__ tcp,
+         const WorkItem* __restrict__ items, const int* __restrict__ n_items, int mode) {
+  __shared__ float red[8][4];
+  const int total = *n_items;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    if (!slot_runs(S.sc, mode)) continue;
+    const bool fx = (S.mir & 1) != 0, fy = (S.mir & 2) != 0;
+    const int ntx = (S.mhx + 31) >> 5;
+    const int x = (it.tile % ntx) * 32 + lane, y = (it.tile / ntx) * 8 + warp;
+    CompDotDF c_rz, c_zq;
+    const bool with_zq = S.sc->flexible != 0 || mode == 2;  // z.q enters only the flexible beta
+    if (x < S.mhx && y < S.mhy) {
+      const int xx = fx ? S.nx - 1 - x : x, yy = fy ? S.ny - 1 - y : y;
+      // every load first: the classes' g at (y, x), then mask, r (and q) at the mirror nodes
+      f2 g[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        g[c] = f2{0.f, 0.f};
+        if (((c & 1) && !fx) || ((c & 2) && !fy)) continue;
+        const SlotDesc& T = tcp[kMirClasses * it.slot + c];
+        const int gi = y * T.nx + x;
+        g[c] = f2{T.z[gi], T.z_lo[gi]};
+      }
+      int gi[4];
+      bool live[4];
+      uint8_t mk[4];
+      float rh[4], rl[4], qh[4], ql[4];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {  // t = 2 (mirrored row) + (mirrored column)
+        live[t] = !((t & 1) && xx == x) && !((t & 2) && yy == y);
+        gi[t] = ((t & 2) ? yy : y) * S.nx + ((t & 1) ? xx : x);
+        mk[t] = 0;
+        rh[t] = rl[t] = qh[t] = ql[t] = 0.f;
+        if (live[t]) {
+          mk[t] = S.mask[gi[t]];
+          rh[t] = S.r[gi[t]];
+          rl[t] = S.r_lo[gi[t]];
+          if (with_zq) {
+            qh[t] = S.q[gi[t]];
+            ql[t] = S.q_lo[gi[t]];
+          }
+        }
+      }
+      // even/odd butterflies along x, then y
+      const f2 a = df_add(g[0], g[1]), b = df_add(g[0], df_neg(g[1]));
+      const f2 c = df_add(g[2], g[3]), d = df_add(g[2], df_neg(g[3]));
+      const f2 v[4] = {df_add(a, c), df_add(b, d), df_add(a, df_neg(c)), df_add(b, df_neg(d))};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        if (!live[t]) continue;
+        const float zh = mk[t] ? v[t].hi : 0.f, zl = mk[t] ? v[t].lo : 0.f;
+        S.z[gi[t]] = zh;
+        S.z_lo[gi[t]] = zl;
+        c_rz.add(rh[t], rl[t], zh, zl);
+        if (with_zq) c_zq.add(zh, zl, qh[t], ql[t]);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      float e;
+      const float a1 = __shfl_xor_sync(0xffffffffu, c_rz.s, o), a2 = __shfl_xor_sync(0xffffffffu, c_rz.c, o);
+      two_sum(c_rz.s, a1, c_rz.s, e);
+      c_rz.c = __fadd_rn(c_rz.c, __fadd_rn(a2, e));
+      const float b1 = __shfl_xor_sync(0xffffffffu, c_zq.s, o), b2 = __shfl_xor_sync(0xffffffffu, c_zq.c, o);
+      two_sum(c_zq.s, b1, c_zq.s, e);
+      c_zq.c = __fadd_rn(c_zq.c, __fadd_rn(b2, e));
+    }
+    if (lane == 0) {
+      red[warp][0] = c_rz.s;
+      red[warp][1] = c_rz.c;
+      red[warp][2] = c_zq.s;
+      red[warp][3] = c_zq.c;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      CompDot t_rz, t_zq;
+      for (int k = 0; k < 8; ++k) {  // the warps in order
+        float e;
+        two_sum(t_rz.s, red[k][0], t_rz.s, e);
+        t_rz.c = __fadd_rn(t_rz.c, __fadd_rn(red[k][1], e));
+        two_sum(t_zq.s, red[k][2], t_zq.s, e);
+        t_zq.c = __fadd_rn(t_zq.c, __fadd_rn(red[k][3], e));
+      }
+      S.part[it.tile * 4 + 2] = t_rz.value();
+      S.part[it.tile * 4 + 3] = t_zq.value();
+    }
+    __syncthreads();
   }
 }
 
@@ -766,6 +992,8 @@ constexpr int kLowTmemCols = 256;            // >= kLowNS * LBN
 constexpr int kLowSmem = kLowNS * (LA_PLANE + LB_PLANE) + 1024 + 256;
 static_assert(kLowNS * LBN <= kLowTmemCols, "low-mode TMEM columns");
 static_assert(kLowK3 == LBK, "the inverse product's k fits one copy");
+static_assert(kLowThreads == 16 * 32 && 2 * BM * 33 * 4 + 2 * BM * kLowM * 4 <= kLowNS * (LA_PLANE + LB_PLANE),
+              "the G stage: sixteen warps (ky = warp, warp + 16) and its staging in the operand buffers");
 
 struct LowCtl {
   uint64_t full, done;
@@ -908,15 +1136,18 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
                                  : S.low_qy_e[min(n0 + cc, S.nyp - 1)];
         scl[c] = pow2f(ea - 16) * pow2f(eb);
       }
+      // the six order sums of the warp's columns, loaded together
+      uint32_t v[kLowNS][kLowCols];
+#pragma unroll
+      for (int d = 0; d < kLowNS; ++d)
+        tmem_ld8(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + d * LBN + cg * kLowCols, v[d]);
+      tmem_wait_ld();
 #pragma unroll
       for (int d = 0; d < kLowNS; ++d) {
         const float od = pow2f(-8 * d);
-        uint32_t v[kLowCols];
-        tmem_ld8(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + d * LBN + cg * kLowCols, v);
-        tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < kLowCols; ++c) {
-          const float t = __uint_as_float(v[c]) * scl[c] * od;
+          const float t = __uint_as_float(v[d][c]) * scl[c] * od;
           if (d <= 2) {
             float e;
             two_sum(hi[c], t, hi[c], e);
@@ -930,18 +1161,39 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       __syncthreads();  // the next block's MMAs overwrite the accumulators
     }
     if (failed) break;
-    // the tile's double-float results
     if (KIND == 0) {
-      if (m < S.ny) {
-        float* hh = S.low_h + static_cast<size_t>(m) * kLowM + cg * kLowCols;
-        float* hl = S.low_h + static_cast<size_t>(S.ny) * kLowM + static_cast<size_t>(m) * kLowM + cg * kLowCols;
+      // the tile's share of G = Qy_low^T H (its 128 rows of y), by compensated dot products of
+      // double-float operands staged in shared memory (the operand buffers are free: the last
+      // MMAs completed before the block's TMEM reads); H itself is not stored
+      float* hs = reinterpret_cast<float*>(smem);  // H tile [128][33]: hi, then lo
+      float* ys = hs + 2 * BM * 33;                 // Qy_low rows m0 .. m0+127 [128][32]: hi, lo
 #pragma unroll
-        for (int c = 0; c < kLowCols; ++c) {
-          const f2 v = df_norm(hi[c], lo[c]);
-          hh[c] = v.hi;
-          hl[c] = v.lo;
-        }
+      for (int c = 0; c < kLowCols; ++c) {
+        const f2 hv = df_norm(hi[c], lo[c]);
+        hs[row * 33 + cg * kLowCols + c] = hv.hi;
+        hs[BM * 33 + row * 33 + cg * kLowCols + c] = hv.lo;
       }
+      for (int e = threadIdx.x; e < BM * kLowM; e += kLowThreads) {
+        const size_t a = static_cast<size_t>(m0) * kLowM + e;
+        ys[e] = S.low_qyd[a];
+        ys[BM * kLowM + e] = S.low_qyd[static_cast<size_t>(S.nyp) * kLowM + a];
+      }
+      __syncthreads();
+      // thread: kx = lane, ky = warp and warp + 16
+      CompDotDF g0, g1;
+#pragma unroll 4
+      for (int rr = 0; rr < BM; ++rr) {
+        const float bh = hs[rr * 33 + lane], bl = hs[BM * 33 + rr * 33 + lane];
+        g0.add(ys[rr * kLowM + warp], ys[BM * kLowM + rr * kLowM + warp], bh, bl);
+        g1.add(ys[rr * kLowM + warp + 16], ys[BM * kLowM + rr * kLowM + warp + 16], bh, bl);
+      }
+      float* gp = S.low_gp + static_cast<size_t>(it.tile) * 2 * kLowM * kLowM;
+      const f2 a0 = df_norm(g0.s, g0.c), a1 = df_norm(g1.s, g1.c);
+      gp[warp * kLowM + lane] = a0.hi;
+      gp[kLowM * kLowM + warp * kLowM + lane] = a0.lo;
+      gp[(warp + 16) * kLowM + lane] = a1.hi;
+      gp[kLowM * kLowM + (warp + 16) * kLowM + lane] = a1.lo;
+      __syncthreads();  // the next item's tensor copies overwrite the staging
     } else {
       const size_t nn = static_cast<size_t>(S.nx) * S.ny;
       if (m < S.nx) {
@@ -1116,16 +1368,18 @@ k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         lo[c] = 0.f;
         scl[c] = sa * pow2f(S.low_qy_e[n0 + c]);
       }
+      uint32_t v[kLowNS][kLowInvCols];  // the six order sums, loaded together
+#pragma unroll
+      for (int d = 0; d < kLowNS; ++d)
+        tmem_ld8(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + b * 256 + d * LBN +
+                     cg * kLowInvCols, v[d]);
+      tmem_wait_ld();
 #pragma unroll
       for (int d = 0; d < kLowNS; ++d) {
         const float od = pow2f(-8 * d);
-        uint32_t v[kLowInvCols];
-        tmem_ld8(tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) + b * 256 + d * LBN +
-                     cg * kLowInvCols, v);
-        tmem_wait_ld();
 #pragma unroll
         for (int c = 0; c < kLowInvCols; ++c) {
-          const float t = __uint_as_float(v[c]) * scl[c] * od;
+          const float t = __uint_as_float(v[d][c]) * scl[c] * od;
           if (d <= 2) {
             float e;
             two_sum(hi[c], t, hi[c], e);
@@ -1182,56 +1436,31 @@ __device__ __forceinline__ void slice_codes_df(float vh, float vl, float s, floa
   for (int k = 0; k < kLowNS; ++k) code[k] = static_cast<uint16_t>(c2[k] & 0xffffu);
 }
 
-// Middle of the low-mode correction, one block per slot: G = Qy_low^T H and J = (w o G) Qx_low^T
-// by compensated dot products of double-float operands (Ogita-Rump-Oishi), then J^T cut into six
-// slices per row with its block exponent (the inverse product's A operand).  G's k sum runs over
-// 32-row chunks of H and Qy_low staged in shared memory; J's row of Qx_low is broadcast across
-// the warp by shuffles, so neither loop waits on global memory per term.
+// Middle of the low-mode correction, one block per (problem, 128 rows of x) (the inverse
+// product's items): G = the forward tiles' shares summed in tile order, G' = w o G, and the
+// block's rows of J^T, J^T[x][ky] = sum_kx G'[ky][kx] Qx[x][kx], by compensated dot products of
+// double-float operands (Ogita-Rump-Oishi), each row then cut into six slices with its block
+// exponent (the inverse product's A operand).  Qx's row is broadcast across the warp by shuffles.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int mode) {
   __shared__ float gh[kLowM][kLowM + 1], gl[kLowM][kLowM + 1];
-  __shared__ float hh[32][kLowM], hl[32][kLowM], yh[32][kLowM], yl[32][kLowM];
   const int total = *n_items;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
     const WorkItem it = items[w];
-    if (it.tile != 0) continue;
     const SlotDesc& S = slots[it.slot];
     if (!slot_runs(S.sc, mode) || S.lowm_x == 0) continue;
-    const float* qy_h = S.low_qyd;
-    const float* qy_l = S.low_qyd + static_cast<size_t>(S.nyp) * kLowM;
     const float* qx_h = S.low_qxd;
     const float* qx_l = S.low_qxd + static_cast<size_t>(S.nxp) * kLowM;
-    const float* h_h = S.low_h;
-    const float* h_l = S.low_h + static_cast<size_t>(S.ny) * kLowM;
-    // G[ky][kx]: thread t owns kx = lane and ky = warp + 8 r, r = 0..3
-    CompDotDF acc[kLowM / 8];
-    for (int y0 = 0; y0 < S.ny; y0 += 32) {
-      // stage rows y0 .. y0+31 of H and Qy_low (zeros beyond ny)
-      for (int e = t; e < 32 * kLowM; e += 256) {
-        const int yy = e / kLowM, c = e - yy * kLowM, y = y0 + yy;
-        const bool in = y < S.ny;
-        const size_t a = static_cast<size_t>(y) * kLowM + c;
-        hh[yy][c] = in ? h_h[a] : 0.f;
-        hl[yy][c] = in ? h_l[a] : 0.f;
-        yh[yy][c] = in ? qy_h[a] : 0.f;
-        yl[yy][c] = in ? qy_l[a] : 0.f;
+    for (int e = t; e < kLowM * kLowM; e += 256) {
+      f2 g{0.f, 0.f};
+      for (int tt = 0; tt < S.n_l1_tiles; ++tt) {
+        const float* gp = S.low_gp + static_cast<size_t>(tt) * 2 * kLowM * kLowM;
+        g = df_add(g, f2{gp[e], gp[kLowM * kLowM + e]});
       }
-      __syncthreads();
-#pragma unroll 4
-      for (int yy = 0; yy < 32; ++yy) {
-        const float bh = hh[yy][lane], bl = hl[yy][lane];
-#pragma unroll
-        for (int r = 0; r < kLowM / 8; ++r) acc[r].add(yh[yy][warp + 8 * r], yl[yy][warp + 8 * r], bh, bl);
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < kLowM / 8; ++r) {
-      const int ky = warp + 8 * r, kx = lane;
-      f2 g = df_norm(acc[r].s, acc[r].c);
+      const int ky = e / kLowM, kx = e - ky * kLowM;
       const float sw = S.lamy[min(ky, S.nyp - 1)] + S.lamx[min(kx, S.nxp - 1)];
       const bool ok = ky < S.lowm_y && kx < S.lowm_x && sw > 0.f;
       g = ok ? df_mul(g, spectral_weight_of(S.wnorm, sw)) : f2{0.f, 0.f};
@@ -1239,7 +1468,6 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       gl[ky][kx] = g.lo;
     }
     __syncthreads();
-    // J^T rows x (one warp per row, lane = ky), sliced for the inverse product
     uint16_t* jt = static_cast<uint16_t*>(S.low_jt);
     const size_t plane = static_cast<size_t>(S.nxp) * kLowK3;
     float gr_h[kLowM], gr_l[kLowM];  // the lane's row ky of G'
@@ -1248,9 +1476,10 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       gr_h[kx] = gh[lane][kx];
       gr_l[kx] = gl[lane][kx];
     }
-    // four rows of J^T per warp at a time: four independent dot-product chains per lane
+    // the warp's 16 rows of the block, four at a time: four independent dot-product chains
     constexpr int kRowsPerWarp = 4;
-    for (int x0 = warp * kRowsPerWarp; x0 < S.nxp; x0 += 8 * kRowsPerWarp) {
+    const int xw = it.tile * BM + warp * (BM / 8);
+    for (int x0 = xw; x0 < xw + BM / 8; x0 += kRowsPerWarp) {
       float qh[kRowsPerWarp], ql[kRowsPerWarp];
 #pragma unroll
       for (int r = 0; r < kRowsPerWarp; ++r) {
@@ -1281,7 +1510,7 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         if (lane == 0) S.low_jt_e[x] = static_cast<int8_t>(E);
       }
     }
-    __syncthreads();
+    __syncthreads();  // gh, gl are rewritten by the next item
   }
 }
 
@@ -1358,6 +1587,15 @@ void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* 
 void launch_low_mid(const LaunchCfg& c, int mode, int split_kind) {
   if (split_kind == 0) k_low_mid<false><<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
   else k_low_mid<true><<<c.grid, 256, 0, c.stream>>>(c.slots, c.items, c.n_items, mode);
+}
+
+void launch_tc_fold(const LaunchCfg& c, int mode, int split_kind) {
+  if (split_kind == 0) k_tc_fold<false><<<c.grid, 256, 0, c.stream>>>(c.slots, c.tcp, c.items, c.n_items, mode);
+  else k_tc_fold<true><<<c.grid, 256, 0, c.stream>>>(c.slots, c.tcp, c.items, c.n_items, mode);
+}
+
+void launch_unfold(const LaunchCfg& c, int mode) {
+  k_unfold<<<c.grid, 256, 0, c.stream>>>(c.slots, c.tcp, c.items, c.n_items, mode);
 }
 
 void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int* err) {

@@ -276,7 +276,7 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
 // ---------------------------------------------------------------------------------------------
 // Iteration, stage 1: p = z + beta p_old (formed in shared memory including the halo, in
 // double-float), q = M L^2 p (Algorithm 1, matvec, with the mask in the epilogue), and p.q as
-// partial sums over fixed 32-node row segments; k_pq_finish then forms alpha = rho / p.q.
+// partial sums over fixed 64 x 16 node blocks; k_pq_finish then forms alpha = rho / p.q.
 //
 // q is the double-float pair of the exact 13-point sum of p's hi plane (compensated FP32) plus
 // the same stencil of p's lo plane in plain FP32.
@@ -291,9 +291,11 @@ k_rhs_scale(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
 // (reflected, wrapped or negated copies of grid nodes under the boundary rule) are gathered by
 // plain loads.  Tiles of other slots fill the free window set with plain loads.
 //
-// The p.q partials do not depend on TY: each 32-node row segment is summed by one half warp
-// (isotropic kernel, two nodes per lane) or one warp (anisotropic kernel) in a fixed butterfly,
-// and k_pq_finish adds the segments in index order, so every tile height gives the same bits.
+// The p.q partials do not depend on TY: they are per 64 x 16 block (a tile holds TY / 16 of
+// them), each thread adds its nodes of a block in step order (the steps cover the block's rows
+// in the same order for either TY), the warp adds its lanes in a fixed butterfly and one thread
+// the eight warps in order; k_pq_finish adds the blocks in index order, so every tile height
+// gives the same bits.
 // ---------------------------------------------------------------------------------------------
 constexpr int kWX = kStWinX;  // 72: window row, floats
 static_assert(kStWinX == kStTileX + 8, "window columns");
@@ -416,6 +418,7 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       (reinterpret_cast<uintptr_t>(st_smem_raw) + 127) & ~static_cast<uintptr_t>(127));
   __shared__ __align__(8) uint64_t full[2];
   __shared__ int s_abort;
+  __shared__ double blk_sm[TY / 16][kStThreads / 32];  // p.q of each warp in each 16-row block
   const int total = *n_items;
   const int lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -553,16 +556,19 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     const uint8_t* mt = buf + 4 * G::kWinBytes;
     float* __restrict__ qh = S.q;
     float* __restrict__ ql = S.q_lo;
-    const int nseg = (S.nx + 31) >> 5;  // 32-node row segments per grid row
+    const int nbx = (S.nx + kStTileX - 1) / kStTileX;  // 64-node blocks per grid row
+    // p.q of the tile's 64 x 16 blocks: each thread sums its nodes of one block in step order, the
+    // warp its lanes in a fixed butterfly, and one thread the eight warps in order
+    CompDotDF dot;
     if (!ANISO) {
       // node pairs (x, x+1): the window's row stride is even and x - x0 is even.  In step j the
-      // warp covers one tile row; lanes 0-15 its first 32 nodes, lanes 16-31 the next 32.
+      // warp covers one tile row; lanes 0-15 its first 32 nodes, lanes 16-31 the next 32.  Two
+      // steps (eight rows each) make a 16-row block.
 #pragma unroll 1
       for (int j = 0; j < G::kOwn / 2; ++j) {
         const int k = threadIdx.x + j * kStThreads;
         const int ly = k / (kStTileX / 2), lx = 2 * (k - ly * (kStTileX / 2));
         const int gx = x0 + lx, gy = y0 + ly;
-        CompDotDF dot;
         if (gx < S.nx && gy < S.ny) {
           const int g = gy * S.nx + gx;
           const int wc = (ly + 2) * kWX + lx + 4;
@@ -602,19 +608,20 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
             ql[g] = q0.lo;
           }
         }
-        // the half warp's row segment: every lane joins the butterfly
-        const double seg = group_sum_comp<16>(dot.s, dot.c);
-        const int sx = (x0 + (lane & 16) * 2) >> 5;
-        if ((lane & 15) == 0 && gy < S.ny && sx < nseg) S.pq_part[gy * nseg + sx] = seg;
+        if (j & 1) {  // the end of a 16-row block: every lane joins the butterfly
+          const double blk = group_sum_comp<32>(dot.s, dot.c);
+          if (lane == 0) blk_sm[j >> 1][threadIdx.x >> 5] = blk;
+          dot = CompDotDF{};
+        }
       }
     } else {
-      // one node per lane; in step j the warp covers 32 consecutive nodes of one tile row
+      // one node per lane; in step j the warp covers 32 consecutive nodes of one tile row; four
+      // steps (four rows each) make a 16-row block
 #pragma unroll 1
       for (int j = 0; j < G::kOwn; ++j) {
         const int k = threadIdx.x + j * kStThreads;
         const int ly = k / kStTileX, lx = k - ly * kStTileX;
         const int gx = x0 + lx, gy = y0 + ly;
-        CompDotDF dot;
         if (gx < S.nx && gy < S.ny) {
           const int g = gy * S.nx + gx;
           const float pvh = wh[(ly + 2) * kWX + lx + 4], pvl = wl[(ly + 2) * kWX + lx + 4];
@@ -630,10 +637,21 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
           ql[g] = qv.lo;
           dot.add(pvh, pvl, qv.hi, qv.lo);
         }
-        const double seg = group_sum_comp<32>(dot.s, dot.c);
-        const int sx = (x0 + (lx & ~31)) >> 5;
-        if (lane == 0 && gy < S.ny && sx < nseg) S.pq_part[gy * nseg + sx] = seg;
+        if ((j & 3) == 3) {
+          const double blk = group_sum_comp<32>(dot.s, dot.c);
+          if (lane == 0) blk_sm[j >> 2][threadIdx.x >> 5] = blk;
+          dot = CompDotDF{};
+        }
       }
+    }
+    __syncthreads();
+    // the 16-row blocks of the tile (TY / 16 of them, so the partials do not depend on TY)
+    if (threadIdx.x < TY / 16) {
+      const int by = (y0 >> 4) + threadIdx.x;
+      double acc = 0.0;
+#pragma unroll
+      for (int w = 0; w < kStThreads / 32; ++w) acc += blk_sm[threadIdx.x][w];
+      if (16 * by < S.ny) S.pq_part[by * nbx + x0 / kStTileX] = acc;
     }
     __syncthreads();  // the window set is free for the copies started at the next copied tile
   }
@@ -649,7 +667,7 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
 }
 
 // One block per slot (the slot's tile-0 item of the per-slot list): p.q from the stencil's
-// row-segment partials in a fixed order, alpha = rho / p.q, breakdown detection.
+// block partials (64 x 16 nodes) in a fixed order, alpha = rho / p.q, breakdown detection.
 __global__ void __launch_bounds__(256)
 k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
             const int* __restrict__ n_items) {
@@ -662,7 +680,7 @@ k_pq_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
     SlotScalars* sc = S.sc;
     if (!sc->active) continue;
     double a = 0.0, b = 0.0;
-    const int nparts = S.ny * ((S.nx + 31) >> 5);
+    const int nparts = ((S.ny + 15) >> 4) * ((S.nx + kStTileX - 1) / kStTileX);
     for (int t = threadIdx.x; t < nparts; t += blockDim.x) a += __ldcg(&S.pq_part[t]);
     block_sum2<256>(a, b, red);
     if (threadIdx.x == 0) {
@@ -876,7 +894,7 @@ k_prec_finish(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ i
     const int run = mode == 0 ? sc->active : (mode == 1 ? sc->need_prec : 1);
     if (!run) continue;
     double a = 0.0, b = 0.0;
-    for (int t = threadIdx.x; t < S.n_gm_tiles; t += blockDim.x) {
+    for (int t = threadIdx.x; t < S.n_prec_parts; t += blockDim.x) {
       a += S.part[t * 4 + 2];
       b += S.part[t * 4 + 3];
     }

@@ -30,10 +30,11 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_poll", "ext_drain", "ext_destroy", "ext_strerror", "ext_last_error",
             "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
             "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
-            "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices", "ext_stencil_tile"]
+            "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices", "ext_stencil_tile",
+            "ext_axis_class_basis"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
-                "pq_finish", "low_fwd", "low_mid", "low_inv"]
+                "pq_finish", "low_fwd", "low_mid", "low_inv", "unfold"]
 
 
 class ExtProblem(C.Structure):
@@ -47,7 +48,7 @@ class ExtOptions(C.Structure):
                 ("iters_per_launch", C.c_int32),
                 ("hbm_budget", C.c_size_t), ("flexible", C.c_int32), ("max_slots", C.c_int32),
                 ("profile", C.c_int32), ("autotune", C.c_int32), ("tile_y", C.c_int32),
-                ("low_modes", C.c_int32), ("wait_cycles", C.c_int64)]
+                ("low_modes", C.c_int32), ("wait_cycles", C.c_int64), ("fold", C.c_int32)]
 
 
 class ExtResult(C.Structure):
@@ -122,6 +123,8 @@ def load():
     lib.ext_noalloc_last_error.restype = C.c_char_p
     lib.ext_axis_basis.argtypes = [C.c_int32, I, P, P]
     lib.ext_axis_basis.restype = I
+    lib.ext_axis_class_basis.argtypes = [C.c_int32, I, C.c_int32, P, P]
+    lib.ext_axis_class_basis.restype = I
     lib.ext_axis_slices.argtypes = [C.c_int32, I, C.c_int32, P, P]
     lib.ext_axis_slices.restype = I
     _lib = lib
@@ -169,7 +172,9 @@ def problem_of(p):
 
 def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launch=10,
             hbm_budget=0, flexible=0, max_slots=256, replace_factor=1e-2, profile=0,
-            wait_cycles=0, autotune=1, tile_y=32, low_modes=1):
+            wait_cycles=0, autotune=1, tile_y=32, low_modes=None, fold=None):
+    """ext_options with the library's defaults for every field not given (low_modes and fold:
+    None keeps the library's default)."""
     o = ExtOptions()
     load().ext_options_default(C.byref(o))
     o.prec = PREC[prec] if isinstance(prec, str) else int(prec)
@@ -178,7 +183,11 @@ def options(prec="fp32", rtol=1e-8, maxit=0, true_res_every=200, iters_per_launc
     o.iters_per_launch, o.hbm_budget = int(iters_per_launch), int(hbm_budget)
     o.flexible, o.max_slots, o.profile = int(flexible), int(max_slots), int(profile)
     o.wait_cycles = int(wait_cycles)
-    o.autotune, o.tile_y, o.low_modes = int(autotune), int(tile_y), int(low_modes)
+    o.autotune, o.tile_y = int(autotune), int(tile_y)
+    if low_modes is not None:
+        o.low_modes = int(low_modes)
+    if fold is not None:
+        o.fold = int(fold)
     return o
 
 
@@ -322,6 +331,17 @@ def ext_axis_basis(n, bc):
     lam = np.empty(int(n), np.float64)
     _check(load().ext_axis_basis(int(n), BC[bc] if isinstance(bc, str) else int(bc), _ptr(Q),
                                  _ptr(lam)), "ext_axis_basis")
+    return Q, lam
+
+
+def ext_axis_class_basis(n, bc, cls):
+    """(Q, lam) of one mirror class (0 even, 1 odd) of an axis's basis, computed by the library on
+    the host (no GPU): Q[i, j] (i, j < ceil(n/2)) is the class's j-th eigenvector at node i."""
+    h = (int(n) + 1) // 2
+    Q = np.empty((h, h), np.float64)
+    lam = np.empty(h, np.float64)
+    _check(load().ext_axis_class_basis(int(n), BC[bc] if isinstance(bc, str) else int(bc), int(cls),
+                                       _ptr(Q), _ptr(lam)), "ext_axis_class_basis")
     return Q, lam
 
 

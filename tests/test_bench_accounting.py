@@ -19,6 +19,7 @@ def test_algorithmic_cost_per_kernel_kind():
     assert bench.algorithmic_cost(probs, "stencil") == (33 * nodes, "byte")
     assert bench.algorithmic_cost(probs, "update") == (48 * nodes, "byte")
     assert bench.algorithmic_cost(probs, "split") == (16 * nodes, "byte")
+    assert bench.algorithmic_cost(probs, "unfold") == (33 * nodes, "byte")
     # stage s contracts one axis: 2 nx ny n_axis flop, x for stages 0 and 2, y for 1 and 3
     p = synth.wobbly(128, 0)
     assert bench.algorithmic_cost([p], "prec_stage0") == (2 * 128 ** 3, "flop")
@@ -28,9 +29,19 @@ def test_algorithmic_cost_per_kernel_kind():
 
 def test_issued_tensor_flop_counts_ten_slice_products_on_padded_tiles():
     p = synth.wobbly(192, 1)  # padded to 256 on every axis
-    assert bench.issued_tensor_flop([p], "prec_stage1") == 2 * 10 * 256 ** 3
-    q = synth.wobbly(128, 2)  # no padding
+    assert bench.issued_tensor_flop([p], "prec_stage1", fold=False) == 2 * 10 * 256 ** 3
+    # folded: four mirror classes of 96 x 96 nodes, each padded to 128 (half the products)
+    assert bench.issued_tensor_flop([p], "prec_stage1", fold=True) == 4 * 2 * 10 * 128 ** 3
+    q = synth.wobbly(128, 2)  # no padding; 64-node classes would pad back to 128: not folded
+    assert bench.mirror_classes(128) == [128]
     assert bench.issued_tensor_flop([q], "prec_stage2") == 10 * bench.algorithmic_cost([q], "prec_stage2")[0]
+
+
+def test_mirror_classes_follow_the_padding_rule():
+    assert bench.mirror_classes(512) == [256, 256]
+    assert bench.mirror_classes(255) == [128, 128]   # odd: the middle node is in the even class
+    assert bench.mirror_classes(300) == [300]        # 150 pads to 256, twice 512 > 384
+    assert bench.mirror_classes(512, fold=False) == [512]
 
 
 def test_error_vs_oracle_is_the_max_norm_relative_error_over_unknowns():

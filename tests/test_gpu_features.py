@@ -140,18 +140,19 @@ def test_tile_heights_and_autotuned_tiles_give_identical_results(ext, prec):
             assert r1["iters"] == r2["iters"] and torch.equal(o1, o2), name
 
 
-def test_low_mode_correction_cuts_iterations_and_keeps_parity(ext):
-    """The lowest 32 x 32 modes of the mixed path's preconditioner come from six-slice products
-    (about 48 bits) instead of the four-slice stages: on batch-workload grids the iteration count
-    at rel-res 1e-8 falls, and both answers stay within the mixed path's bound of the direct
-    solve."""
+@pytest.mark.parametrize("fold", [0, 1])
+def test_low_mode_correction_cuts_iterations_and_keeps_parity(ext, fold):
+    """The lowest 32 x 32 modes of the mixed path's preconditioner (of each mirror class when the
+    transforms are folded) come from six-slice products (about 48 bits) instead of the four-slice
+    stages: on batch-workload grids the iteration count at rel-res 1e-8 falls, and both answers
+    stay within the mixed path's bound of the direct solve."""
     its = {}
     for p in (synth.wobbly(256, 0), synth.wobbly(384, 5), synth.star(256, "periodic", "in")):
         phi64, f64 = p.phi.astype(np.float64), p.f.astype(np.float64)
         ref, _ = ob.extend(phi64, f64, p.direction, p.bc_x, p.bc_y, p.hx, p.hy, method="direct")
         known = ob.known_mask(phi64, p.direction)
         for low in (0, 1):
-            c = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, low_modes=low))
+            c = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, low_modes=low, fold=fold))
             try:
                 out64 = torch.empty(p.phi.shape, device="cuda", dtype=torch.float64)
                 res = ext.ext_solve_f64(c, ext.problem_of(p), dev(p.phi), dev(p.f), out64)

@@ -409,6 +409,38 @@ def test_mixed_preconditioner_matches_fast_poisson(ext, mixed, bc_x, bc_y, nx, n
     np.testing.assert_allclose(got, ref, rtol=0, atol=5e-6 * np.abs(ref).max())
 
 
+@pytest.fixture(scope="module")
+def fold_ctxs(ext):
+    # folded, full-size, and folded with the low-mode correction
+    cs = [ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, fold=f, low_modes=lm))
+          for f, lm in ((1, 0), (0, 0), (1, 1))]
+    yield cs
+    for c in cs:
+        ext.ext_destroy(c)
+
+
+@pytest.mark.parametrize("bc_x", ob.BCS)
+@pytest.mark.parametrize("bc_y", ob.BCS)
+# both axes folded (odd and even n), x only (y = 128 does not pay), y only (x = 300 does not)
+@pytest.mark.parametrize("nx,ny", [(255, 200), (256, 193), (255, 128), (300, 255)])
+def test_folded_preconditioner_matches_fast_poisson(ext, fold_ctxs, bc_x, bc_y, nx, ny):
+    """The transforms run per mirror class (even / odd vectors under i -> n-1-i) on axes where
+    that halves the work: the same operator as the full-size transforms and the oracle's."""
+    phi = _rand_phi(nx, ny, 5)
+    known = ob.known_mask(phi.astype(np.float64), "out")
+    r = np.random.default_rng(6).standard_normal((ny, nx)).astype(np.float32)
+    r[known] = 0
+    ref = ob.poisson_squared_pinv(r.astype(np.float64), bc_x, bc_y)
+    ref[known] = 0
+    got = []
+    for c in fold_ctxs:
+        z = torch.empty((ny, nx), device="cuda")
+        scale = ext.ext_apply_preconditioner(c, ext.problem(nx, ny, bc_x, bc_y, "out"), dev(phi), dev(r), z)
+        got.append(z.cpu().numpy().astype(np.float64) / scale)
+        np.testing.assert_allclose(got[-1], ref, rtol=0, atol=5e-6 * np.abs(ref).max())
+        assert np.all(got[-1][known] == 0)
+
+
 @pytest.mark.parametrize("maker", [lambda: synth.circle(64), lambda: synth.wobbly(192, 3),
                                    lambda: synth.star(256, "periodic", "in")])
 def test_mixed_solve_validity_and_uniqueness(ext, mixed, maker):

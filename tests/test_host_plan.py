@@ -99,3 +99,65 @@ def test_axis_slices_rejects_bad_arguments(ext):
     for n, bc, t in ((3, 0, 1), (32769, 0, 1), (8, 3, 1), (8, 0, 2)):
         assert lib.ext_axis_slices(n, bc, t, codes.ctypes.data, exps.ctypes.data) == ext.EXT_EINVAL
     assert lib.ext_axis_slices(8, 0, 1, None, None) == ext.EXT_EINVAL
+
+
+def _fold(r, cls):
+    """Mirror fold of an axis vector (i -> n-1-i) for class cls: sum (even) or difference (odd) of
+    each node and its mirror on the first ceil(n/2) nodes; the middle node of an odd n alone."""
+    n = r.shape[0]
+    h = (n + 1) // 2
+    m = r[::-1][:h]
+    v = r[:h] + m if cls == 0 else r[:h] - m
+    if n % 2:
+        v[h - 1] = r[h - 1] if cls == 0 else 0.0
+    return v
+
+
+def _unfold(E, O, n):
+    """Inverse of the fold: E + O on the first ceil(n/2) nodes, E - O on their mirrors."""
+    h, k = (n + 1) // 2, n // 2  # k nodes have a distinct mirror
+    y = np.empty(n)
+    y[:h] = E + O
+    y[n - 1 - np.arange(k)] = (E - O)[:k]
+    return y
+
+
+@pytest.mark.parametrize("bc", ob.BCS)
+@pytest.mark.parametrize("n", [4, 5, 7, 16, 33, 64, 100, 129])
+def test_mirror_classes_apply_the_same_function_of_T(ext, bc, n):
+    # g(T) r with g = 1/(1 + lambda), through the two half-size class bases (fold, transform,
+    # scale, inverse transform, unfold), against a dense solve with the oracle's T
+    T = ob.axis_second_difference(n, bc).toarray()
+    rng = np.random.default_rng(n)
+    r = rng.standard_normal(n)
+    ref = np.linalg.solve(np.eye(n) + T, r)
+    parts = []
+    for cls in (0, 1):
+        F, lam = ext.ext_axis_class_basis(n, bc, cls)
+        c = F.T @ _fold(r, cls)
+        parts.append(F @ (c / (1.0 + lam)))
+    y = _unfold(parts[0], parts[1], n)
+    np.testing.assert_allclose(y, ref, rtol=0, atol=1e-12 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("bc", ob.BCS)
+@pytest.mark.parametrize("n", [5, 16, 33, 128])
+def test_mirror_classes_split_the_spectrum(ext, bc, n):
+    h = (n + 1) // 2
+    w = np.full(h, 2.0)
+    if n % 2:
+        w[h - 1] = 1.0  # the middle node is its own mirror
+    lams, count = [], 0
+    for cls in (0, 1):
+        F, lam = ext.ext_axis_class_basis(n, bc, cls)
+        live = np.abs(F).sum(axis=0) > 0
+        k = int(live.sum())
+        assert live[:k].all() and not live[k:].any()        # the class's modes come first
+        assert np.all(np.diff(lam[:k]) >= -1e-15)             # in ascending order
+        # orthonormal as full-length vectors (each node and its mirror)
+        np.testing.assert_allclose(F[:, :k].T @ (w[:, None] * F[:, :k]), np.eye(k), rtol=0, atol=1e-13)
+        lams.append(lam[:k])
+        count += k
+    assert count == n
+    np.testing.assert_allclose(np.sort(np.concatenate(lams)), np.sort(ob.axis_eigenvalues(n, bc)),
+                               rtol=0, atol=1e-13)
