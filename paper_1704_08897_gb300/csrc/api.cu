@@ -91,7 +91,8 @@ struct Workspace {
   WorkItem* d_sl = nullptr;     // one item per slot (tile 0), for the per-slot scalar kernels
   int *d_counts = nullptr;      // [0] grid tiles, [1] vector items, [2] gemm items, [3] slots,
                                 // [4] stencil tiles, [5] [6] low-mode tiles, [7] fold items,
-                                // [8] unfold tiles, [9] tensor-core problems
+                                // [8] unfold tiles, [9] tensor-core problems, [10] grid tiles
+                                // of unfolded slots
   int n_st = 0, n_vec = 0, n_gm = 0, n_sl = 0;
   WorkItem* d_sten = nullptr;   // the stencil kernel's tiles (64 x sten_ty)
   int n_sten = 0;
@@ -104,6 +105,8 @@ struct Workspace {
   SlotDesc* d_tcp = nullptr;
   WorkItem *d_fold = nullptr, *d_unfold = nullptr, *d_tcl = nullptr;
   int n_fold = 0, n_unfold = 0, n_tcl = 0;
+  WorkItem* d_prep = nullptr;  // grid tiles of the unfolded slots (their residual slicing)
+  int n_prep = 0;
   const float** d_phis = nullptr;
   const float** d_fs = nullptr;
   float** d_outs = nullptr;
@@ -470,6 +473,7 @@ static void free_workspace(Workspace* W) {
   cudaFree(W->d_fold);
   cudaFree(W->d_unfold);
   cudaFree(W->d_tcl);
+  cudaFree(W->d_prep);
   cudaFree(W->d_counts);
   cudaFree(W->d_phis);
   cudaFree(W->d_fs);
@@ -815,7 +819,7 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   W->key = shape_key(count, probs, host_io);
   W->host_io = host_io;
   W->slots.resize(count);
-  std::vector<WorkItem> st, vec, gm, l1, l3, fold, unfold, tcl;
+  std::vector<WorkItem> st, vec, gm, l1, l3, fold, unfold, tcl, prep;
   for (int i = 0; i < count; ++i) {
     SlotHost& s = W->slots[i];
     int rc = build_slot(ctx, probs[i], host_io, s);
@@ -832,6 +836,8 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
       tc_items(s, i, gm, l1, l3, tcl);
       for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
       for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
+      if (!d.mir)
+        for (int t = 0; t < d.n_st_tiles; ++t) prep.push_back({i, t});
     } else {
       for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
     }
@@ -866,6 +872,7 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   if (!rc) rc = upload(&W->d_fold, fold);
   if (!rc) rc = upload(&W->d_unfold, unfold);
   if (!rc) rc = upload(&W->d_tcl, tcl);
+  if (!rc) rc = upload(&W->d_prep, prep);
   if (rc) return rc;
   W->n_sten = W->n_st;
   W->n_l1 = (int)l1.size();
@@ -873,8 +880,9 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   W->n_fold = (int)fold.size();
   W->n_unfold = (int)unfold.size();
   W->n_tcl = (int)tcl.size();
-  int counts[10] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten, W->n_l1, W->n_l3,
-                    W->n_fold, W->n_unfold, W->n_tcl};
+  W->n_prep = (int)prep.size();
+  int counts[11] = {W->n_st, W->n_vec, W->n_gm, W->n_sl, W->n_sten, W->n_l1, W->n_l3,
+                    W->n_fold, W->n_unfold, W->n_tcl, W->n_prep};
   BX_CUDA(cudaMalloc(&W->d_counts, sizeof(counts)));
   BX_CUDA(cudaMemcpy(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * count));
@@ -923,6 +931,10 @@ static LaunchCfg cfg_of(ext_ctx* ctx, Workspace* W, int which) {
     c.items = W->d_tcl;
     c.n_items = W->d_counts + 9;
     c.grid = std::max(1, std::min(W->n_tcl, cap));
+  } else if (which == 10) {
+    c.items = W->d_prep;
+    c.n_items = W->d_counts + 10;
+    c.grid = std::max(1, std::min(W->n_prep, cap));
   } else if (which == 0) {
     c.items = W->d_st;
     c.n_items = W->d_counts + 0;
@@ -1015,9 +1027,8 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
   LaunchCfg g = cfg_of(ctx, W, 2);
   if (ctx->tc) {
     // residual slices: unfolded slots directly, folded slots per mirror class
-    const LaunchCfg st = cfg_of(ctx, W, 0);
     timed(ctx, EXT_KERNEL_SPLIT, [&] {
-      launch_prec_tc_prepare(st, mode, ctx->split);
+      if (W->n_prep > 0) launch_prec_tc_prepare(cfg_of(ctx, W, 10), mode, ctx->split);
       if (W->n_fold > 0) launch_tc_fold(cfg_of(ctx, W, 7), mode, ctx->split);
     }, g.stream);
     // the transform kernels run over the tensor-core problems
@@ -1759,10 +1770,12 @@ static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
   cudaFree(W->d_fold);
   cudaFree(W->d_unfold);
   cudaFree(W->d_tcl);
+  cudaFree(W->d_prep);
   cudaFree(S->d_new);
   cudaFree(S->d_ret);
   W->d_st = W->d_sten = W->d_vec = W->d_gm = W->d_l1 = W->d_l3 = S->d_new = S->d_ret = nullptr;
-  W->d_fold = W->d_unfold = W->d_tcl = nullptr;
+  W->d_fold = W->d_unfold = W->d_tcl = W->d_prep = nullptr;
+  BX_CUDA(cudaMalloc(&W->d_prep, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_fold, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_unfold, sizeof(WorkItem) * cap));
   BX_CUDA(cudaMalloc(&W->d_tcl, sizeof(WorkItem) * cap));
@@ -1777,7 +1790,7 @@ static int serve_alloc_lists(ext_ctx::Serve* S, int cap) {
   S->cap_items = cap;
   // grids sized for the capacity
   W->n_st = W->n_vec = W->n_gm = W->n_sten = W->n_l1 = W->n_l3 = cap;
-  W->n_fold = W->n_unfold = W->n_tcl = cap;
+  W->n_fold = W->n_unfold = W->n_tcl = W->n_prep = cap;
   if (W->graph) {
     cudaGraphExecDestroy(W->graph);
     W->graph = nullptr;
@@ -1799,8 +1812,8 @@ static int serve_init(ext_ctx* ctx) {
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * cap));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * cap));
   memset(W->h_sc, 0, sizeof(SlotScalars) * cap);
-  BX_CUDA(cudaMalloc(&W->d_counts, 10 * sizeof(int)));
-  BX_CUDA(cudaMemset(W->d_counts, 0, 10 * sizeof(int)));
+  BX_CUDA(cudaMalloc(&W->d_counts, 11 * sizeof(int)));
+  BX_CUDA(cudaMemset(W->d_counts, 0, 11 * sizeof(int)));
   BX_CUDA(cudaMalloc(&W->d_sl, sizeof(WorkItem) * cap));
   W->n_sl = cap;  // the per-slot grid is sized for the slot table
   BX_CUDA(cudaMalloc(&W->d_phis, sizeof(void*) * cap));
@@ -1823,7 +1836,7 @@ static int serve_init(ext_ctx* ctx) {
 static int serve_rebuild_lists(ext_ctx* ctx) {
   ext_ctx::Serve* S = ctx->serve;
   Workspace* W = S->W;
-  std::vector<WorkItem> st, vec, gm, sl, l1, l3, fold, unfold, tcl;
+  std::vector<WorkItem> st, vec, gm, sl, l1, l3, fold, unfold, tcl, prep;
   bool aniso = false;
   for (int i = 0; i < (int)S->slots.size(); ++i) {
     if (!S->slots[i].used) continue;
@@ -1836,6 +1849,8 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
       tc_items(h, i, gm, l1, l3, tcl);
       for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
       for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
+      if (!d.mir)
+        for (int t = 0; t < d.n_st_tiles; ++t) prep.push_back({i, t});
     } else {
       for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
     }
@@ -1844,7 +1859,7 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
   if (ctx->tc) longest_first_tc(gm, W->slots);
   else longest_first(gm, W->slots);
   size_t need = 0;
-  for (const auto* v : {&st, &vec, &gm, &l1, &l3, &fold, &unfold, &tcl}) need = std::max(need, v->size());
+  for (const auto* v : {&st, &vec, &gm, &l1, &l3, &fold, &unfold, &tcl, &prep}) need = std::max(need, v->size());
   if ((int)need > S->cap_items) {
     int cap = S->cap_items;
     while (cap < (int)need) cap *= 2;
@@ -1873,9 +1888,11 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
   if (!rc) rc = put(W->d_fold, fold);
   if (!rc) rc = put(W->d_unfold, unfold);
   if (!rc) rc = put(W->d_tcl, tcl);
+  if (!rc) rc = put(W->d_prep, prep);
   if (rc) return rc;
-  int counts[10] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size(),
-                    (int)l1.size(), (int)l3.size(), (int)fold.size(), (int)unfold.size(), (int)tcl.size()};
+  int counts[11] = {(int)st.size(), (int)vec.size(), (int)gm.size(), (int)sl.size(), (int)st.size(),
+                    (int)l1.size(), (int)l3.size(), (int)fold.size(), (int)unfold.size(), (int)tcl.size(),
+                    (int)prep.size()};
   BX_CUDA(cudaMemcpyAsync(W->d_counts, counts, sizeof(counts), cudaMemcpyHostToDevice, s));
   // the host vectors die here: the copies above must finish first (pageable sources are staged)
   BX_CUDA(cudaStreamSynchronize(s));

@@ -644,8 +644,9 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         }
       }
     }
-    __syncthreads();
-    // the 16-row blocks of the tile (TY / 16 of them, so the partials do not depend on TY)
+    __syncthreads();  // the window set is free for the copies started at the next copied tile
+    // the 16-row blocks of the tile (TY / 16 of them, so the partials do not depend on TY); the
+    // next tile writes blk_sm only after its own block barriers, which these threads join later
     if (threadIdx.x < TY / 16) {
       const int by = (y0 >> 4) + threadIdx.x;
       double acc = 0.0;
@@ -653,7 +654,6 @@ k_stencil(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       for (int w = 0; w < kStThreads / 32; ++w) acc += blk_sm[threadIdx.x][w];
       if (16 * by < S.ny) S.pq_part[by * nbx + x0 / kStTileX] = acc;
     }
-    __syncthreads();  // the window set is free for the copies started at the next copied tile
   }
   if (threadIdx.x == 0) {
     // copies still in flight (only after an abort) land before the block's memory is released
