@@ -169,8 +169,8 @@ def algorithmic_cost(probs, kind):
         return sum(48 * p.nx * p.ny for p in probs), "byte"
     if kind == "split":     # read r (8); write four 16-bit slices (8)
         return sum(16 * p.nx * p.ny for p in probs), "byte"
-    if kind == "unfold":    # read the classes' g (8), r (8), q (8), mask (1); write z (8)
-        return sum(33 * p.nx * p.ny for p in probs), "byte"
+    if kind == "unfold":    # read the classes' g (8), r (8), mask (1); write z (8); q (8) is read
+        return sum(25 * p.nx * p.ny for p in probs), "byte"  # only for the flexible beta
     return None, None
 
 

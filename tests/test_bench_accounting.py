@@ -19,7 +19,7 @@ def test_algorithmic_cost_per_kernel_kind():
     assert bench.algorithmic_cost(probs, "stencil") == (33 * nodes, "byte")
     assert bench.algorithmic_cost(probs, "update") == (48 * nodes, "byte")
     assert bench.algorithmic_cost(probs, "split") == (16 * nodes, "byte")
-    assert bench.algorithmic_cost(probs, "unfold") == (33 * nodes, "byte")
+    assert bench.algorithmic_cost(probs, "unfold") == (25 * nodes, "byte")
     # stage s contracts one axis: 2 nx ny n_axis flop, x for stages 0 and 2, y for 1 and 3
     p = synth.wobbly(128, 0)
     assert bench.algorithmic_cost([p], "prec_stage0") == (2 * 128 ** 3, "flop")
