@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="batch: requests of the serving leg (config-4 shape); 0 skips it")
+    ap.add_argument("--peanut3d", default="64,128",
+                    help="batch: sides of the three-dimensional Example 2 leg ('' skips it)")
     ap.add_argument("--low-modes", type=int, default=None,
                     help="low-mode correction of the mixed preconditioner: 1 on, 0 off (library default)")
     ap.add_argument("--fold", type=int, default=None,
@@ -531,6 +533,55 @@ def error_vs_oracle(probs, answers, refs, prec, at="rel-res 1e-8, answers of the
             "at": at}
 
 
+# The paper's Example 2 table (three-dimensional peanut, periodic): n -> (iterations, error)
+PAPER_EXAMPLE2 = {32: (21, 1.08e-01), 64: (46, 3.42e-02), 128: (112, 1.07e-02), 256: (276, 2.84e-03)}
+
+
+def peanut3d_leg(sides=(64, 128)):
+    """The three-dimensional extension (Sec. 3 Example 2): the peanut on [-pi, pi]^3, periodic,
+    extend out, through ext_solve3d.  Per side: time and iterations at rel-res 1e-8, the
+    iterations at the paper's rel-res 1e-6 beside the printed ones, and the max error within one
+    grid cell of the interface against the analytic field beside the printed error."""
+    import numpy as np
+    import torch
+    from paper_1704_08897_gb300 import ext
+    out = {"workload": "Example 2 peanut, [-pi, pi]^3, periodic, extend out, FP32 path",
+           "note": "paper errors match the one-cell band (its caption says four cells)", "sides": {}}
+    for n in sides:
+        h = 2 * np.pi / n
+        xs = -np.pi + (np.arange(n) + 0.5) * h
+        Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+        phi = np.minimum(np.sqrt((X - 0.8) ** 2 + Y ** 2 + Z ** 2) - 1,
+                         np.sqrt((X + 0.8) ** 2 + Y ** 2 + Z ** 2) - 1).astype(np.float32)
+        f = (np.cos(X) * np.sin(Y) * np.sin(np.pi / 4 - Z)).astype(np.float32)
+        band = np.abs(phi) <= h
+        dphi, dfv = torch.from_numpy(phi).cuda(), torch.from_numpy(f).cuda()
+        o = torch.empty_like(dphi)
+        prob = ext.problem3(n, n, n, "periodic", "periodic", "periodic", "out", h)
+        row = {}
+        for rtol in (1e-8, 1e-6):
+            c = ext.ext_create(_options("fp32", rtol=rtol))
+            try:
+                ext.ext_solve3d(c, prob, dphi, dfv, o)            # warm-up (plans, code)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res = ext.ext_solve3d(c, prob, dphi, dfv, o)
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+            finally:
+                ext.ext_destroy(c)
+            err = float(np.abs(o.cpu().numpy() - f)[band].max())
+            row[f"rtol_{rtol:g}"] = {"iterations": res["iters"], "s_per_solve": round(dt, 4),
+                                     "relres_true": res["relres_true"], "error_1cell": err}
+        if n in PAPER_EXAMPLE2:
+            row["paper"] = {"iterations": PAPER_EXAMPLE2[n][0], "error": PAPER_EXAMPLE2[n][1]}
+        # the six dense transform products dominate: 2 n^4 multiply-adds each per application
+        it = row["rtol_1e-08"]["iterations"]
+        row["transform_fma_per_s"] = (6 * 2 * n ** 4 * (it + 1)) / row["rtol_1e-08"]["s_per_solve"]
+        out["sides"][str(n)] = row
+    return out
+
+
 def serving_leg(count=48, seed=None, side_lo=64, side_hi=2048, plain_budget_s=20.0):
     """A bounded sample of the serving workload (config-4 shape): `count` requests with sides
     log-uniform in [side_lo, side_hi], star or multi-circle interfaces, extend in or out and
@@ -680,6 +731,8 @@ def main():
     out, probs, answers, (sample_answers, sample_iters) = run_ours(args, rank, world)
     if rank == 0 and args.workload == "batch" and args.serve_requests > 0:
         out["serving"] = serving_leg(count=args.serve_requests)
+    if rank == 0 and args.workload == "batch" and args.peanut3d:
+        out["peanut3d"] = peanut3d_leg(tuple(int(v) for v in args.peanut3d.split(",")))
     if rank == 0:
         if not args.no_cpu_baseline:
             out["cpu_baseline"], refs = cpu_baseline(args, probs)

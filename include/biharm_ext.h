@@ -123,6 +123,16 @@ enum {
   EXT_KERNEL_KINDS = 16
 };
 
+/* A three-dimensional problem (Sec. 3 Example 2: the equations of Sec. 2 in three dimensions;
+ * at an interior node with equal spacings the operator is the 25-point squared 7-point
+ * Laplacian).  Grid arrays are row-major [nz][ny][nx] (x contiguous), float32. */
+typedef struct {
+  int32_t nx, ny, nz;        /* nodes along x (contiguous), y and z; each >= 4                 */
+  double hx, hy, hz;         /* node spacings (> 0); the solution depends only on their ratios */
+  int32_t bc_x, bc_y, bc_z;  /* ext_bc of each axis                                            */
+  int32_t dir;               /* ext_dir                                                        */
+} ext_problem3;
+
 typedef struct {
   int32_t status;      /* EXT_OK, EXT_ENOTCONV, EXT_EBREAKDOWN, ...                            */
   int32_t iters;       /* CG iterations taken                                                  */
@@ -248,6 +258,34 @@ int ext_apply_preconditioner(ext_ctx* ctx, const ext_problem* prob, const float*
  * lam (n doubles, lam[k] its eigenvalue) are caller-owned host arrays; T = Q diag(lam) Q^T.
  * Returns EXT_OK, or EXT_EINVAL for n < 4, n > 32768, an unknown bc or a NULL array. */
 int ext_axis_basis(int32_t n, ext_bc bc, double* Q, double* lam);
+
+/* Three-dimensional extension (Sec. 3 Example 2).  Solves the masked biharmonic system on the
+ * nz x ny x nx box by preconditioned CG from x = 0 to the context's rtol (relative FP64 residual on
+ * the unknowns), the preconditioner being the fast Poisson solve on the box by separable
+ * transforms along the three axes.  It runs the CUDA-core double-float path in every precision
+ * mode (double-float CG vectors, compensated products in the transforms, FP64 right-hand side and
+ * residual replacements), one problem per call, the iteration driven from the host.  phi, f and
+ * out are device pointers ([nz][ny][nx] float32; host pointers return EXT_EINVAL); out = f at
+ * known nodes (bit copy), the extension elsewhere; out may alias f.  res (may be NULL) receives
+ * status, iterations, the true and recursive relative residuals, counts and err_est.  Returns
+ * EXT_OK, EXT_EINVAL (sizes, spacings, enums, NaN phi, a non-finite known value, host pointers),
+ * EXT_ENOKNOWN, EXT_ENOMEM, EXT_ENOTCONV (out holds the last iterate), EXT_EBREAKDOWN or
+ * EXT_ECUDA.  Allocates its workspace per call (about 90 bytes per node). */
+int ext_solve3d(ext_ctx* ctx, const ext_problem3* prob, const float* phi, const float* f, float* out,
+                ext_result* res);
+
+/* q = M L^2 M p for the 3-D problem (the solver's operator passes; M zeroes known nodes), with
+ * the spacings normalised so that the largest 1/h^2 is 1.  phi, p, q: device pointers
+ * [nz][ny][nx]; q receives the hi plane of the double-float result (exact for integer p of
+ * moderate size). */
+int ext_apply_biharmonic3d(ext_ctx* ctx, const ext_problem3* prob, const float* phi, const float* p,
+                           float* q);
+
+/* z = M (L^2)^+ M r for the 3-D problem (the solver's preconditioner; pseudo-inverse when no axis
+ * is Dirichlet), scale-free: z is (L^2)^+ M r times the positive constant written to *scale (may
+ * be NULL).  phi, r, z: device pointers [nz][ny][nx]; z receives the hi plane. */
+int ext_apply_preconditioner3d(ext_ctx* ctx, const ext_problem3* prob, const float* phi, const float* r,
+                               float* z, double* scale);
 
 /* One mirror class of the same axis, computed on the host (no GPU, no context); this is what the
  * tensor-core preconditioner applies on axes where folding halves the work (Sec. 2.2: the fast

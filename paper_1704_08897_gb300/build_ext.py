@@ -18,7 +18,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbiharm_ext.so")
 SOURCES = ["api.cu", "kernels_grid.cu", "kernels_gemm_simt.cu", "kernels_gemm_tc.cu",
-           "plan.cpp", "noalloc.cu"]
+           "plan.cpp", "noalloc.cu", "solve3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1561,6 +1561,118 @@ int ext_solve_f64(ext_ctx* ctx, const ext_problem* prob, const float* phi, const
   return run_solve(ctx, W, phis, fs, outs, dirs, res, out64);
 }
 
+// ---- three-dimensional extension --------------------------------------------------------------
+static int validate_problem3(const ext_problem3* p) {
+  if (!p) return EXT_EINVAL;
+  if (p->nx < 4 || p->ny < 4 || p->nz < 4) return EXT_EINVAL;
+  if (p->nz > 65535 || (int64_t)p->nx * p->ny * p->nz > (int64_t)1 << 30) return EXT_EINVAL;
+  const double h[3] = {p->hx, p->hy, p->hz};
+  for (double v : h)
+    if (!(v > 0.0) || !std::isfinite(v)) return EXT_EINVAL;
+  const int bc[3] = {p->bc_x, p->bc_y, p->bc_z};
+  for (int b : bc)
+    if (b < 0 || b > 2) return EXT_EINVAL;
+  if (p->dir != 0 && p->dir != 1) return EXT_EINVAL;
+  return EXT_OK;
+}
+
+// The arguments of the 3-D kernels: the axis plans (built or found in the context's cache).
+static int args3(ext_ctx* ctx, const ext_problem3* p, Solve3Args& a) {
+  std::lock_guard<std::recursive_mutex> plk(ctx->plan_mu);
+  a.nx = p->nx;
+  a.ny = p->ny;
+  a.nz = p->nz;
+  a.bc[0] = p->bc_x;
+  a.bc[1] = p->bc_y;
+  a.bc[2] = p->bc_z;
+  a.dir = p->dir;
+  a.h[0] = p->hx;
+  a.h[1] = p->hy;
+  a.h[2] = p->hz;
+  const int n[3] = {p->nx, p->ny, p->nz};
+  for (int ax = 0; ax < 3; ++ax) {
+    PlanDev* P = nullptr;
+    const int rc = get_plan(ctx, n[ax], a.bc[ax], -1, &P);
+    if (rc) return rc;
+    a.q[ax] = P->q;
+    a.qt[ax] = P->qt;
+    a.np[ax] = P->np;
+    a.lam[ax] = P->lam.data();
+  }
+  a.rtol = ctx->opt.rtol;
+  a.maxit = ctx->opt.maxit;
+  a.true_res_every = ctx->opt.true_res_every;
+  a.replace_factor = ctx->opt.replace_factor;
+  a.stream = ctx->stream;
+  return EXT_OK;
+}
+
+int ext_solve3d(ext_ctx* ctx, const ext_problem3* prob, const float* phi, const float* f, float* out,
+                ext_result* res) {
+  if (!ctx || !prob || !phi || !f || !out) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  int rc = validate_problem3(prob);
+  if (rc) return rc;
+  if (!is_device_ptr(phi) || !is_device_ptr(f) || !is_device_ptr(out)) {
+    g_last_error = "phi, f and out must be device pointers";
+    return EXT_EINVAL;
+  }
+  Solve3Args a;
+  rc = args3(ctx, prob, a);
+  if (rc) return rc;
+  ext_result r{};
+  r.status = EXT_ECUDA;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::string err;
+  long long nl = 0;
+  a.launches = &nl;
+  rc = solve3d_run(a, phi, f, out, &r, &err);
+  ctx->launches += nl;
+  r.ms_solve = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  if (rc != EXT_OK && rc != EXT_ENOTCONV && rc != EXT_EBREAKDOWN) r.status = rc;
+  if (!err.empty()) g_last_error = err;
+  if (res) *res = r;
+  return rc;
+}
+
+int ext_apply_biharmonic3d(ext_ctx* ctx, const ext_problem3* prob, const float* phi, const float* p,
+                           float* q) {
+  if (!ctx || !prob || !phi || !p || !q) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  int rc = validate_problem3(prob);
+  if (rc) return rc;
+  if (!is_device_ptr(phi) || !is_device_ptr(p) || !is_device_ptr(q)) return EXT_EINVAL;
+  Solve3Args a;
+  rc = args3(ctx, prob, a);
+  if (rc) return rc;
+  std::string err;
+  long long nl = 0;
+  a.launches = &nl;
+  rc = apply3d_operator(a, phi, p, q, &err);
+  ctx->launches += nl;
+  if (!err.empty()) g_last_error = err;
+  return rc;
+}
+
+int ext_apply_preconditioner3d(ext_ctx* ctx, const ext_problem3* prob, const float* phi, const float* r,
+                               float* z, double* scale) {
+  if (!ctx || !prob || !phi || !r || !z) return EXT_EINVAL;
+  std::lock_guard<std::mutex> lk(ctx->api_mu);
+  int rc = validate_problem3(prob);
+  if (rc) return rc;
+  if (!is_device_ptr(phi) || !is_device_ptr(r) || !is_device_ptr(z)) return EXT_EINVAL;
+  Solve3Args a;
+  rc = args3(ctx, prob, a);
+  if (rc) return rc;
+  std::string err;
+  long long nl = 0;
+  a.launches = &nl;
+  rc = apply3d_preconditioner(a, phi, r, z, scale, &err);
+  ctx->launches += nl;
+  if (!err.empty()) g_last_error = err;
+  return rc;
+}
+
 int ext_profile_read(ext_ctx* ctx, int kinds, double* total_ms, int64_t* launches, int reset) {
   if (!ctx || kinds < 0) return EXT_EINVAL;
   std::lock_guard<std::mutex> lk(ctx->api_mu);

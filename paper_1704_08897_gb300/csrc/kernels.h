@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <string>
+
 #include "../../include/biharm_ext.h"
 #include "common.cuh"
 
@@ -67,6 +69,29 @@ void launch_tc_fold(const LaunchCfg& c, int mode, int split_kind);
 void launch_unfold(const LaunchCfg& c, int mode);
 int tc_block();
 bool tc_supported();
+
+// three-dimensional extension (solve3d.cu): the CUDA-core double-float path, host-driven CG
+struct Solve3Args {
+  int nx, ny, nz;
+  int bc[3];               // ext_bc of x, y, z
+  int dir;                 // ext_dir
+  double h[3];             // spacings of x, y, z
+  const float* q[3];       // per axis: Q and Q^T as double-float planes [2][np][np] (device)
+  const float* qt[3];
+  int np[3];
+  const double* lam[3];    // per axis: eigenvalues of T (h = 1), n entries (host)
+  double rtol;
+  int maxit;
+  int true_res_every;
+  double replace_factor;
+  cudaStream_t stream;
+  long long* launches;     // incremented by every kernel launch (host counter)
+};
+int solve3d_run(const Solve3Args& a, const float* phi, const float* f, float* out, ext_result* res,
+                std::string* err);
+int apply3d_operator(const Solve3Args& a, const float* phi, const float* p, float* q, std::string* err);
+int apply3d_preconditioner(const Solve3Args& a, const float* phi, const float* r, float* z, double* scale,
+                           std::string* err);
 // opt the tensor-core kernels into their dynamic shared memory (once per process and device)
 cudaError_t tc_init();
 

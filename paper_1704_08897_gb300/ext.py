@@ -31,7 +31,8 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_apply_biharmonic", "ext_rhs", "ext_apply_preconditioner", "ext_solve_f64",
             "ext_profile_read", "ext_launch_count", "ext_apply_biharmonic_noalloc",
             "ext_noalloc_last_error", "ext_axis_basis", "ext_axis_slices", "ext_stencil_tile",
-            "ext_axis_class_basis"]
+            "ext_axis_class_basis", "ext_solve3d", "ext_apply_biharmonic3d",
+            "ext_apply_preconditioner3d"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
                 "pq_finish", "low_fwd", "low_mid", "low_inv", "unfold"]
@@ -40,6 +41,12 @@ KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "p
 class ExtProblem(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("hx", C.c_double), ("hy", C.c_double),
                 ("bc_x", C.c_int32), ("bc_y", C.c_int32), ("dir", C.c_int32)]
+
+
+class ExtProblem3(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("hx", C.c_double),
+                ("hy", C.c_double), ("hz", C.c_double), ("bc_x", C.c_int32), ("bc_y", C.c_int32),
+                ("bc_z", C.c_int32), ("dir", C.c_int32)]
 
 
 class ExtOptions(C.Structure):
@@ -111,6 +118,12 @@ def load():
     lib.ext_rhs.restype = I
     lib.ext_apply_preconditioner.argtypes = [P, C.POINTER(ExtProblem), P, P, P, C.POINTER(D)]
     lib.ext_apply_preconditioner.restype = I
+    lib.ext_solve3d.argtypes = [P, C.POINTER(ExtProblem3), P, P, P, C.POINTER(ExtResult)]
+    lib.ext_solve3d.restype = I
+    lib.ext_apply_biharmonic3d.argtypes = [P, C.POINTER(ExtProblem3), P, P, P]
+    lib.ext_apply_biharmonic3d.restype = I
+    lib.ext_apply_preconditioner3d.argtypes = [P, C.POINTER(ExtProblem3), P, P, P, C.POINTER(D)]
+    lib.ext_apply_preconditioner3d.restype = I
     lib.ext_profile_read.argtypes = [P, I, C.POINTER(D), C.POINTER(C.c_int64), I]
     lib.ext_profile_read.restype = I
     lib.ext_stencil_tile.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
@@ -163,6 +176,19 @@ def problem(nx, ny, bc_x="symmetric", bc_y=None, direction="out", hx=1.0, hy=Non
     return ExtProblem(int(nx), int(ny), float(hx), float(hy), BC[bc_x] if isinstance(bc_x, str)
                       else int(bc_x), BC[bc_y] if isinstance(bc_y, str) else int(bc_y),
                       DIR[direction] if isinstance(direction, str) else int(direction))
+
+
+def problem3(nx, ny, nz, bc_x="periodic", bc_y=None, bc_z=None, direction="out", hx=1.0, hy=None,
+             hz=None):
+    """ExtProblem3 of an nz x ny x nx box (bc_y, bc_z default to bc_x; hy, hz to hx)."""
+    bc_y = bc_x if bc_y is None else bc_y
+    bc_z = bc_x if bc_z is None else bc_z
+    hy = hx if hy is None else hy
+    hz = hx if hz is None else hz
+    code = lambda b: BC[b] if isinstance(b, str) else int(b)
+    return ExtProblem3(int(nx), int(ny), int(nz), float(hx), float(hy), float(hz), code(bc_x),
+                       code(bc_y), code(bc_z), DIR[direction] if isinstance(direction, str)
+                       else int(direction))
 
 
 def problem_of(p):
@@ -297,6 +323,30 @@ def ext_apply_preconditioner(ctx, prob, phi, r, z):
     s = C.c_double()
     _check(load().ext_apply_preconditioner(ctx, C.byref(prob), _ptr(phi), _ptr(r), _ptr(z),
                                            C.byref(s)), "ext_apply_preconditioner")
+    return s.value
+
+
+def ext_solve3d(ctx, prob3, phi, f, out, check=True):
+    """Solve one three-dimensional extension (device arrays [nz][ny][nx]); returns the result as
+    a dict (status may be a non-OK code if check=False)."""
+    res = ExtResult()
+    rc = load().ext_solve3d(ctx, C.byref(prob3), _ptr(phi), _ptr(f), _ptr(out), C.byref(res))
+    if check:
+        _check(rc, "ext_solve3d")
+    d = res.as_dict()
+    d["rc"] = rc
+    return d
+
+
+def ext_apply_biharmonic3d(ctx, prob3, phi, p, q):
+    _check(load().ext_apply_biharmonic3d(ctx, C.byref(prob3), _ptr(phi), _ptr(p), _ptr(q)),
+           "ext_apply_biharmonic3d")
+
+
+def ext_apply_preconditioner3d(ctx, prob3, phi, r, z):
+    s = C.c_double()
+    _check(load().ext_apply_preconditioner3d(ctx, C.byref(prob3), _ptr(phi), _ptr(r), _ptr(z),
+                                             C.byref(s)), "ext_apply_preconditioner3d")
     return s.value
 
 

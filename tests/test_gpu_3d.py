@@ -1,0 +1,163 @@
+"""The three-dimensional extension on the GPU (Sec. 3 Example 2) against the 3-D FP64 oracle,
+through the C ABI: the operator bit for bit on integer inputs for every boundary triple, the
+preconditioner element by element, solves within the FP32 path's bound at rel-res 1e-8, the
+paper's Example 2, and the edge cases."""
+
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import biharmonic as ob
+from oracle import biharmonic3d as o3
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+BC_TRIPLES = list(itertools.product(ob.BCS, repeat=3))
+
+
+@pytest.fixture(scope="module")
+def ext():
+    from paper_1704_08897_gb300 import ext as e
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    e.load()
+    return e
+
+
+@pytest.fixture(scope="module")
+def ctx(ext):
+    c = ext.ext_create(ext.options("fp32", rtol=1e-8))
+    yield c
+    ext.ext_destroy(c)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _rand_phi(shape, seed, frac=0.35):
+    rng = np.random.default_rng(seed)
+    phi = rng.uniform(-1, 1, shape).astype(np.float32)
+    phi[rng.uniform(size=shape) > frac] = 1.0
+    return phi
+
+
+@pytest.mark.parametrize("bcs", BC_TRIPLES)
+@pytest.mark.parametrize("shape", [(6, 7, 9), (5, 10, 33)])
+def test_operator_bitwise_on_integers(ext, ctx, bcs, shape):
+    nz, ny, nx = shape
+    phi = _rand_phi(shape, 1)
+    unk = ~ob.known_mask(phi.astype(np.float64), "out")
+    p = np.random.default_rng(2).integers(-4, 5, shape).astype(np.float32)
+    want = o3.apply_squared_laplacian3_padded(np.where(unk, p, 0).astype(np.float64), *bcs)
+    want = np.where(unk, want, 0.0)
+    q = torch.empty(shape, device="cuda")
+    ext.ext_apply_biharmonic3d(ctx, ext.problem3(nx, ny, nz, *bcs, "out"), dev(phi), dev(p), q)
+    assert np.array_equal(q.cpu().numpy().astype(np.float64), want)
+
+
+@pytest.mark.parametrize("bcs", [("periodic",) * 3, ("symmetric",) * 3, ("dirichlet",) * 3,
+                                 ("symmetric", "periodic", "dirichlet"),
+                                 ("dirichlet", "symmetric", "periodic")])
+@pytest.mark.parametrize("shape", [(12, 10, 16), (17, 9, 20)])
+def test_preconditioner_matches_the_box_solve(ext, ctx, bcs, shape):
+    nz, ny, nx = shape
+    phi = _rand_phi(shape, 3)
+    unk = ~ob.known_mask(phi.astype(np.float64), "out")
+    r = np.random.default_rng(4).standard_normal(shape).astype(np.float32)
+    r[~unk] = 0
+    ref = np.where(unk, o3.poisson_squared_pinv3(r.astype(np.float64), bcs), 0.0)
+    z = torch.empty(shape, device="cuda")
+    scale = ext.ext_apply_preconditioner3d(ctx, ext.problem3(nx, ny, nz, *bcs, "out"), dev(phi), dev(r), z)
+    got = z.cpu().numpy().astype(np.float64) / scale
+    np.testing.assert_allclose(got, ref, rtol=0, atol=5e-6 * np.abs(ref).max())
+
+
+def _check(ext, ctx, phi, f, bcs, hs=(1.0, 1.0, 1.0), direction="out", tol=1e-6):
+    nz, ny, nx = phi.shape
+    out = torch.empty(phi.shape, device="cuda")
+    res = ext.ext_solve3d(ctx, ext.problem3(nx, ny, nz, *bcs, direction, *hs), dev(phi), dev(f), out)
+    o = out.cpu().numpy()
+    phi64, f64 = phi.astype(np.float64), f.astype(np.float64)
+    ref, _ = o3.extend3(phi64, f64, direction, bcs, hs, method="direct")
+    known = ob.known_mask(phi64, direction)
+    assert res["status"] == 0 and res["relres_true"] <= 1e-8, res
+    assert np.array_equal(o[known], f[known])
+    assert ob.max_rel_error(o, ref, known) <= tol
+    return res
+
+
+@pytest.mark.parametrize("bcs", [("periodic",) * 3, ("symmetric", "dirichlet", "periodic"),
+                                 ("dirichlet",) * 3, ("symmetric",) * 3])
+def test_solve_random_box_within_the_bound(ext, ctx, bcs):
+    shape = (10, 12, 14)
+    phi = _rand_phi(shape, 5, frac=0.5)
+    f = np.random.default_rng(6).standard_normal(shape).astype(np.float32)
+    _check(ext, ctx, phi, f, bcs)
+
+
+def test_solve_anisotropic_spacing(ext, ctx):
+    shape = (9, 11, 13)
+    phi = _rand_phi(shape, 7, frac=0.5)
+    f = np.random.default_rng(8).standard_normal(shape).astype(np.float32)
+    _check(ext, ctx, phi, f, ("periodic", "symmetric", "dirichlet"), hs=(1.0, 0.7, 1.3))
+
+
+def _peanut(n):
+    h = 2 * np.pi / n
+    xs = -np.pi + (np.arange(n) + 0.5) * h
+    Z, Y, X = np.meshgrid(xs, xs, xs, indexing="ij")
+    phi = np.minimum(np.sqrt((X - 0.8) ** 2 + Y ** 2 + Z ** 2) - 1,
+                     np.sqrt((X + 0.8) ** 2 + Y ** 2 + Z ** 2) - 1)
+    return phi.astype(np.float32), (np.cos(X) * np.sin(Y) * np.sin(np.pi / 4 - Z)).astype(np.float32), h
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_example2_peanut_against_the_oracle_and_the_paper(ext, n):
+    """Example 2 (periodic, extend out): at rel-res 1e-8 the answer is within 1e-6 of the oracle's
+    PCG answer at rel-res 1e-11; at the paper's rel-res 1e-6 the iteration count is within 20% of
+    the printed one (21 at 32^3, 46 at 64^3)."""
+    phi, f, h = _peanut(n)
+    bcs = ("periodic",) * 3
+    phi64, f64 = phi.astype(np.float64), f.astype(np.float64)
+    ref, _ = o3.extend3(phi64, f64, "out", bcs, (h, h, h), method="pcg", rtol=1e-11)
+    known = ob.known_mask(phi64, "out")
+    for rtol in (1e-8, 1e-6):
+        c = ext.ext_create(ext.options("fp32", rtol=rtol))
+        try:
+            out = torch.empty(phi.shape, device="cuda")
+            res = ext.ext_solve3d(c, ext.problem3(n, n, n, *bcs, "out", h), dev(phi), dev(f), out)
+        finally:
+            ext.ext_destroy(c)
+        assert res["status"] == 0 and res["relres_true"] <= rtol, res
+        if rtol == 1e-8:
+            assert ob.max_rel_error(out.cpu().numpy(), ref, known) <= 1e-6
+        else:
+            paper = {32: 21, 64: 46}[n]
+            assert abs(res["iters"] / paper - 1) <= 0.2, (res["iters"], paper)
+
+
+def test_edge_cases(ext, ctx):
+    shape = (6, 6, 6)
+    f = np.random.default_rng(9).standard_normal(shape).astype(np.float32)
+    out = torch.empty(shape, device="cuda")
+    # nothing known on a periodic box: not unique
+    phi = np.ones(shape, np.float32)
+    res = ext.ext_solve3d(ctx, ext.problem3(6, 6, 6, "periodic"), dev(phi), dev(f), out, check=False)
+    assert res["rc"] == ext.EXT_ENOKNOWN
+    # everything known: f back, bit for bit
+    phi = -np.ones(shape, np.float32)
+    res = ext.ext_solve3d(ctx, ext.problem3(6, 6, 6, "periodic"), dev(phi), dev(f), out)
+    assert res["status"] == 0 and np.array_equal(out.cpu().numpy(), f)
+    # NaN phi, a non-finite known value, a bad size, host arrays
+    phi = _rand_phi(shape, 10, frac=0.5)
+    bad = phi.copy()
+    bad[0, 0, 0] = np.nan
+    assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 6), dev(bad), dev(f), out, check=False)["rc"] == ext.EXT_EINVAL
+    g = f.copy()
+    g[ob.known_mask(phi.astype(np.float64), "out")] = np.inf
+    assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 6), dev(phi), dev(g), out, check=False)["rc"] == ext.EXT_EINVAL
+    assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 3), dev(phi), dev(f), out, check=False)["rc"] == ext.EXT_EINVAL
+    assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 6), phi, f, out, check=False)["rc"] == ext.EXT_EINVAL
