@@ -169,8 +169,11 @@ def algorithmic_cost(probs, kind):
         return sum(33 * p.nx * p.ny for p in probs), "byte"
     if kind == "update":    # read x, p, q, r; write x, r (8 bytes each)
         return sum(48 * p.nx * p.ny for p in probs), "byte"
-    if kind == "split":     # read r (8); write four 16-bit slices (8)
-        return sum(16 * p.nx * p.ny for p in probs), "byte"
+    if kind in ("split", "fold"):  # read r (8); write four 16-bit slices (8): unfolded / folded
+        f = kind == "fold"
+        return sum(16 * p.nx * p.ny for p in probs
+                   if (len(mirror_classes(p.nx, _fold_default())) > 1 or
+                       len(mirror_classes(p.ny, _fold_default())) > 1) == f), "byte"
     if kind == "unfold":    # read the classes' g (8), r (8), mask (1); write z (8); q (8) is read
         return sum(25 * p.nx * p.ny for p in probs), "byte"  # only for the flexible beta
     return None, None
@@ -228,7 +231,7 @@ class ClockSampler:
 # our implementation
 # ----------------------------------------------------------------------------------------------
 def kernel_hash(kind, prec="fp32"):
-    if kind.startswith("prec") or kind in ("split", "unfold") or kind.startswith("low"):
+    if kind.startswith("prec") or kind in ("split", "fold", "unfold") or kind.startswith("low"):
         f = "kernels_gemm_simt.cu" if prec == "fp32" else "kernels_gemm_tc.cu"
     else:
         f = "kernels_grid.cu"
@@ -454,7 +457,7 @@ def run_ours(args, rank, world):
             with open(PEAKS_FILE) as fh:
                 hbm_peak = json.load(fh)["hbm_gbs"]
             hbm = {}
-            for kd in ("stencil", "update", "split", "unfold"):
+            for kd in ("stencil", "update", "split", "fold", "unfold"):
                 amt, un = algorithmic_cost(probs, kd)
                 if kd in prof and prof[kd][1] and un == "byte":
                     gbs = amt / (prof[kd][0] / prof[kd][1] / 1e3) / 1e9

@@ -90,8 +90,9 @@ typedef struct {
   int32_t low_modes;       /* mixed modes: 1 = the lowest 32 x 32 modes of each transform
                               problem (those with the largest weights) come from six-slice
                               tensor-core products of about 48 bits instead of the four-slice
-                              stages: about 28% fewer iterations at more cost per iteration;
-                              0 = all modes from the four-slice stages (default)              */
+                              stages: 20-28% fewer iterations at more cost per iteration;
+                              0 = all modes from the four-slice stages; 2 = on for grids with a
+                              side of at least 2048 nodes, off otherwise (default)            */
   int64_t wait_cycles;     /* bound, in SM clock cycles, of every wait of a kernel for its own
                               tensor copies and tensor-core pipeline; a wait that runs out makes
                               the kernel drain what it issued and return, and the call returns
@@ -113,14 +114,15 @@ enum {
   EXT_KERNEL_PREC2 = 6,
   EXT_KERNEL_PREC3 = 7,
   EXT_KERNEL_OUTPUT = 8,         /* out = f on Omega, x elsewhere                            */
-  EXT_KERNEL_SPLIT = 9,          /* residual -> 16-bit integer slices (mixed modes)           */
+  EXT_KERNEL_SPLIT = 9,          /* residual -> 16-bit integer slices (mixed modes, unfolded)  */
   EXT_KERNEL_PREC_FINISH = 10,   /* per-slot r.z, z.q -> rho, beta                            */
   EXT_KERNEL_PQ_FINISH = 11,     /* per-slot p.q -> alpha                                     */
   EXT_KERNEL_LOW_FWD = 12,       /* low-mode correction: forward product, middle, inverse    */
   EXT_KERNEL_LOW_MID = 13,
   EXT_KERNEL_LOW_INV = 14,
   EXT_KERNEL_UNFOLD = 15,        /* mirror classes -> masked z, r.z, z.q (folded slots)       */
-  EXT_KERNEL_KINDS = 16
+  EXT_KERNEL_FOLD = 16,          /* residual -> mirror classes' slices (folded slots)          */
+  EXT_KERNEL_KINDS = 17
 };
 
 /* A three-dimensional problem (Sec. 3 Example 2: the equations of Sec. 2 in three dimensions;

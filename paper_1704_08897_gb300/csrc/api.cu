@@ -105,7 +105,7 @@ struct Workspace {
   SlotDesc* d_tcp = nullptr;
   WorkItem *d_fold = nullptr, *d_unfold = nullptr, *d_tcl = nullptr;
   int n_fold = 0, n_unfold = 0, n_tcl = 0;
-  WorkItem* d_prep = nullptr;  // grid tiles of the unfolded slots (their residual slicing)
+  WorkItem* d_prep = nullptr;  // residual slicing of the unfolded slots (32 rows x 128 columns)
   int n_prep = 0;
   const float** d_phis = nullptr;
   const float** d_fs = nullptr;
@@ -536,6 +536,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.mhx = (d.mir & 1) ? mirror_half(nx) : nx;
   d.mhy = (d.mir & 2) ? mirror_half(ny) : ny;
   d.n_fold_items = d.mir ? ((d.mhy + 7) / 8) * ((d.mhx + 127) / 128) : 0;
+  d.n_prep_items = (ctx->tc && !d.mir) ? ((ny + kStTileY - 1) / kStTileY) * ((nx + 127) / 128) : 0;
   d.n_unfold_tiles = d.mir ? ((d.mhx + 31) / 32) * ((d.mhy + 7) / 8) : 0;
   d.n_prec_parts = d.mir ? d.n_unfold_tiles : n_gm;
   const int n_part = std::max(std::max(d.n_st_tiles, d.n_vec_items), std::max(n_gm, d.n_unfold_tiles));
@@ -567,7 +568,10 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   };
   std::vector<TcLay> tl;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
-  const bool low = ctx->tc && ctx->opt.low_modes != 0;
+  // the low-mode correction: always (1), never (0), or for grids of side >= 2048 (2), where the
+  // four-slice stages dominate an iteration and the correction's iterations saved outweigh its cost
+  const bool low = ctx->tc && (ctx->opt.low_modes == 1 ||
+                               (ctx->opt.low_modes == 2 && std::max(nx, ny) >= kLowAutoSide));
   if (ctx->tc) {
     for (int cy = 0; cy < ((d.mir & 2) ? 2 : 1); ++cy)
       for (int cx = 0; cx < ((d.mir & 1) ? 2 : 1); ++cx) {
@@ -837,7 +841,7 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
       for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
       for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
       if (!d.mir)
-        for (int t = 0; t < d.n_st_tiles; ++t) prep.push_back({i, t});
+        for (int t = 0; t < d.n_prep_items; ++t) prep.push_back({i, t});
     } else {
       for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
     }
@@ -1027,10 +1031,11 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
   LaunchCfg g = cfg_of(ctx, W, 2);
   if (ctx->tc) {
     // residual slices: unfolded slots directly, folded slots per mirror class
-    timed(ctx, EXT_KERNEL_SPLIT, [&] {
-      if (W->n_prep > 0) launch_prec_tc_prepare(cfg_of(ctx, W, 10), mode, ctx->split);
-      if (W->n_fold > 0) launch_tc_fold(cfg_of(ctx, W, 7), mode, ctx->split);
-    }, g.stream);
+    if (W->n_prep > 0)
+      timed(ctx, EXT_KERNEL_SPLIT, [&] { launch_prec_tc_prepare(cfg_of(ctx, W, 10), mode, ctx->split); },
+            g.stream);
+    if (W->n_fold > 0)
+      timed(ctx, EXT_KERNEL_FOLD, [&] { launch_tc_fold(cfg_of(ctx, W, 7), mode, ctx->split); }, g.stream);
     // the transform kernels run over the tensor-core problems
     g.slots = W->d_tcp;
     g.grid = std::max(1, std::min(W->n_gm, ctx->sm_count));
@@ -1391,7 +1396,7 @@ void ext_options_default(ext_options* o) {
   o->max_slots = 256;
   o->autotune = 1;
   o->tile_y = 32;
-  o->low_modes = 0;
+  o->low_modes = 2;
   o->fold = 1;
 }
 
@@ -1962,7 +1967,7 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
       for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
       for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
       if (!d.mir)
-        for (int t = 0; t < d.n_st_tiles; ++t) prep.push_back({i, t});
+        for (int t = 0; t < d.n_prep_items; ++t) prep.push_back({i, t});
     } else {
       for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
     }

@@ -22,6 +22,7 @@ constexpr int kStWinX = kStTileX + 8;
 constexpr int kStWinY = kStTileY + 4;
 constexpr int kStMaps = 7;          // stencil tensor maps per slot
 constexpr int kLowM = 32;           // low modes per axis computed in high precision
+constexpr int kLowAutoSide = 2048;  // low_modes = 2: grids with a side of at least this many nodes
 constexpr int kLowNS = 6;           // integer slices per operand of the low-mode products
 constexpr int kLowK3 = 64;          // k extent of the inverse low-mode product (32 modes, zero-padded)
 constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels
@@ -143,6 +144,7 @@ struct SlotDesc {
   int mir;           // slot: bit 0 = x folded, bit 1 = y folded (0: the slot is its own problem)
   int mhx, mhy;      // slot: class nodes along x, y (ceil(n/2) on a folded axis, else n)
   int n_fold_items;  // slot: items of the fold kernel (8 class rows x 128 columns)
+  int n_prep_items;  // slot with no folded axis: items of its residual slicing (32 rows x 128)
   int n_unfold_tiles;// slot: tiles of the unfold kernel (32 x 8 class nodes)
   int n_prec_parts;  // slot: r.z, z.q partials the preconditioner leaves (stage-3 or unfold tiles)
   int mir_out;       // class problem: stage 3 writes the class result g to z, z_lo ([ny][nx])

@@ -687,9 +687,8 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
   if (threadIdx.x == 0 && ctl->abort_flag) atomicExch(err, 1);
 }
 
-// Residual -> slices of the first stage's A operand.  One warp per (row, KC-column block); the
-// work list is the stencil's (64 x 32 tiles): a tile starting at a multiple of KC takes the KC
-// columns of its block, the others (if KC > 64) have nothing to do.
+// Residual -> slices of the first stage's A operand (slots with no folded axis).  One item per
+// 32 rows and KC columns; one warp per four of the rows, all four loaded before any is sliced.
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
@@ -701,10 +700,9 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
     const SlotDesc& S = slots[it.slot];
     SlotScalars* sc = S.sc;
     if (!slot_runs(sc, mode) || S.mir) continue;  // folded slots: k_tc_fold
-    const int tx = (S.nx + kStTileX - 1) / kStTileX;
-    const int x0 = (it.tile % tx) * kStTileX;
+    const int tx = (S.nx + KC - 1) / KC;
+    const int x0 = (it.tile % tx) * KC;
     const int y0 = (it.tile / tx) * kStTileY;
-    if (x0 % KC != 0) continue;
     const int kblocks = S.nxp / KC;
     const size_t plane = static_cast<size_t>(S.nyp) * S.nxp;
     uint16_t* out = static_cast<uint16_t*>(S.tc_r);
@@ -775,7 +773,7 @@ __device__ __forceinline__ f2 df_neg(f2 a) { return f2{-a.hi, -a.lo}; }
 
 // One warp per (class row y, 128 class columns); lane pairs (x, x+1) at x = 64 k + 2 lane.
 template <bool BF16>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 k_tc_fold(const SlotDesc* __restrict__ slots, const SlotDesc* __restrict__ tcp,
           const WorkItem* __restrict__ items, const int* __restrict__ n_items, int mode) {
   const int total = *n_items;

@@ -35,7 +35,7 @@ EXPORTED = ["ext_options_default", "ext_create", "ext_solve", "ext_solve_batch",
             "ext_apply_preconditioner3d"]
 KERNEL_KINDS = ["setup", "stencil", "update", "true_residual", "prec_stage0", "prec_stage1",
                 "prec_stage2", "prec_stage3", "output", "split", "prec_finish",
-                "pq_finish", "low_fwd", "low_mid", "low_inv", "unfold"]
+                "pq_finish", "low_fwd", "low_mid", "low_inv", "unfold", "fold"]
 
 
 class ExtProblem(C.Structure):

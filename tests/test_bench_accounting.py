@@ -18,7 +18,11 @@ def test_algorithmic_cost_per_kernel_kind():
     # double-float CG vectors: 8 bytes per node per vector
     assert bench.algorithmic_cost(probs, "stencil") == (33 * nodes, "byte")
     assert bench.algorithmic_cost(probs, "update") == (48 * nodes, "byte")
+    # 64 and 128 do not fold: all slicing is the unfolded kind
     assert bench.algorithmic_cost(probs, "split") == (16 * nodes, "byte")
+    assert bench.algorithmic_cost(probs, "fold") == (0, "byte")
+    big = [synth.wobbly(256, 1)]
+    assert bench.algorithmic_cost(big, "fold") == (16 * 256 * 256, "byte")
     assert bench.algorithmic_cost(probs, "unfold") == (25 * nodes, "byte")
     # stage s contracts one axis: 2 nx ny n_axis flop, x for stages 0 and 2, y for 1 and 3
     p = synth.wobbly(128, 0)
