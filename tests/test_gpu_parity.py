@@ -441,6 +441,30 @@ def test_folded_preconditioner_matches_fast_poisson(ext, fold_ctxs, bc_x, bc_y, 
         assert np.all(got[-1][known] == 0)
 
 
+@pytest.mark.parametrize("bc", ob.BCS)
+def test_folded_solve_on_odd_sides(ext, bc):
+    """A grid with odd sides on both folded axes (middle nodes in the even classes) solves to
+    rel-res 1e-8 within the mixed path's bound of the direct solve, folded and not."""
+    nx, ny = 255, 193
+    X, Y = np.meshgrid(np.linspace(-1, 1, nx), np.linspace(-1, 1, ny))
+    phi = (np.hypot(X - 0.1, Y + 0.05) - 0.45 - 0.05 * np.cos(5 * np.arctan2(Y, X))).astype(np.float32)
+    f = (np.cos(3 * X + 1) * np.sin(2 * Y) + 0.3 * X * Y).astype(np.float32)
+    phi64, f64 = phi.astype(np.float64), f.astype(np.float64)
+    ref, _ = ob.extend(phi64, f64, "out", bc, bc, method="direct")
+    known = ob.known_mask(phi64, "out")
+    for fold in (1, 0):
+        c = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, maxit=40 * nx, fold=fold))
+        try:
+            out64 = torch.empty((ny, nx), device="cuda", dtype=torch.float64)
+            res = ext.ext_solve_f64(c, ext.problem(nx, ny, bc, bc, "out"), dev(phi), dev(f), out64)
+        finally:
+            ext.ext_destroy(c)
+        o = out64.cpu().numpy()
+        rr = ob.true_relative_residual(o, phi64, f64, "out", bc, bc)
+        assert res["status"] == 0 and rr <= 1.05e-8, (bc, fold, rr, res)
+        assert ob.max_rel_error(o, ref, known) <= TOL_MIXED
+
+
 @pytest.mark.parametrize("maker", [lambda: synth.circle(64), lambda: synth.wobbly(192, 3),
                                    lambda: synth.star(256, "periodic", "in")])
 def test_mixed_solve_validity_and_uniqueness(ext, mixed, maker):
