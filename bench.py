@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=48,
                     help="batch: requests of the serving leg (config-4 shape); 0 skips it")
-    ap.add_argument("--peanut3d", default="64,128",
+    ap.add_argument("--peanut3d", default="64,128,256",
                     help="batch: sides of the three-dimensional Example 2 leg ('' skips it)")
     ap.add_argument("--low-modes", type=int, default=None,
                     help="low-mode correction of the mixed preconditioner: 1 on, 0 off (library default)")
@@ -540,11 +540,12 @@ def error_vs_oracle(probs, answers, refs, prec, at="rel-res 1e-8, answers of the
 PAPER_EXAMPLE2 = {32: (21, 1.08e-01), 64: (46, 3.42e-02), 128: (112, 1.07e-02), 256: (276, 2.84e-03)}
 
 
-def peanut3d_leg(sides=(64, 128)):
+def peanut3d_leg(sides=(64, 128, 256)):
     """The three-dimensional extension (Sec. 3 Example 2): the peanut on [-pi, pi]^3, periodic,
-    extend out, through ext_solve3d.  Per side: time and iterations at rel-res 1e-8, the
-    iterations at the paper's rel-res 1e-6 beside the printed ones, and the max error within one
-    grid cell of the interface against the analytic field beside the printed error."""
+    extend out, through ext_solve3d, on the FP32 path (CUDA-core transforms) and, for sides that
+    are multiples of 128, the mixed path (tensor-core transforms).  Per side and path: time and
+    iterations at rel-res 1e-8 and at the paper's 1e-6 (beside the printed iterations), and the
+    max error within one grid cell of the interface against the analytic field."""
     import numpy as np
     import torch
     from paper_1704_08897_gb300 import ext
@@ -562,25 +563,27 @@ def peanut3d_leg(sides=(64, 128)):
         o = torch.empty_like(dphi)
         prob = ext.problem3(n, n, n, "periodic", "periodic", "periodic", "out", h)
         row = {}
-        for rtol in (1e-8, 1e-6):
-            c = ext.ext_create(_options("fp32", rtol=rtol))
-            try:
-                ext.ext_solve3d(c, prob, dphi, dfv, o)            # warm-up (plans, code)
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                res = ext.ext_solve3d(c, prob, dphi, dfv, o)
-                torch.cuda.synchronize()
-                dt = time.perf_counter() - t0
-            finally:
-                ext.ext_destroy(c)
-            err = float(np.abs(o.cpu().numpy() - f)[band].max())
-            row[f"rtol_{rtol:g}"] = {"iterations": res["iters"], "s_per_solve": round(dt, 4),
-                                     "relres_true": res["relres_true"], "error_1cell": err}
+        for prec in ("fp32", "mixed_bf16") if n % 128 == 0 else ("fp32",):
+            for rtol in (1e-8, 1e-6):
+                c = ext.ext_create(_options(prec, rtol=rtol))
+                try:
+                    if rtol == 1e-8:
+                        ext.ext_solve3d(c, prob, dphi, dfv, o)    # warm-up (plans, code)
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    res = ext.ext_solve3d(c, prob, dphi, dfv, o)
+                    torch.cuda.synchronize()
+                    dt = time.perf_counter() - t0
+                finally:
+                    ext.ext_destroy(c)
+                err = float(np.abs(o.cpu().numpy() - f)[band].max())
+                row[f"{prec}_rtol_{rtol:g}"] = {"iterations": res["iters"], "s_per_solve": round(dt, 4),
+                                                "relres_true": res["relres_true"], "error_1cell": err}
         if n in PAPER_EXAMPLE2:
             row["paper"] = {"iterations": PAPER_EXAMPLE2[n][0], "error": PAPER_EXAMPLE2[n][1]}
-        # the six dense transform products dominate: 2 n^4 multiply-adds each per application
-        it = row["rtol_1e-08"]["iterations"]
-        row["transform_fma_per_s"] = (6 * 2 * n ** 4 * (it + 1)) / row["rtol_1e-08"]["s_per_solve"]
+        # the six dense transform products dominate the FP32 path: 2 n^4 multiply-adds each
+        it = row["fp32_rtol_1e-08"]["iterations"]
+        row["fp32_transform_fma_per_s"] = (6 * 2 * n ** 4 * (it + 1)) / row["fp32_rtol_1e-08"]["s_per_solve"]
         out["sides"][str(n)] = row
     return out
 

@@ -1582,6 +1582,8 @@ static int validate_problem3(const ext_problem3* p) {
 }
 
 // The arguments of the 3-D kernels: the axis plans (built or found in the context's cache).
+static int tc3_build(ext_ctx* ctx, const Solve3Args& a, const Tc3Io& io, Tc3& t);
+
 static int args3(ext_ctx* ctx, const ext_problem3* p, Solve3Args& a) {
   std::lock_guard<std::recursive_mutex> plk(ctx->plan_mu);
   a.nx = p->nx;
@@ -1609,6 +1611,176 @@ static int args3(ext_ctx* ctx, const ext_problem3* p, Solve3Args& a) {
   a.true_res_every = ctx->opt.true_res_every;
   a.replace_factor = ctx->opt.replace_factor;
   a.stream = ctx->stream;
+  if (ctx->tc && p->nx % 128 == 0 && p->ny % 128 == 0 && p->nz % 128 == 0)
+    a.tc_build = [ctx, &a](const Tc3Io& io, Tc3& t) { return tc3_build(ctx, a, io, t); };
+  return EXT_OK;
+}
+
+// The 3-D transforms on the tensor cores (mixed modes, every side a multiple of 128).  Each of
+// the six products contracts the contiguous axis of its operand and writes its result with that
+// axis first, exactly the form of the 2-D stage kernels, so every product is one launch of
+// k_prec_tc over a descriptor whose dimensions are the box's: with X, Y, Z the sides, the
+// forward products are [Z Y][X] x Qx^T -> [X][Z Y], [X Z][Y] x Qy^T -> [Y][X Z] and
+// [Y X][Z] x Qz^T -> [Z][Y X] (stage-1 form: the weights, with lam_x + lam_y of the rows folded
+// into one array), the inverse ones the same with Q, the last in stage-3 form (mask, z, r.z).
+// With every side a multiple of 128, each output's 128-blocks along its rows are exactly the
+// next product's k-blocks, so the exponents carry over unchanged.
+static int tc3_build(ext_ctx* ctx, const Solve3Args& a, const Tc3Io& io, Tc3& t) {
+  const int X = a.nx, Y = a.ny, Z = a.nz;
+  const size_t N3 = (size_t)X * Y * Z;
+  const int NS = tc_planes(ctx->split);
+  const bool bf = ctx->split == 1;
+  PlanDev* P[3];
+  {
+    std::lock_guard<std::recursive_mutex> plk(ctx->plan_mu);
+    const int n[3] = {X, Y, Z};
+    for (int ax = 0; ax < 3; ++ax) {
+      int rc = get_plan(ctx, n[ax], a.bc[ax], -1, &P[ax]);
+      if (!rc) rc = ensure_tc_plan(ctx, P[ax]);
+      if (rc) return rc;
+    }
+  }
+  auto take = [&](size_t bytes) -> void* {
+    void* v = nullptr;
+    if (cudaMalloc(&v, bytes ? bytes : 1) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    t.owned.push_back(v);
+    return v;
+  };
+  void* S0 = take(2 * (size_t)NS * N3);
+  void* SA = take(2 * (size_t)NS * N3);
+  void* SB = take(2 * (size_t)NS * N3);
+  int8_t* E0 = (int8_t*)take(N3 / 128);
+  int8_t* EA = (int8_t*)take(N3 / 128);
+  int8_t* EB = (int8_t*)take(N3 / 128);
+  const int tiles3 = ((Y * X) / 128) * (Z / 64);
+  double* part = (double*)take(sizeof(double) * 4 * (size_t)tiles3);
+  float* lam = (float*)take(sizeof(float) * ((size_t)Y * X + Z));
+  SlotScalars* sc = (SlotScalars*)take(sizeof(SlotScalars));
+  void* maps = take(6 * 8 * sizeof(CUtensorMap));
+  SlotDesc* descs = (SlotDesc*)take(7 * sizeof(SlotDesc));
+  if (!S0 || !SA || !SB || !E0 || !EA || !EB || !part || !lam || !sc || !maps || !descs) {
+    g_last_error = "cudaMalloc of the 3-D tensor-core workspace failed";
+    return EXT_ENOMEM;
+  }
+  BX_CUDA(cudaMemset(S0, 0, 2 * (size_t)NS * N3));
+  BX_CUDA(cudaMemset(E0, 0, N3 / 128));
+  SlotScalars hsc{};
+  hsc.active = 1;
+  hsc.need_prec = 1;
+  BX_CUDA(cudaMemcpy(sc, &hsc, sizeof(hsc), cudaMemcpyHostToDevice));
+  // eigenvalues scaled like the stencil (largest 1/h^2 = 1): lam_y + lam_x per row of the
+  // weighted product ([ky][kx] flattened), lam_z per column; wnorm = (smallest nonzero sum)^2
+  const double c[3] = {1.0 / (a.h[0] * a.h[0]), 1.0 / (a.h[1] * a.h[1]), 1.0 / (a.h[2] * a.h[2])};
+  const double cm = std::max(c[0], std::max(c[1], c[2]));
+  std::vector<float> lh((size_t)Y * X + Z);
+  double lo0[3], lo1[3];
+  const int nn[3] = {X, Y, Z};
+  std::vector<float> la[3];
+  for (int ax = 0; ax < 3; ++ax) {
+    lo0[ax] = lo1[ax] = 1e300;
+    la[ax].resize(nn[ax]);
+    for (int k = 0; k < nn[ax]; ++k) {
+      la[ax][k] = (float)(P[ax]->lam[k] * c[ax] / cm);
+      lo0[ax] = std::min(lo0[ax], (double)la[ax][k]);
+      if (la[ax][k] > 0) lo1[ax] = std::min(lo1[ax], (double)la[ax][k]);
+    }
+  }
+  for (int ky = 0; ky < Y; ++ky)
+    for (int kx = 0; kx < X; ++kx) lh[(size_t)ky * X + kx] = la[1][ky] + la[0][kx];
+  for (int kz = 0; kz < Z; ++kz) lh[(size_t)Y * X + kz] = la[2][kz];
+  BX_CUDA(cudaMemcpy(lam, lh.data(), sizeof(float) * lh.size(), cudaMemcpyHostToDevice));
+  double smin = lo0[0] + lo0[1] + lo0[2];
+  if (!(smin > 0))
+    smin = std::min(lo1[0] + lo0[1] + lo0[2], std::min(lo0[0] + lo1[1] + lo0[2], lo0[0] + lo0[1] + lo1[2]));
+  // descriptors
+  SlotDesc d[7];
+  for (int k = 0; k < 7; ++k) {
+    d[k] = SlotDesc{};
+    d[k].sc = sc;
+  }
+  const uint16_t* q[3] = {(const uint16_t*)P[0]->tc, (const uint16_t*)P[1]->tc, (const uint16_t*)P[2]->tc};
+  const size_t pl[3] = {(size_t)X * X, (size_t)Y * Y, (size_t)Z * Z};
+  auto QT = [&](int ax) { return (void*)(q[ax] + NS * pl[ax]); };  // Q^T planes follow the Q planes
+  auto QQ = [&](int ax) { return (void*)q[ax]; };
+  CUtensorMap m[6][8];
+  memset(m, 0, sizeof(m));
+  // [0]: residual slicing, rows (z, y), columns x
+  d[0].nx = X; d[0].ny = Z * Y; d[0].nxp = X; d[0].nyp = Z * Y;
+  d[0].r = const_cast<float*>(io.rh); d[0].r_lo = const_cast<float*>(io.rl);
+  d[0].tc_r = S0; d[0].tc_e[0] = E0;
+  // [1] F1 (stage-0 form): A = r slices [Z Y][X], B = Qx^T -> SA [X][Z Y]
+  d[1].nyp = Z * Y; d[1].nxp = X; d[1].nx = X; d[1].ny = Z * Y;
+  int rc = make_tmap(&m[0][0], S0, bf, X, (uint64_t)NS * Z * Y, 128);
+  if (!rc) rc = make_tmap(&m[0][4], QT(0), bf, X, (uint64_t)NS * X, 64);
+  d[1].tc_e[0] = E0; d[1].tc_eb[0] = plan_exps(P[0], 1); d[1].tc_t1 = SA; d[1].tc_e[1] = EA;
+  // [2] F2 (stage-0 form): A = SA as [X Z][Y], B = Qy^T -> SB [Y][X Z]
+  d[2].nyp = X * Z; d[2].nxp = Y; d[2].nx = Y; d[2].ny = X * Z;
+  if (!rc) rc = make_tmap(&m[1][0], SA, bf, Y, (uint64_t)NS * X * Z, 128);
+  if (!rc) rc = make_tmap(&m[1][4], QT(1), bf, Y, (uint64_t)NS * Y, 64);
+  d[2].tc_e[0] = EA; d[2].tc_eb[0] = plan_exps(P[1], 1); d[2].tc_t1 = SB; d[2].tc_e[1] = EB;
+  // [3] F3 (stage-1 form, weights): A = SB as [Y X][Z], B = Qz^T -> SA [Z][Y X]
+  d[3].nxp = Y * X; d[3].nyp = Z; d[3].nx = Y * X; d[3].ny = Z;
+  if (!rc) rc = make_tmap(&m[2][1], SB, bf, Z, (uint64_t)NS * Y * X, 128);
+  if (!rc) rc = make_tmap(&m[2][5], QT(2), bf, Z, (uint64_t)NS * Z, 64);
+  d[3].tc_e[1] = EB; d[3].tc_eb[1] = plan_exps(P[2], 1); d[3].tc_t2 = SA; d[3].tc_e[2] = EA;
+  d[3].lamx = lam; d[3].lamy = lam + (size_t)Y * X; d[3].wnorm = (float)(smin * smin);
+  // [4] I1 (stage-2 form): A = SA as [Z Y][X], B = Qx -> SB [X][Z Y]
+  d[4].nyp = Z * Y; d[4].nxp = X; d[4].nx = X; d[4].ny = Z * Y;
+  if (!rc) rc = make_tmap(&m[3][2], SA, bf, X, (uint64_t)NS * Z * Y, 128);
+  if (!rc) rc = make_tmap(&m[3][6], QQ(0), bf, X, (uint64_t)NS * X, 64);
+  d[4].tc_e[2] = EA; d[4].tc_eb[2] = plan_exps(P[0], 0); d[4].tc_t3 = SB; d[4].tc_e[3] = EB;
+  // [5] I2 (stage-2 form): A = SB as [X Z][Y], B = Qy -> SA [Y][X Z]
+  d[5].nyp = X * Z; d[5].nxp = Y; d[5].nx = Y; d[5].ny = X * Z;
+  if (!rc) rc = make_tmap(&m[4][2], SB, bf, Y, (uint64_t)NS * X * Z, 128);
+  if (!rc) rc = make_tmap(&m[4][6], QQ(1), bf, Y, (uint64_t)NS * Y, 64);
+  d[5].tc_e[2] = EB; d[5].tc_eb[2] = plan_exps(P[1], 0); d[5].tc_t3 = SA; d[5].tc_e[3] = EA;
+  // [6] I3 (stage-3 form): A = SA as [Y X][Z], B = Qz -> z[Z][Y X] masked, r.z per tile
+  d[6].nxp = Y * X; d[6].nyp = Z; d[6].nx = Y * X; d[6].ny = Z;
+  if (!rc) rc = make_tmap(&m[5][3], SA, bf, Z, (uint64_t)NS * Y * X, 128);
+  if (!rc) rc = make_tmap(&m[5][7], QQ(2), bf, Z, (uint64_t)NS * Z, 64);
+  if (rc) return rc;
+  d[6].tc_e[3] = EA; d[6].tc_eb[3] = plan_exps(P[2], 0);
+  d[6].r = const_cast<float*>(io.rh); d[6].r_lo = const_cast<float*>(io.rl);
+  d[6].q = const_cast<float*>(io.qh); d[6].q_lo = const_cast<float*>(io.ql);
+  d[6].z = io.zh; d[6].z_lo = io.zl; d[6].mask = const_cast<uint8_t*>(io.mask); d[6].part = part;
+  BX_CUDA(cudaMemcpy(maps, m, sizeof(m), cudaMemcpyHostToDevice));
+  for (int k = 1; k < 7; ++k) d[k].tmaps = (const char*)maps + (size_t)(k - 1) * 8 * sizeof(CUtensorMap);
+  BX_CUDA(cudaMemcpy(descs, d, sizeof(d), cudaMemcpyHostToDevice));
+  // work items: [0] 32 rows x 128 columns; the products tiles of 128 x 64 (M x N)
+  static const int kForm[7] = {-1, 0, 0, 1, 2, 2, 3};
+  std::vector<WorkItem> items[7];
+  for (int tt = 0; tt < ((Z * Y) / 32) * (X / 128); ++tt) items[0].push_back({0, tt});
+  for (int k = 1; k < 7; ++k) {
+    const bool mrows_y = kForm[k] == 0 || kForm[k] == 2;  // M = nyp in the stage-0/2 forms
+    const int M = mrows_y ? d[k].nyp : d[k].nxp, N = mrows_y ? d[k].nxp : d[k].nyp;
+    for (int tt = 0; tt < (M / 128) * (N / 64); ++tt) items[k].push_back({k, tt});
+  }
+  int counts[7];
+  for (int k = 0; k < 7; ++k) {
+    WorkItem* di = (WorkItem*)take(sizeof(WorkItem) * items[k].size());
+    if (!di) {
+      g_last_error = "cudaMalloc of the 3-D tensor-core work lists failed";
+      return EXT_ENOMEM;
+    }
+    BX_CUDA(cudaMemcpy(di, items[k].data(), sizeof(WorkItem) * items[k].size(), cudaMemcpyHostToDevice));
+    t.d_items[k] = di;
+    t.n_items[k] = counts[k] = (int)items[k].size();
+  }
+  int* dc = (int*)take(sizeof(counts));
+  if (!dc) return EXT_ENOMEM;
+  BX_CUDA(cudaMemcpy(dc, counts, sizeof(counts), cudaMemcpyHostToDevice));
+  t.d_counts = dc;
+  t.d_descs = descs;
+  t.split = ctx->split;
+  t.d_err = ctx->d_err;
+  t.wait_cycles = ctx->opt.wait_cycles;
+  t.sm_count = ctx->sm_count;
+  t.part = part;
+  t.n_tiles3 = counts[6];
+  t.on = true;
   return EXT_OK;
 }
 

@@ -3,7 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <functional>
 #include <string>
+#include <vector>
 
 #include "../../include/biharm_ext.h"
 #include "common.cuh"
@@ -70,6 +72,30 @@ void launch_unfold(const LaunchCfg& c, int mode);
 int tc_block();
 bool tc_supported();
 
+// Tensor-core preconditioner of the 3-D path (mixed modes, every side a multiple of 128): the
+// residual slicing and the six transform products as launches of the 2-D kernels over prepared
+// descriptors (one per launch, [0] = slicing, [1..6] = products), built by the context.
+struct Tc3 {
+  bool on = false;
+  SlotDesc* d_descs = nullptr;
+  const WorkItem* d_items[7] = {};
+  const int* d_counts = nullptr;  // [7]
+  int n_items[7] = {};
+  int split = 0;
+  int* d_err = nullptr;
+  long long wait_cycles = 0;
+  int sm_count = 148;
+  double* part = nullptr;         // the last product's tile partials (4 doubles per tile)
+  int n_tiles3 = 0;
+  std::vector<void*> owned;       // device allocations, freed by the solve
+};
+// the solve's vectors the descriptors refer to
+struct Tc3Io {
+  const float *rh, *rl, *qh, *ql;
+  float *zh, *zl;
+  const uint8_t* mask;
+};
+
 // three-dimensional extension (solve3d.cu): the CUDA-core double-float path, host-driven CG
 struct Solve3Args {
   int nx, ny, nz;
@@ -86,6 +112,8 @@ struct Solve3Args {
   double replace_factor;
   cudaStream_t stream;
   long long* launches;     // incremented by every kernel launch (host counter)
+  // builds the tensor-core preconditioner for the given vectors (empty: CUDA-core transforms)
+  std::function<int(const Tc3Io&, Tc3&)> tc_build;
 };
 int solve3d_run(const Solve3Args& a, const float* phi, const float* f, float* out, ext_result* res,
                 std::string* err);

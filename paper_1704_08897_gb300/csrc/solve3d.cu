@@ -260,12 +260,13 @@ k3_output(size_t n, const float* __restrict__ xh, const float* __restrict__ xl, 
     out[i] = mask[i] ? static_cast<float>(ldexp(static_cast<double>(xh[i]) + static_cast<double>(xl[i]), e)) : f[i];
 }
 
-// Sum of partials in index order by one block (thread t adds t, t + 256, ...; then the block).
+// Sum of partials in index order by one block (thread t adds t, t + 256, ...; then the block);
+// entry i is part[i * stride].
 __global__ void __launch_bounds__(kT)
-k3_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+k3_sum(const double* __restrict__ part, int n, double* __restrict__ out, int stride = 1) {
   __shared__ double sh[kT / 32];
   double v = 0.0;
-  for (int i = threadIdx.x; i < n; i += kT) v += part[i];
+  for (int i = threadIdx.x; i < n; i += kT) v += part[static_cast<size_t>(i) * stride];
   const double s = block_sum_d(v, sh);
   if (threadIdx.x == 0) *out = s;
 }
@@ -396,8 +397,10 @@ struct State3 {
   float *th = nullptr, *tl = nullptr, *lam = nullptr;
   unsigned long long* counts = nullptr;
   std::vector<void*> owned;
+  Tc3 tc;  // the tensor-core preconditioner, when built
   ~State3() {
     for (void* p : owned) cudaFree(p);
+    for (void* p : tc.owned) cudaFree(p);
   }
   template <class T>
   int take(T** p, size_t count, std::string* err) {
@@ -497,6 +500,32 @@ void precondition(const Solve3Args& a, const State3& s, float wnorm, const float
                   float* zh, float* zl, bool with_dot) {
   const int nx = a.nx, ny = a.ny, nz = a.nz;
   cudaStream_t st = a.stream;
+  if (s.tc.on) {
+    // the tensor-core path: its descriptors hold r, q, z and the mask of this solve
+    const Tc3& t = s.tc;
+    LaunchCfg c;
+    c.slots = t.d_descs;
+    c.stream = st;
+    c.wait_cycles = t.wait_cycles;
+    c.items = t.d_items[0];
+    c.n_items = t.d_counts;
+    c.grid = std::max(1, std::min(t.n_items[0], t.sm_count * 8));
+    launch_prec_tc_prepare(c, 2, t.split);
+    ++*a.launches;
+    static const int kForm[7] = {-1, 0, 0, 1, 2, 2, 3};
+    for (int k = 1; k < 7; ++k) {
+      c.items = t.d_items[k];
+      c.n_items = t.d_counts + k;
+      c.grid = std::max(1, std::min(t.n_items[k], t.sm_count));
+      launch_prec_tc(c, kForm[k], 2, t.split, t.d_err);
+      ++*a.launches;
+    }
+    if (with_dot) {
+      k3_sum<<<1, kT, 0, st>>>(t.part + 2, t.n_tiles3, s.scal + 1, 4);
+      ++*a.launches;
+    }
+    return;
+  }
   auto gemm = [&](const float* A, const float* Al, int M, int K, const float* B, int ldb, int N, float* o, float* ol) {
     const dim3 grid((M + GM - 1) / GM, (N + GN - 1) / GN);
     k3_gemm<<<grid, kT, 0, st>>>(A, Al, M, K, B, ldb, N, o, ol);
@@ -557,6 +586,10 @@ int solve3d_run(const Solve3Args& a, const float* phi, const float* f, float* ou
   State3 s;
   int rc = alloc_state(a, s, true, err);
   if (rc) return rc;
+  if (a.tc_build) {
+    rc = a.tc_build(Tc3Io{s.rh, s.rl, s.qh, s.ql, s.zh, s.zl, s.mask}, s.tc);
+    if (rc) return rc;
+  }
   const Grid3 G = grid_of(a);
   float wnorm = 1.f;
   rc = upload_eigen(a, G, s, &wnorm, err);
@@ -709,6 +742,17 @@ int solve3d_run(const Solve3Args& a, const float* phi, const float* f, float* ou
   ++*a.launches;
   BX3(cudaGetLastError());
   BX3(cudaStreamSynchronize(st));
+  if (s.tc.on) {
+    // a bounded wait of the tensor-core kernels that ran out
+    int flag = 0;
+    BX3(cudaMemcpy(&flag, s.tc.d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      BX3(cudaMemset(s.tc.d_err, 0, sizeof(int)));
+      *err = "a bounded device wait (tensor-core pipeline) ran out";
+      res->status = EXT_ETIMEOUT;
+      return EXT_ETIMEOUT;
+    }
+  }
   res->status = status;
   return status == EXT_OK ? EXT_OK : status;
 }
@@ -747,6 +791,13 @@ int apply3d_preconditioner(const Solve3Args& a, const float* phi, const float* r
   // the masked copy goes to d0 reinterpreted as two float planes
   float* rh = reinterpret_cast<float*>(s.d0);
   float* rl = rh + s.n;
+  if (a.tc_build) {
+    // z.q of the last product's epilogue is not used here: q = zeros
+    BX3(cudaMemsetAsync(s.uh, 0, 4 * s.n, a.stream));
+    BX3(cudaMemsetAsync(s.ul, 0, 4 * s.n, a.stream));
+    rc = a.tc_build(Tc3Io{rh, rl, s.uh, s.ul, s.zh, s.zl, s.mask}, s.tc);
+    if (rc) return rc;
+  }
   k3_load_masked<<<s.vec_blocks, kT, 0, a.stream>>>(s.n, r, s.mask, rh, rl);
   ++*a.launches;
   precondition(a, s, wnorm, rh, rl, s.zh, s.zl, false);

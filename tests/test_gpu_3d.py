@@ -161,3 +161,58 @@ def test_edge_cases(ext, ctx):
     assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 6), dev(phi), dev(g), out, check=False)["rc"] == ext.EXT_EINVAL
     assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 3), dev(phi), dev(f), out, check=False)["rc"] == ext.EXT_EINVAL
     assert ext.ext_solve3d(ctx, ext.problem3(6, 6, 6), phi, f, out, check=False)["rc"] == ext.EXT_EINVAL
+
+
+# ----------------------------------------------------------------------------------------------
+# mixed modes: boxes whose sides are multiples of 128 run the six transform products on the
+# tensor cores (exact block-scaled integer slices, as in two dimensions); other boxes the CUDA cores
+# ----------------------------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def mixed3(ext):
+    c = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8))
+    yield c
+    ext.ext_destroy(c)
+
+
+@pytest.mark.parametrize("bcs", [("periodic",) * 3, ("symmetric", "dirichlet", "periodic")])
+@pytest.mark.parametrize("shape", [(128, 128, 128), (128, 256, 128)])
+def test_tensor_core_preconditioner_matches_the_box_solve(ext, mixed3, bcs, shape):
+    nz, ny, nx = shape
+    phi = _rand_phi(shape, 13)
+    unk = ~ob.known_mask(phi.astype(np.float64), "out")
+    r = np.random.default_rng(14).standard_normal(shape).astype(np.float32)
+    r[~unk] = 0
+    ref = np.where(unk, o3.poisson_squared_pinv3(r.astype(np.float64), bcs), 0.0)
+    z = torch.empty(shape, device="cuda")
+    scale = ext.ext_apply_preconditioner3d(mixed3, ext.problem3(nx, ny, nz, *bcs, "out"), dev(phi), dev(r), z)
+    got = z.cpu().numpy().astype(np.float64) / scale
+    np.testing.assert_allclose(got, ref, rtol=0, atol=5e-6 * np.abs(ref).max())
+
+
+def test_tensor_core_solve_of_example2_at_128(ext, mixed3, ctx):
+    """The 128^3 peanut through the tensor-core transforms at rel-res 1e-8 (the FP64 residual of
+    the double-float iterate, recomputed on the GPU): the error near the interface against the
+    analytic field (the paper's 1.07e-2), and the distance to the CUDA-core path's answer within
+    the mixed bound.  (The float32 answer itself carries rounding of 2^-24 relative, whose
+    residual through this operator is above 1e-8.)"""
+    n = 128
+    phi, f, h = _peanut(n)
+    prob = ext.problem3(n, n, n, "periodic", "periodic", "periodic", "out", h)
+    outs = []
+    for c in (mixed3, ctx):
+        out = torch.empty(phi.shape, device="cuda")
+        res = ext.ext_solve3d(c, prob, dev(phi), dev(f), out)
+        assert res["status"] == 0 and res["relres_true"] <= 1e-8, res
+        outs.append(out.cpu().numpy())
+    o = outs[0]
+    err = float(np.abs(o - f)[np.abs(phi) <= h].max())
+    assert abs(err / 1.07e-2 - 1) < 0.1, err
+    known = ob.known_mask(phi.astype(np.float64), "out")
+    assert ob.max_rel_error(o, outs[1].astype(np.float64), known) <= 1e-5
+
+
+def test_mixed_context_on_other_sides_uses_the_cuda_core_transforms(ext, mixed3):
+    shape = (10, 12, 14)
+    phi = _rand_phi(shape, 15, frac=0.5)
+    f = np.random.default_rng(16).standard_normal(shape).astype(np.float32)
+    _check(ext, mixed3, phi, f, ("periodic", "symmetric", "dirichlet"))
