@@ -549,7 +549,8 @@ def peanut3d_leg(sides=(64, 128, 256)):
     import numpy as np
     import torch
     from paper_1704_08897_gb300 import ext
-    out = {"workload": "Example 2 peanut, [-pi, pi]^3, periodic, extend out, FP32 path",
+    out = {"workload": "Example 2 peanut, [-pi, pi]^3, periodic, extend out; FP32 path, and mixed "
+                       "(tensor-core transforms) for sides that are multiples of 128",
            "note": "paper errors match the one-cell band (its caption says four cells)", "sides": {}}
     for n in sides:
         h = 2 * np.pi / n
