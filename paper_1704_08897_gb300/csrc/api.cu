@@ -529,13 +529,15 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   // the tensor-core transforms fold an axis by its mirror symmetry where both classes, padded,
   // fit in the padded axis: each stage then does half the products
   d.mir = 0;
-  if (ctx->tc && ctx->opt.fold) {
+  if (ctx->opt.fold) {
     if (mirror_pays(nx, kPad)) d.mir |= 1;
     if (mirror_pays(ny, kPad)) d.mir |= 2;
   }
   d.mhx = (d.mir & 1) ? mirror_half(nx) : nx;
   d.mhy = (d.mir & 2) ? mirror_half(ny) : ny;
-  d.n_fold_items = d.mir ? ((d.mhy + 7) / 8) * ((d.mhx + 127) / 128) : 0;
+  // fold items: mixed modes 8 class rows x 128 columns (a warp per row); CUDA cores 32 x 8 class
+  // nodes (one per thread, the unfold tiles)
+  d.n_fold_items = !d.mir ? 0 : ctx->tc ? ((d.mhy + 7) / 8) * ((d.mhx + 127) / 128) : 0;
   d.n_prep_items = (ctx->tc && !d.mir) ? ((ny + kStTileY - 1) / kStTileY) * ((nx + 127) / 128) : 0;
   d.n_unfold_tiles = d.mir ? ((d.mhx + 31) / 32) * ((d.mhy + 7) / 8) : 0;
   d.n_prec_parts = d.mir ? d.n_unfold_tiles : n_gm;
@@ -551,7 +553,8 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   const size_t o_q = take(4 * N), o_z = take(4 * N), o_mask = take(N);
   const size_t o_rl = take(4 * N), o_p0l = take(4 * N), o_p1l = take(4 * N);
   const size_t o_ql = take(4 * N), o_zl = take(4 * N);
-  const size_t fp = ctx->tc ? 0 : 4 * Np;  // SIMT transform intermediates (hi, lo planes)
+  // CUDA-core transform intermediates (hi, lo planes) of an unfolded slot
+  const size_t fp = (ctx->tc || d.mir) ? 0 : 4 * Np;
   const size_t o_t1 = take(fp), o_t2 = take(fp), o_t3 = take(fp);
   const size_t o_t1l = take(fp), o_t2l = take(fp), o_t3l = take(fp);
   const size_t o_lx = take(4 * (size_t)d.nxp), o_ly = take(4 * (size_t)d.nyp);
@@ -565,6 +568,7 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
     PlanDev *px = nullptr, *py = nullptr;
     size_t o_tr = 0, o_tt1 = 0, o_tt2 = 0, o_tt3 = 0, o_maps = 0, o_ex = 0, o_lx = 0, o_ly = 0;
     size_t o_g = 0, o_lh = 0, o_ljt = 0, o_ljte = 0, o_lz = 0, o_lmaps = 0;
+    size_t o_s1 = 0, o_s2 = 0, o_s3 = 0, o_cr = 0;  // CUDA-core class problems: T1..T3, residual
   };
   std::vector<TcLay> tl;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
@@ -572,7 +576,9 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   // four-slice stages dominate an iteration and the correction's iterations saved outweigh its cost
   const bool low = ctx->tc && (ctx->opt.low_modes == 1 ||
                                (ctx->opt.low_modes == 2 && std::max(nx, ny) >= kLowAutoSide));
-  if (ctx->tc) {
+  // transform problems: in mixed modes always (the slot itself or its classes), on the CUDA
+  // cores only for a folded slot (its classes; an unfolded slot runs on its own buffers)
+  if (ctx->tc || d.mir) {
     for (int cy = 0; cy < ((d.mir & 2) ? 2 : 1); ++cy)
       for (int cx = 0; cx < ((d.mir & 1) ? 2 : 1); ++cx) {
         TcLay L;
@@ -581,12 +587,19 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
         if (!rc) rc = get_plan(ctx, ny, prob.bc_y, (d.mir & 2) ? cy : -1, &L.py);
         if (rc) return rc;
         const size_t Npc = (size_t)L.px->np * L.py->np;
-        L.o_tr = take(2 * (low ? kLowNS : NS) * Npc);
-        L.o_tt1 = take(2 * NS * Npc);
-        L.o_tt2 = take(2 * NS * Npc);
-        L.o_tt3 = take(2 * NS * Npc);
-        L.o_maps = take(8 * sizeof(CUtensorMap));
-        L.o_ex = take(4 * (Npc / 64));
+        if (ctx->tc) {
+          L.o_tr = take(2 * (low ? kLowNS : NS) * Npc);
+          L.o_tt1 = take(2 * NS * Npc);
+          L.o_tt2 = take(2 * NS * Npc);
+          L.o_tt3 = take(2 * NS * Npc);
+          L.o_maps = take(8 * sizeof(CUtensorMap));
+          L.o_ex = take(4 * (Npc / 64));
+        } else {
+          L.o_s1 = take(8 * Npc);
+          L.o_s2 = take(8 * Npc);
+          L.o_s3 = take(8 * Npc);
+          L.o_cr = take(8 * (size_t)L.px->n * L.py->n);
+        }
         if (d.mir) {
           L.o_lx = take(4 * (size_t)L.px->np);
           L.o_ly = take(4 * (size_t)L.py->np);
@@ -681,12 +694,55 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   d.lamy = (const float*)(A + o_ly);
   BX_CUDA(cudaMemcpy(A + o_lx, lx.data(), 4 * lx.size(), cudaMemcpyHostToDevice));
   BX_CUDA(cudaMemcpy(A + o_ly, ly.data(), 4 * ly.size(), cudaMemcpyHostToDevice));
-  // the tensor-core problems
+  // the transform problems
   const bool bf = ctx->split == 1;
   for (const TcLay& L : tl) {
     SlotDesc t = d;  // the slot's fields; a class problem overrides its domain and operands below
     PlanDev* qx = L.px;
     PlanDev* qy = L.py;
+    if (!ctx->tc) {
+      // a class problem on the CUDA cores: its residual (formed by the fold kernel), T1..T3, the
+      // class bases as double-float planes, its eigenvalues and its result g
+      t.nx = qx->n;
+      t.ny = qy->n;
+      t.nxp = qx->np;
+      t.nyp = qy->np;
+      t.n_gm_tiles = (t.nxp / 128) * (t.nyp / 64);
+      t.mir = 0;
+      t.mir_out = 1;
+      t.mask = nullptr;
+      t.b = nullptr;
+      t.xhi = t.xlo = nullptr;
+      t.q = t.q_lo = nullptr;
+      t.p[0] = t.p[1] = t.p_lo[0] = t.p_lo[1] = nullptr;
+      t.part = t.pq_part = nullptr;
+      t.st_maps = nullptr;
+      const size_t Npc = (size_t)t.nxp * t.nyp, nc = (size_t)t.nx * t.ny;
+      t.t1 = (float*)(A + L.o_s1);
+      t.t1_lo = t.t1 + Npc;
+      t.t2 = (float*)(A + L.o_s2);
+      t.t2_lo = t.t2 + Npc;
+      t.t3 = (float*)(A + L.o_s3);
+      t.t3_lo = t.t3 + Npc;
+      t.r = (float*)(A + L.o_cr);
+      t.r_lo = t.r + nc;
+      t.qx = qx->q;
+      t.qxt = qx->qt;
+      t.qy = qy->q;
+      t.qyt = qy->qt;
+      t.z = (float*)(A + L.o_g);
+      t.z_lo = t.z + nc;
+      std::vector<float> lxc(t.nxp, 0.f), lyc(t.nyp, 0.f);
+      for (int k = 0; k < t.nx; ++k) lxc[k] = (float)(qx->lam[k] * a);
+      for (int k = 0; k < t.ny; ++k) lyc[k] = (float)(qy->lam[k] * c);
+      BX_CUDA(cudaMemcpy(A + L.o_lx, lxc.data(), 4 * lxc.size(), cudaMemcpyHostToDevice));
+      BX_CUDA(cudaMemcpy(A + L.o_ly, lyc.data(), 4 * lyc.size(), cudaMemcpyHostToDevice));
+      t.lamx = (const float*)(A + L.o_lx);
+      t.lamy = (const float*)(A + L.o_ly);
+      t.lowm_x = t.lowm_y = 0;
+      s.tcp[L.c] = t;
+      continue;
+    }
     int rc2 = ensure_tc_plan(ctx, qx);
     if (!rc2) rc2 = ensure_tc_plan(ctx, qy);
     if (rc2) return rc2;
@@ -775,6 +831,10 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   }
   s.n_tcp = (int)tl.size();
   if (ctx->tc && !d.mir) d = s.tcp[0];  // the slot is its own problem (k_tc_prepare reads it)
+  if (!ctx->tc && !d.mir) {             // the slot's own transforms on the CUDA cores
+    s.tcp[0] = d;
+    s.n_tcp = 1;
+  }
   return EXT_OK;
 }
 
@@ -836,18 +896,13 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
     if (d.aniso) W->aniso = true;
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
-    if (ctx->tc) {
-      tc_items(s, i, gm, l1, l3, tcl);
-      for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
-      for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
-      if (!d.mir)
-        for (int t = 0; t < d.n_prep_items; ++t) prep.push_back({i, t});
-    } else {
-      for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
-    }
+    tc_items(s, i, gm, l1, l3, tcl);
+    for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
+    for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
+    if (ctx->tc && !d.mir)
+      for (int t = 0; t < d.n_prep_items; ++t) prep.push_back({i, t});
   }
-  if (ctx->tc) longest_first_tc(gm, W->slots);
-  else longest_first(gm, W->slots);
+  longest_first_tc(gm, W->slots);
   std::vector<WorkItem> sl;
   for (int i = 0; i < count; ++i) sl.push_back({i, 0});
   W->n_sl = (int)sl.size();
@@ -858,11 +913,10 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   BX_CUDA(cudaMemset(W->d_sc, 0, sizeof(SlotScalars) * count));
   BX_CUDA(cudaMallocHost(&W->h_sc, sizeof(SlotScalars) * count));
   for (int i = 0; i < count; ++i) set_slot_scalars(W->slots[i], W->d_sc + i);
-  std::vector<SlotDesc> descs(count), tcps(ctx->tc ? kMirClasses * count : 0);
+  std::vector<SlotDesc> descs(count), tcps(kMirClasses * count);
   for (int i = 0; i < count; ++i) {
     descs[i] = W->slots[i].d;
-    if (ctx->tc)
-      for (int c = 0; c < kMirClasses; ++c) tcps[kMirClasses * i + c] = W->slots[i].tcp[c];
+    for (int c = 0; c < kMirClasses; ++c) tcps[kMirClasses * i + c] = W->slots[i].tcp[c];
   }
   int rc = upload(&W->d_slots, descs);
   if (!rc) rc = upload(&W->d_tcp, tcps);
@@ -1049,13 +1103,20 @@ static void launch_prec(ext_ctx* ctx, Workspace* W, int mode) {
       timed(ctx, EXT_KERNEL_LOW_INV, [&] { launch_low_tc(c3, 1, mode, ctx->split, ctx->d_err); }, g.stream);
     }
   }
+  if (!ctx->tc) {
+    // CUDA-core transforms over the transform problems: a folded slot's classes get their
+    // residuals from the fold first
+    g.slots = W->d_tcp;
+    if (W->n_unfold > 0)
+      timed(ctx, EXT_KERNEL_FOLD, [&] { launch_simt_fold(cfg_of(ctx, W, 8), mode); }, g.stream);
+  }
   for (int s = 0; s < 4; ++s) {
     timed(ctx, EXT_KERNEL_PREC0 + s, [&] {
       if (!ctx->tc) launch_prec_simt(g, s, mode);
       else launch_prec_tc(g, s, mode, ctx->split, ctx->d_err);
     }, g.stream);
   }
-  if (ctx->tc && W->n_unfold > 0)
+  if (W->n_unfold > 0)
     timed(ctx, EXT_KERNEL_UNFOLD, [&] { launch_unfold(cfg_of(ctx, W, 8), mode); }, g.stream);
   const LaunchCfg f = cfg_of(ctx, W, 3);  // one block per slot
   timed(ctx, EXT_KERNEL_PREC_FINISH, [&] { launch_prec_finish(f, mode); }, f.stream);
@@ -2134,19 +2195,14 @@ static int serve_rebuild_lists(ext_ctx* ctx) {
     aniso |= d.aniso != 0;
     for (int t = 0; t < d.n_st_tiles; ++t) st.push_back({i, t});
     for (int t = 0; t < d.n_vec_items; ++t) vec.push_back({i, t});
-    if (ctx->tc) {
-      tc_items(h, i, gm, l1, l3, tcl);
-      for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
-      for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
-      if (!d.mir)
-        for (int t = 0; t < d.n_prep_items; ++t) prep.push_back({i, t});
-    } else {
-      for (int t = 0; t < d.n_gm_tiles; ++t) gm.push_back({i, t});
-    }
+    tc_items(h, i, gm, l1, l3, tcl);
+    for (int t = 0; t < d.n_fold_items; ++t) fold.push_back({i, t});
+    for (int t = 0; t < d.n_unfold_tiles; ++t) unfold.push_back({i, t});
+    if (ctx->tc && !d.mir)
+      for (int t = 0; t < d.n_prep_items; ++t) prep.push_back({i, t});
     sl.push_back({i, 0});
   }
-  if (ctx->tc) longest_first_tc(gm, W->slots);
-  else longest_first(gm, W->slots);
+  longest_first_tc(gm, W->slots);
   size_t need = 0;
   for (const auto* v : {&st, &vec, &gm, &l1, &l3, &fold, &unfold, &tcl, &prep}) need = std::max(need, v->size());
   if ((int)need > S->cap_items) {
@@ -2271,9 +2327,8 @@ static int serve_setup_slots(ext_ctx* ctx, const std::vector<int>& admitted) {
     BX_CUDA(cudaMemcpyAsync(W->d_outs + i, &h_outs[i], sizeof(void*), cudaMemcpyHostToDevice, s));
     BX_CUDA(cudaMemcpyAsync(W->d_dirs + i, &h_dirs[i], sizeof(int), cudaMemcpyHostToDevice, s));
     BX_CUDA(cudaMemcpyAsync(W->d_slots + i, &sl.d, sizeof(SlotDesc), cudaMemcpyHostToDevice, s));
-    if (ctx->tc)
-      BX_CUDA(cudaMemcpyAsync(W->d_tcp + kMirClasses * i, sl.tcp, sizeof(SlotDesc) * kMirClasses,
-                              cudaMemcpyHostToDevice, s));
+    BX_CUDA(cudaMemcpyAsync(W->d_tcp + kMirClasses * i, sl.tcp, sizeof(SlotDesc) * kMirClasses,
+                            cudaMemcpyHostToDevice, s));
     SlotScalars& sc = W->h_sc[i];
     memset(&sc, 0, sizeof(sc));
     sc.rtol2 = ctx->opt.rtol * ctx->opt.rtol;

@@ -359,6 +359,7 @@ __device__ __forceinline__ f2 df_fma(f2 a, f2 b, f2 c) {
   e = __fadd_rn(e, __fadd_rn(c.lo, pe));
   return df_norm(s, e);
 }
+__device__ __forceinline__ f2 df_neg(f2 a) { return f2{-a.hi, -a.lo}; }
 // an FP64 value as a double-float pair (host and device)
 __host__ __device__ __forceinline__ f2 df_of(double v) {
   const float h = (float)v;

@@ -54,15 +54,20 @@ void launch_apply(const SlotDesc* slot, int n_tiles, bool aniso, const float* p,
 // mode 0: slots with active iterations; mode 1: slots with a pending preconditioner pass;
 // mode 2: every slot (verification entry point).
 void launch_prec_simt(const LaunchCfg& c, int stage, int mode);
+// the mirror classes' residuals of folded slots in double-float (c.slots = slots, c.tcp = the
+// transform problems, items: the unfold tiles of 32 x 8 class nodes)
+void launch_simt_fold(const LaunchCfg& c, int mode);
 
 // tensor-core variant (kernels_gemm_tc.cu): exact block-scaled integer slice planes stored as
 // FP16 (split_kind 0) or BF16 (split_kind 1); err receives 1 if a bounded wait ran out.
 void launch_prec_tc(const LaunchCfg& c, int stage, int mode, int split_kind, int* err);
-// residual -> integer slice planes of the first stage's A operand (stencil tile work list)
+// residual -> integer slice planes of the first stage's A operand, slots with no folded axis
+// (items of 32 rows x 128 columns)
 void launch_prec_tc_prepare(const LaunchCfg& c, int mode, int split_kind);
 int tc_planes(int split_kind);
-// low-mode correction of the tensor-core preconditioner: kind 0 = forward product (one tile per
-// 128 rows of y), kind 1 = inverse product (tiles of 128 x 32); the middle step one block per slot
+// low-mode correction of the tensor-core preconditioner: kind 0 = forward product with the tiles'
+// shares of G (one CTA per 128 rows of y), kind 1 = inverse product (one CTA per 128 rows of x,
+// walking the y-tiles); the middle step one block per (problem, 128 rows of x)
 void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* err);
 void launch_low_mid(const LaunchCfg& c, int mode, int split_kind);
 // mirror fold: residual -> slices of each class's first operand (c.slots = slots, items of the

@@ -177,6 +177,20 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
               make_float4(o[0].hi, o[1].hi, o[2].hi, o[3].hi);
           *reinterpret_cast<float4*>(v.out_lo + (size_t)n * v.M + mb) =
               make_float4(o[0].lo, o[1].lo, o[2].lo, o[3].lo);
+        } else if (S.mir_out) {
+          // one mirror class of a folded slot: its result g, unmasked (k_unfold combines the
+          // classes, masks and forms the dot products)
+          const int y = n;
+          if (y < S.ny) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+              const int x = mb + i;
+              if (x < S.nx) {
+                S.z[y * S.nx + x] = o[i].hi;
+                S.z_lo[y * S.nx + x] = o[i].lo;
+              }
+            }
+          }
         } else {
           const int y = n;
           if (y < S.ny) {
@@ -196,7 +210,7 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
         }
       }
     }
-    if (STAGE == 3) {
+    if (STAGE == 3 && !S.mir_out) {  // a class problem leaves no partial sums
       double d_rz = c_rz.value(), d_zq = c_zq.value();
       block_sum2<NT>(d_rz, d_zq, red);
       if (t == 0) {  // tile partials; k_prec_finish forms rho and beta from them
@@ -206,6 +220,52 @@ k_prec_simt(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ ite
     }
     __syncthreads();
   }
+}
+
+// The residuals of the mirror classes of a folded slot (CUDA-core path): one thread per class
+// node (tiles of 32 x 8), the signed sums of r at the node and its mirrors in double-float (the
+// even class adds, the odd class subtracts; a middle node, its own mirror, counts once in the even
+// class and not in the odd one), written to each class problem's residual planes.
+__global__ void __launch_bounds__(256)
+k_simt_fold(const SlotDesc* __restrict__ slots, const SlotDesc* __restrict__ tcp,
+            const WorkItem* __restrict__ items, const int* __restrict__ n_items, int mode) {
+  const int total = *n_items;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int w = blockIdx.x; w < total; w += gridDim.x) {
+    const WorkItem it = items[w];
+    const SlotDesc& S = slots[it.slot];
+    SlotScalars* sc = S.sc;
+    const int run = mode == 0 ? sc->active : (mode == 1 ? sc->need_prec : 1);
+    if (!run) continue;
+    const bool fx = (S.mir & 1) != 0, fy = (S.mir & 2) != 0;
+    const int ntx = (S.mhx + 31) >> 5;
+    const int x = (it.tile % ntx) * 32 + lane, y = (it.tile / ntx) * 8 + warp;
+    if (x >= S.mhx || y >= S.mhy) continue;
+    const int xx = fx ? S.nx - 1 - x : x, yy = fy ? S.ny - 1 - y : y;
+    const bool xmid = xx == x, ymid = yy == y;
+    const size_t gy = static_cast<size_t>(y) * S.nx, gyy = static_cast<size_t>(yy) * S.nx;
+    const f2 a{S.r[gy + x], S.r_lo[gy + x]};
+    const f2 b = xmid ? f2{0.f, 0.f} : f2{S.r[gy + xx], S.r_lo[gy + xx]};
+    const f2 c = ymid ? f2{0.f, 0.f} : f2{S.r[gyy + x], S.r_lo[gyy + x]};
+    const f2 d = (xmid || ymid) ? f2{0.f, 0.f} : f2{S.r[gyy + xx], S.r_lo[gyy + xx]};
+    const f2 e0 = df_add(a, b), o0 = df_add(a, df_neg(b));
+    const f2 e1 = df_add(c, d), o1 = df_add(c, df_neg(d));
+    f2 v[4] = {df_add(e0, e1), df_add(o0, o1), df_add(e0, df_neg(e1)), df_add(o0, df_neg(o1))};
+    if (xmid && fx) v[1] = v[3] = f2{0.f, 0.f};  // the odd x classes vanish at the middle column
+    if (ymid && fy) v[2] = v[3] = f2{0.f, 0.f};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (((k & 1) && !fx) || ((k & 2) && !fy)) continue;
+      const SlotDesc& T = tcp[kMirClasses * it.slot + k];
+      const size_t gi = static_cast<size_t>(y) * T.nx + x;
+      T.r[gi] = v[k].hi;
+      T.r_lo[gi] = v[k].lo;
+    }
+  }
+}
+
+void launch_simt_fold(const LaunchCfg& c, int mode) {
+  k_simt_fold<<<c.grid, 256, 0, c.stream>>>(c.slots, c.tcp, c.items, c.n_items, mode);
 }
 
 void launch_prec_simt(const LaunchCfg& c, int stage, int mode) {

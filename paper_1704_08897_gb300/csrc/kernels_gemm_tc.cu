@@ -769,7 +769,6 @@ k_tc_prepare(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ it
 // with the odd ones' signs flipped on the mirrored side, masks it and leaves the r.z and z.q
 // partials that stage 3 leaves for an unfolded slot.
 // ---------------------------------------------------------------------------------------------
-__device__ __forceinline__ f2 df_neg(f2 a) { return f2{-a.hi, -a.lo}; }
 
 // One warp per (class row y, 128 class columns); lane pairs (x, x+1) at x = 64 k + 2 lane.
 template <bool BF16>
@@ -965,20 +964,23 @@ k_unfold(const SlotDesc* __restrict__ slots, const SlotDesc* __restrict__ tcp,
 // Low-mode correction (mixed modes).  The weights 1/(lam_y + lam_x)^2 of the smoothest modes are up
 // to (64/lam_min)^2 times those of the roughest, so rounding noise of the 32-bit stages, relative
 // to |r|, is amplified in exactly these modes and costs CG iterations.  The modes kx < 32,
-// ky < 32 are therefore left out of stage 1's weights and computed here to about 48 bits:
-//   forward (KIND 0):  H[y][kx] = sum_x r[y][x] Qx[x][kx]            six slices each side
-//   middle (k_low_mid): G = Qy_low^T H, G' = w o G, J[ky][x] = sum_kx G'[ky][kx] Qx[x][kx]
-//                      (double-float dot products on the CUDA cores), J^T cut into six slices
-//   inverse (KIND 1):  zl[y][x] = sum_ky Qy[y][ky] J[ky][x]           six slices each side
+// ky < 32 (of each transform problem) are therefore left out of stage 1's weights and computed
+// here to about 48 bits:
+//   forward (k_low_tc):  H[y][kx] = sum_x r[y][x] Qx[x][kx], six slices each side, and each
+//                        128-row tile's share of G = Qy_low^T H (double-float dot products)
+//   middle (k_low_mid):  G = the shares in tile order, G' = w o G,
+//                        J[ky][x] = sum_kx G'[ky][kx] Qx[x][kx] (double-float), J^T in six slices
+//   inverse (k_low_inv): zl[y][x] = sum_ky Qy[y][ky] J[ky][x], six slices each side
 // and stage 3 adds zl to its result.  With six 8-bit slices per operand the products of orders
 // 0..5 (21 of them) are kept, each order in its own TMEM accumulator; per k, the products of one
 // order add up to at most 2^17 in magnitude, so over a 128-wide block every partial sum is an
 // exact integer of at most 2^24.  Orders 0..2 are merged into the double-float result with TwoSum,
 // orders 3..5 (below 2^-24 of it) in plain FP32.
 //
-// One CTA per output tile of 128 rows x 32 columns, four warps; thread 0 issues the tensor copies
-// and the MMAs one 64-wide k step at a time (the products are thin, so a simple serial pipeline
-// suffices), and every thread drains its own TMEM lane after each exponent block.
+// The forward product: one CTA per 128 rows of y, sixteen warps (four per TMEM lane quarter, eight
+// of the 32 columns each); thread 0 issues the tensor copies and the MMAs one 64-wide k step at a
+// time (the products are thin, so a simple serial pipeline suffices), every thread drains its own
+// TMEM lane after each exponent block, and after the last block the CTA forms its share of G.
 // ---------------------------------------------------------------------------------------------
 constexpr int LBN = kLowM;                   // N tile (columns)
 constexpr int LBK = 64;                      // k per tensor copy
@@ -1008,7 +1010,7 @@ __device__ __forceinline__ int low_block_exp(float amax) {
   return max(e, -90);
 }
 
-template <bool BF16, int KIND>
+template <bool BF16>
 __global__ void __launch_bounds__(kLowThreads, 1)
 k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
          const int* __restrict__ n_items, int mode, int* __restrict__ err, long long wait_cycles) {
@@ -1046,27 +1048,11 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
     const WorkItem it = items[w];
     const SlotDesc& S = slots[it.slot];
     if (!slot_runs(S.sc, mode) || S.lowm_x == 0) continue;
-    // geometry of this product
-    int m0, n0, K, KC, rowsA, rowsB;
+    // geometry: A = the residual's six slice planes (rows y), B = Qx_low^T's (rows kx)
     const unsigned char* maps = static_cast<const unsigned char*>(S.low_maps);
-    const void* ma = maps + 128 * (KIND == 0 ? 0 : 2);
-    const void* mb = maps + 128 * (KIND == 0 ? 1 : 3);
-    if (KIND == 0) {
-      m0 = it.tile * BM;
-      n0 = 0;
-      K = S.nxp;
-      KC = 128;
-      rowsA = S.nyp;
-      rowsB = kLowM;
-    } else {
-      const int mt = S.nxp / BM;
-      m0 = (it.tile % mt) * BM;
-      n0 = (it.tile / mt) * LBN;
-      K = kLowK3;
-      KC = kLowK3;
-      rowsA = S.nxp;
-      rowsB = S.nyp;
-    }
+    const void* ma = maps;
+    const void* mb = maps + 128;
+    const int m0 = it.tile * BM, n0 = 0, K = S.nxp, KC = 128, rowsA = S.nyp, rowsB = kLowM;
     if (threadIdx.x == 0) {
       tmap_acquire(ma);
       tmap_acquire(mb);
@@ -1122,16 +1108,13 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       }
       tc_fence_after();
       // exponents of the block: the thread's row (A) and every column (B)
-      int ea;
-      if (KIND == 0) ea = S.tc_e[0][static_cast<size_t>(min(m, S.nyp - 1)) * (S.nxp / 128) + kb];
-      else ea = S.low_jt_e[min(m, S.nxp - 1)];
+      const int ea = S.tc_e[0][static_cast<size_t>(min(m, S.nyp - 1)) * (S.nxp / 128) + kb];
       // 2^(E_A + E_B - 16) of every column (exact products of powers of two)
       float scl[kLowCols];
 #pragma unroll
       for (int c = 0; c < kLowCols; ++c) {
         const int cc = cg * kLowCols + c;
-        const int eb = KIND == 0 ? S.low_qxt_e[static_cast<size_t>(cc) * (S.nxp / 128) + kb]
-                                 : S.low_qy_e[min(n0 + cc, S.nyp - 1)];
+        const int eb = S.low_qxt_e[static_cast<size_t>(cc) * (S.nxp / 128) + kb];
         scl[c] = pow2f(ea - 16) * pow2f(eb);
       }
       // the six order sums of the warp's columns, loaded together
@@ -1159,7 +1142,7 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       __syncthreads();  // the next block's MMAs overwrite the accumulators
     }
     if (failed) break;
-    if (KIND == 0) {
+    {
       // the tile's share of G = Qy_low^T H (its 128 rows of y), by compensated dot products of
       // double-float operands staged in shared memory (the operand buffers are free: the last
       // MMAs completed before the block's TMEM reads); H itself is not stored
@@ -1192,20 +1175,6 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       gp[(warp + 16) * kLowM + lane] = a1.hi;
       gp[kLowM * kLowM + (warp + 16) * kLowM + lane] = a1.lo;
       __syncthreads();  // the next item's tensor copies overwrite the staging
-    } else {
-      const size_t nn = static_cast<size_t>(S.nx) * S.ny;
-      if (m < S.nx) {
-#pragma unroll
-        for (int c = 0; c < kLowCols; ++c) {
-          const int n = n0 + cg * kLowCols + c;
-          if (n < S.ny) {
-            const f2 v = df_norm(hi[c], lo[c]);
-            const size_t g = static_cast<size_t>(n) * S.nx + m;
-            S.low_z[g] = v.hi;
-            S.low_z[nn + g] = v.lo;
-          }
-        }
-      }
     }
   }
   if (threadIdx.x == 0) {
@@ -1235,8 +1204,8 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
 // Inverse low-mode product, zl[y][x] = sum_ky Qy[y][ky] J[ky][x], one item per (slot, 128-row
 // tile of x).  The tile's six J^T slice planes (its A operand, k = ky padded to 64) are copied
 // once; the B operand (Qy_low's slices for 32 values of y) is double-buffered, and the products of
-// consecutive y-tiles go to two TMEM sets, so that the MMAs of one y-tile run while the four warps
-// merge and store the previous one.
+// consecutive y-tiles go to two TMEM sets, so that the MMAs of one y-tile run while the sixteen
+// warps merge and store the previous one.
 struct LowInvCtl {
   uint64_t fa, fb[2], md[2];
   uint32_t tmem;
@@ -1556,7 +1525,7 @@ int tc_block() { return KC; }
 template <bool BF16, int KIND>
 static cudaError_t set_low_attr() {
   if (KIND == 0)
-    return cudaFuncSetAttribute(k_low_tc<BF16, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowSmem);
+    return cudaFuncSetAttribute(k_low_tc<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowSmem);
   return cudaFuncSetAttribute(k_low_inv<BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, kLowInvSmem);
 }
 
@@ -1574,10 +1543,10 @@ cudaError_t tc_init() {
 void launch_low_tc(const LaunchCfg& c, int kind, int mode, int split_kind, int* err) {
   const long long wc = c.wait_cycles > 0 ? c.wait_cycles : kWaitCycles;
   if (split_kind == 0) {
-    if (kind == 0) k_low_tc<false, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    if (kind == 0) k_low_tc<false><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
     else k_low_inv<false><<<c.grid, kLowInvThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
   } else {
-    if (kind == 0) k_low_tc<true, 0><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
+    if (kind == 0) k_low_tc<true><<<c.grid, kLowThreads, kLowSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
     else k_low_inv<true><<<c.grid, kLowInvThreads, kLowInvSmem, c.stream>>>(c.slots, c.items, c.n_items, mode, err, wc);
   }
 }

@@ -441,8 +441,33 @@ def test_folded_preconditioner_matches_fast_poisson(ext, fold_ctxs, bc_x, bc_y, 
         assert np.all(got[-1][known] == 0)
 
 
+@pytest.mark.parametrize("bc_x", ob.BCS)
+@pytest.mark.parametrize("bc_y", ob.BCS)
+@pytest.mark.parametrize("nx,ny", [(255, 200), (300, 255)])
+def test_folded_preconditioner_fp32(ext, bc_x, bc_y, nx, ny):
+    """The CUDA-core path folds the same axes: its preconditioner per mirror class equals the
+    oracle's, folded and not."""
+    phi = _rand_phi(nx, ny, 7)
+    known = ob.known_mask(phi.astype(np.float64), "out")
+    r = np.random.default_rng(8).standard_normal((ny, nx)).astype(np.float32)
+    r[known] = 0
+    ref = ob.poisson_squared_pinv(r.astype(np.float64), bc_x, bc_y)
+    ref[known] = 0
+    for fold in (1, 0):
+        c = ext.ext_create(ext.options("fp32", rtol=1e-8, fold=fold))
+        try:
+            z = torch.empty((ny, nx), device="cuda")
+            scale = ext.ext_apply_preconditioner(c, ext.problem(nx, ny, bc_x, bc_y, "out"), dev(phi),
+                                                 dev(r), z)
+        finally:
+            ext.ext_destroy(c)
+        got = z.cpu().numpy().astype(np.float64) / scale
+        np.testing.assert_allclose(got, ref, rtol=0, atol=1e-6 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "fp32"])
 @pytest.mark.parametrize("bc", ob.BCS)
-def test_folded_solve_on_odd_sides(ext, bc):
+def test_folded_solve_on_odd_sides(ext, bc, prec):
     """A grid with odd sides on both folded axes (middle nodes in the even classes) solves to
     rel-res 1e-8 within the mixed path's bound of the direct solve, folded and not."""
     nx, ny = 255, 193
@@ -453,7 +478,7 @@ def test_folded_solve_on_odd_sides(ext, bc):
     ref, _ = ob.extend(phi64, f64, "out", bc, bc, method="direct")
     known = ob.known_mask(phi64, "out")
     for fold in (1, 0):
-        c = ext.ext_create(ext.options("mixed_bf16", rtol=1e-8, maxit=40 * nx, fold=fold))
+        c = ext.ext_create(ext.options(prec, rtol=1e-8, maxit=40 * nx, fold=fold))
         try:
             out64 = torch.empty((ny, nx), device="cuda", dtype=torch.float64)
             res = ext.ext_solve_f64(c, ext.problem(nx, ny, bc, bc, "out"), dev(phi), dev(f), out64)
@@ -462,7 +487,7 @@ def test_folded_solve_on_odd_sides(ext, bc):
         o = out64.cpu().numpy()
         rr = ob.true_relative_residual(o, phi64, f64, "out", bc, bc)
         assert res["status"] == 0 and rr <= 1.05e-8, (bc, fold, rr, res)
-        assert ob.max_rel_error(o, ref, known) <= TOL_MIXED
+        assert ob.max_rel_error(o, ref, known) <= (TOL_MIXED if prec != "fp32" else TOL_FP32)
 
 
 @pytest.mark.parametrize("maker", [lambda: synth.circle(64), lambda: synth.wobbly(192, 3),
