@@ -83,36 +83,176 @@ __device__ __forceinline__ Taps7 taps7(const Grid3& G, int x, int y, int z) {
   return t;
 }
 
-// Double-float Laplacian pass.  FINAL = false: out = L in at every node.  FINAL = true:
-// out = M L in (zero at known nodes), and the block's partial p.out (compensated) in part.
+// Double-float Laplacian pass, marching along z.  A block of 32 x 8 threads owns 32 x kBy nodes of
+// (x, y) (two rows per thread, ty and ty + 8) and a chunk of kZc planes.  Each thread keeps its
+// own two columns in registers (planes z - 1, z, z + 1 and the two in flight); the x and y
+// neighbours come from a shared-memory tile of the plane with its one-node halo, written once per
+// plane and double-buffered, so one barrier per plane suffices.  Global loads run two planes ahead
+// of their use.  Every cell's ghost map in x and y is taken once per thread, the z map once per
+// plane; ghost signs are folded into the loaded values.  FINAL = false: out = L in at every node.
+// FINAL = true: out = M L in (zero at known nodes), and the block's partial p.out (compensated).
+// The terms are added in the order centre, x-1, x+1, y-1, y+1, z-1, z+1, as the single-node form
+// would.
+constexpr int kZc = 16;                       // planes per block
+constexpr int kBy = 16;                       // rows per block
+constexpr int kTw = 34, kTh = kBy + 2;        // tile with halo
+constexpr int kHalo = 2 * kTw + 2 * kBy;      // halo cells of a tile
+static_assert(kHalo <= kT && kBy == 2 * (kT / 32), "one halo cell per thread, two rows per thread");
+
+// One cell that a thread loads on every plane: its offset within a plane and the product of its
+// x and y ghost signs; ok = false for cells that are no node's neighbour (nothing is loaded).
+struct Cell3 {
+  size_t off = 0;
+  float sxy = 0.f;
+  bool ok = false;
+};
+__device__ __forceinline__ Cell3 cell3(const Grid3& G, int gx, int gy) {
+  Cell3 c;
+  if (gx > G.nx || gy > G.ny) return c;  // farther cells neighbour no node of the grid
+  float sx, sy;
+  const int mx = ghost(gx, G.nx, G.bcx, sx), my = ghost(gy, G.ny, G.bcy, sy);
+  c.sxy = sx * sy;
+  c.ok = c.sxy != 0.f;
+  c.off = static_cast<size_t>(my) * G.nx + mx;
+  return c;
+}
+
+// Tile coordinates of halo cell k: the row above, the row below, the left and the right column.
+__device__ __forceinline__ int halo_pos(int k) {
+  if (k < kTw) return k;
+  if (k < 2 * kTw) return (kTh - 1) * kTw + (k - kTw);
+  if (k < 2 * kTw + kBy) return (1 + k - 2 * kTw) * kTw;
+  return (1 + k - 2 * kTw - kBy) * kTw + kTw - 1;
+}
+
+// A thread's values of one plane: its two own cells and its halo cell (hi, lo).
+struct Plane3 {
+  float h[3] = {0.f, 0.f, 0.f}, l[3] = {0.f, 0.f, 0.f};
+};
+__device__ __forceinline__ Plane3 k3_fetch(const Grid3& G, const float* __restrict__ ih,
+                                           const float* __restrict__ il, const Cell3 (&cl)[3], int zz) {
+  Plane3 p;
+  float sz;
+  const int mz = ghost(zz, G.nz, G.bcz, sz);
+  if (sz == 0.f) return p;
+  const size_t base = static_cast<size_t>(mz) * G.ny * G.nx;
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    if (cl[k].ok) {
+      const float s = cl[k].sxy * sz;
+      p.h[k] = s * ih[base + cl[k].off];
+      p.l[k] = s * il[base + cl[k].off];
+    }
+  return p;
+}
+
+__device__ __forceinline__ void k3_put(const Plane3& p, float* th, float* tl, int ca, int hp) {
+  th[ca] = p.h[0];
+  tl[ca] = p.l[0];
+  th[ca + 8 * kTw] = p.h[1];
+  tl[ca + 8 * kTw] = p.l[1];
+  if (hp >= 0) {
+    th[hp] = p.h[2];
+    tl[hp] = p.l[2];
+  }
+}
+
+// The seven-term double-float Laplacian of one node: x and y neighbours from the tile at c, the
+// centre and the z neighbours (below, up) from the thread's registers.
+__device__ __forceinline__ f2 k3_node(const Grid3& G, const float* th, const float* tl, int c, float ch,
+                                      float cl, float bh, float bl, float uh, float ul) {
+  const float w0 = 2.f * (G.cx + G.cy + G.cz);
+  const float hv[7] = {ch, th[c - 1], th[c + 1], th[c - kTw], th[c + kTw], bh, uh};
+  const float lv[7] = {cl, tl[c - 1], tl[c + 1], tl[c - kTw], tl[c + kTw], bl, ul};
+  const float w[7] = {w0, -G.cx, -G.cx, -G.cy, -G.cy, -G.cz, -G.cz};
+  CompSum a;
+  float lo = 0.f;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) {
+    a.add_prod(w[k], hv[k]);
+    lo = __fmaf_rn(w[k], lv[k], lo);
+  }
+  return df_norm(a.s, __fadd_rn(a.c, lo));
+}
+
 template <bool FINAL>
 __global__ void __launch_bounds__(kT)
 k3_lap(Grid3 G, const float* __restrict__ ih, const float* __restrict__ il, float* __restrict__ oh,
        float* __restrict__ ol, const uint8_t* __restrict__ mask, const float* __restrict__ ph,
        const float* __restrict__ pl, double* __restrict__ part) {
   __shared__ double sh[kT / 32];
-  const int x = blockIdx.x * 32 + (threadIdx.x & 31);
-  const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
-  const int z = blockIdx.z;
-  CompDotDF dot;
-  if (x < G.nx && y < G.ny) {
-    const Taps7 t = taps7(G, x, y, z);
-    const size_t g = t.g[0];
-    f2 v{0.f, 0.f};
-    if (!FINAL || mask[g]) {
-      CompSum a;
-      float lo = 0.f;
+  __shared__ float tile[2][2][kTh * kTw];  // [buffer][hi, lo]
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * kBy, z0 = blockIdx.z * kZc;
+  const int z1 = min(z0 + kZc, G.nz);
+  const int x = x0 + tx;
+  const int yr[2] = {y0 + ty, y0 + ty + 8};
+  const bool in[2] = {x < G.nx && yr[0] < G.ny, x < G.nx && yr[1] < G.ny};
+  const int ca = (ty + 1) * kTw + tx + 1;  // tile position of the first own node
+  Cell3 cl[3];
+  cl[0] = cell3(G, x, yr[0]);
+  cl[1] = cell3(G, x, yr[1]);
+  int hp = -1;
+  if (threadIdx.x < kHalo) {
+    hp = halo_pos(threadIdx.x);
+    const int ly = hp / kTw, lx = hp - ly * kTw;
+    cl[2] = cell3(G, x0 - 1 + lx, y0 - 1 + ly);
+  }
+  const size_t plane = static_cast<size_t>(G.ny) * G.nx;
+  // p and the mask at the own nodes, loaded one plane ahead (FINAL only)
+  uint8_t mk[2] = {0, 0};
+  float pph[2] = {0.f, 0.f}, ppl[2] = {0.f, 0.f};
+  auto load_p = [&](int z, uint8_t (&m)[2], float (&h)[2], float (&l)[2]) {
 #pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        const float w = t.w[k] * t.s[k];
-        a.add_prod(w, ih[t.g[k]]);
-        lo = __fmaf_rn(w, il[t.g[k]], lo);
+    for (int i = 0; i < 2; ++i)
+      if (in[i]) {
+        const size_t g = z * plane + cl[i].off;
+        m[i] = mask[g];
+        h[i] = ph[g];
+        l[i] = pl[g];
       }
-      v = df_norm(a.s, __fadd_rn(a.c, lo));
+  };
+  Plane3 below = k3_fetch(G, ih, il, cl, z0 - 1);
+  Plane3 cur = k3_fetch(G, ih, il, cl, z0);
+  Plane3 up = k3_fetch(G, ih, il, cl, z0 + 1);
+  Plane3 n1;
+  if (z0 + 1 < z1) n1 = k3_fetch(G, ih, il, cl, z0 + 2);
+  if (FINAL) load_p(z0, mk, pph, ppl);
+  k3_put(cur, tile[0][0], tile[0][1], ca, hp);
+  __syncthreads();
+  CompDotDF dot;
+  for (int z = z0; z < z1; ++z) {
+    const int b = (z - z0) & 1;
+    Plane3 n2;  // plane z + 3, needed from the step of plane z + 2 on
+    if (z + 2 < z1) n2 = k3_fetch(G, ih, il, cl, z + 3);
+    uint8_t nmk[2] = {0, 0};
+    float nph[2] = {0.f, 0.f}, npl[2] = {0.f, 0.f};
+    if (FINAL && z + 1 < z1) load_p(z + 1, nmk, nph, npl);
+    const float* th = tile[b][0];
+    const float* tl = tile[b][1];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+      if (in[i]) {
+        const size_t g = z * plane + cl[i].off;
+        f2 v{0.f, 0.f};
+        if (!FINAL || mk[i])
+          v = k3_node(G, th, tl, ca + i * 8 * kTw, cur.h[i], cur.l[i], below.h[i], below.l[i], up.h[i], up.l[i]);
+        oh[g] = v.hi;
+        ol[g] = v.lo;
+        if (FINAL) dot.add(pph[i], ppl[i], v.hi, v.lo);
+      }
+    if (z + 1 < z1) k3_put(up, tile[b ^ 1][0], tile[b ^ 1][1], ca, hp);
+    __syncthreads();
+    below = cur;
+    cur = up;
+    up = n1;
+    n1 = n2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      mk[i] = nmk[i];
+      pph[i] = nph[i];
+      ppl[i] = npl[i];
     }
-    oh[g] = v.hi;
-    ol[g] = v.lo;
-    if (FINAL) dot.add(ph[g], pl[g], v.hi, v.lo);
   }
   if (FINAL) {
     const double s = block_sum_d(dot.value(), sh);
@@ -388,8 +528,8 @@ k3_mask_dot(size_t n, const float* __restrict__ Zh, const float* __restrict__ Zl
 struct State3 {
   size_t n = 0;
   int vec_blocks = 0;
-  dim3 grid3, block3;
-  int n_parts = 0;
+  dim3 grid3, gridz, block3;  // gridz: the z-marching double-float passes
+  int n_parts = 0, n_parts_z = 0;
   uint8_t* mask = nullptr;
   double *b = nullptr, *d0 = nullptr, *d1 = nullptr, *part = nullptr, *scal = nullptr;
   float *xh = nullptr, *xl = nullptr, *rh = nullptr, *rl = nullptr, *ph = nullptr, *pl = nullptr;
@@ -440,6 +580,8 @@ int alloc_state(const Solve3Args& a, State3& s, bool solve, std::string* err) {
   s.block3 = dim3(kT);
   s.grid3 = dim3((a.nx + 31) / 32, (a.ny + 7) / 8, a.nz);
   s.n_parts = (int)(s.grid3.x * s.grid3.y * s.grid3.z);
+  s.gridz = dim3(s.grid3.x, (a.ny + kBy - 1) / kBy, (a.nz + kZc - 1) / kZc);
+  s.n_parts_z = (int)(s.gridz.x * s.gridz.y * s.gridz.z);
   s.vec_blocks = (int)std::min<size_t>((s.n + kT - 1) / kT, 4096);
   const size_t n = s.n;
   int rc = s.take(&s.mask, n, err);
@@ -549,11 +691,11 @@ void precondition(const Solve3Args& a, const State3& s, float wnorm, const float
 // q = M L^2 p (p double-float, zero at known nodes), p.q into scal[0]
 void apply_operator(const Solve3Args& a, const Grid3& G, const State3& s, const float* ph, const float* pl,
                     float* qh, float* ql) {
-  k3_lap<false><<<s.grid3, s.block3, 0, a.stream>>>(G, ph, pl, s.uh, s.ul, s.mask, nullptr, nullptr, nullptr);
+  k3_lap<false><<<s.gridz, s.block3, 0, a.stream>>>(G, ph, pl, s.uh, s.ul, s.mask, nullptr, nullptr, nullptr);
   ++*a.launches;
-  k3_lap<true><<<s.grid3, s.block3, 0, a.stream>>>(G, s.uh, s.ul, qh, ql, s.mask, ph, pl, s.part);
+  k3_lap<true><<<s.gridz, s.block3, 0, a.stream>>>(G, s.uh, s.ul, qh, ql, s.mask, ph, pl, s.part);
   ++*a.launches;
-  k3_sum<<<1, kT, 0, a.stream>>>(s.part, s.n_parts, s.scal + 0);
+  k3_sum<<<1, kT, 0, a.stream>>>(s.part, s.n_parts_z, s.scal + 0);
   ++*a.launches;
 }
 

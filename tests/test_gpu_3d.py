@@ -45,7 +45,9 @@ def _rand_phi(shape, seed, frac=0.35):
 
 
 @pytest.mark.parametrize("bcs", BC_TRIPLES)
-@pytest.mark.parametrize("shape", [(6, 7, 9), (5, 10, 33)])
+# (nz, ny, nx): one block; several z chunks, y blocks and x blocks with ragged tails; sides equal
+# to whole blocks with a one-plane last chunk
+@pytest.mark.parametrize("shape", [(6, 7, 9), (5, 10, 33), (37, 35, 70), (17, 16, 32)])
 def test_operator_bitwise_on_integers(ext, ctx, bcs, shape):
     nz, ny, nx = shape
     phi = _rand_phi(shape, 1)
@@ -96,6 +98,34 @@ def test_solve_random_box_within_the_bound(ext, ctx, bcs):
     phi = _rand_phi(shape, 5, frac=0.5)
     f = np.random.default_rng(6).standard_normal(shape).astype(np.float32)
     _check(ext, ctx, phi, f, bcs)
+
+
+def test_solve_across_blocks_and_chunks(ext):
+    """A box of several z chunks, y blocks and x blocks with ragged tails (the per-block partials
+    of p.q feed every step): the FP64 true residual reaches the target, the known values are kept,
+    the oracle's FP64 residual of the FP32 answer sits at the output's rounding level, and the
+    iteration count is the FP64 oracle PCG's within a quarter (the random known set makes this a
+    hard case: about 700 iterations, hence the explicit limit)."""
+    shape = (37, 35, 70)
+    bcs = ("periodic", "symmetric", "dirichlet")
+    phi = _rand_phi(shape, 7, frac=0.5)
+    f = np.random.default_rng(8).standard_normal(shape).astype(np.float32)
+    nz, ny, nx = shape
+    out = torch.empty(shape, device="cuda")
+    c = ext.ext_create(ext.options("fp32", rtol=1e-8, maxit=4000))
+    try:
+        res = ext.ext_solve3d(c, ext.problem3(nx, ny, nz, *bcs, "out"), dev(phi), dev(f), out)
+    finally:
+        ext.ext_destroy(c)
+    assert res["status"] == 0 and res["relres_true"] <= 1e-8, res
+    o = out.cpu().numpy()
+    phi64 = phi.astype(np.float64)
+    known = ob.known_mask(phi64, "out")
+    assert np.array_equal(o[known], f[known])
+    assert o3.true_relative_residual3(o, phi, f, "out", bcs) <= 1e-5
+    A, b, unk, _ = o3.system3(phi64, f.astype(np.float64), "out", bcs)
+    _, it_ref, _ = ob.cg(A, b, rtol=1e-8, maxit=4000, precond=o3.fast_poisson_preconditioner3(unk, shape, bcs))
+    assert abs(res["iters"] - it_ref) <= 0.25 * it_ref, (res["iters"], it_ref)
 
 
 def test_solve_anisotropic_spacing(ext, ctx):
