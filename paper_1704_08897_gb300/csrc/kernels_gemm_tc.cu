@@ -169,14 +169,20 @@ __device__ __forceinline__ int block_exp(float amax) {
 // removes it exactly (FMA; the product is exact) and renormalises the remainder with the lo plane
 // (TwoSum), so the slices carry the value to 2^-32 of the block whatever its size; the last
 // slice is rounded to an integer.  The 16-bit codes are returned as (lane x, lane y) pairs.
+// Every slice is an integer of magnitude at most 256, which keeps the two per-value conversions
+// off the (quarter-rate) conversion pipe: the rounding to the nearest integer (ties to even) adds
+// and removes 1.5 * 2^23 on packed FP32x2, exact for magnitudes below 2^22; and such an integer is
+// exact in BF16, whose bits are then the upper half of the FP32 bits (one byte permutation packs
+// the two lanes' codes).  FP16 codes come from the packed two-value conversion.
 template <bool BF16, int NSL = NS>
 __device__ __forceinline__ void slice_codes2_df(float2 vh, float2 vl, float2 s, float2 is,
                                                 uint32_t (&code)[NSL]) {
+  const float2 rnd = make_float2(12582912.f, 12582912.f), rnd_n = make_float2(-12582912.f, -12582912.f);
   float2 rh = vh, rl = vl, up = s, down = make_float2(-is.x, -is.y);
 #pragma unroll
   for (int k = 0; k < NSL; ++k) {
     const float2 t = __fmul2_rn(rh, up);
-    const float2 c = make_float2(rintf(t.x), rintf(t.y));
+    const float2 c = __fadd2_rn(__fadd2_rn(t, rnd), rnd_n);
     if (k + 1 < NSL) {
       const float2 h = __ffma2_rn(c, down, rh);
       two_sum2(h, rl, rh, rl);
@@ -184,11 +190,11 @@ __device__ __forceinline__ void slice_codes2_df(float2 vh, float2 vl, float2 s, 
     up = mul2(256.f, up);
     down = mul2(0.00390625f, down);
     if (BF16) {
-      code[k] = static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(c.x))) |
-                (static_cast<uint32_t>(__bfloat16_as_ushort(__float2bfloat16_rn(c.y))) << 16);
+      code[k] = __byte_perm(__float_as_uint(c.x), __float_as_uint(c.y), 0x7632);
     } else {
-      code[k] = static_cast<uint32_t>(__half_as_ushort(__float2half_rn(c.x))) |
-                (static_cast<uint32_t>(__half_as_ushort(__float2half_rn(c.y))) << 16);
+      const __half2 h2 = __floats2half2_rn(c.x, c.y);
+      code[k] = static_cast<uint32_t>(__half_as_ushort(__low2half(h2))) |
+                (static_cast<uint32_t>(__half_as_ushort(__high2half(h2))) << 16);
     }
   }
 }
@@ -422,11 +428,23 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         }
       }
       // stage 1's eigenvalues, read now so their latency hides behind the k-blocks
-      float lamx_m = 0.f, lamy_mine = 0.f;
+      // and everything else the weights read from the descriptor, so that nothing is loaded after
+      // the k-blocks: the row's flags, and per column lane a flag word (bit 0: the column is in the
+      // grid, bit 1: it is in the low-mode block) that the weight loop takes by shuffles
+      float lamx_m = 0.f, lamy_mine = 0.f, wnorm = 0.f;
+      bool row_in = false, row_low = false;
+      uint32_t col_flags = 0;
       if (STAGE == 1) {
         // issued here, not where the compiler would sink them: the MMA waits hide their latency
-        if (m < S.nx) lamx_m = ld_early(S.lamx + m);
-        if (col_lane && ncol0 + lane < S.ny) lamy_mine = ld_early(S.lamy + ncol0 + lane);
+        row_in = m < S.nx;
+        row_low = m < S.lowm_x;
+        if (row_in) lamx_m = ld_early(S.lamx + m);
+        const int n_mine = ncol0 + lane;
+        if (col_lane && n_mine < S.ny) {
+          lamy_mine = ld_early(S.lamy + n_mine);
+          col_flags = 1u | (n_mine < S.lowm_y ? 2u : 0u);
+        }
+        wnorm = ld_early(&S.wnorm);
       }
       const int8_t* ea_row = S.tc_e[STAGE] + static_cast<size_t>(m) * kblocks;
       const int8_t* eb_col = S.tc_eb[STAGE] + static_cast<size_t>(ncol0 + (col_lane ? lane : 0)) * kblocks;
@@ -514,11 +532,11 @@ k_prec_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         // weight 1/(lam_y + lam_x)^2 (normalised); lam_y of the warp's columns via shuffles
 #pragma unroll
         for (int i = 0; i < kEpiCols; ++i) {
-          const int n = ncol0 + i;
           const float s = __shfl_sync(0xffffffffu, lamy_mine, i) + lamx_m;
+          const uint32_t f = __shfl_sync(0xffffffffu, col_flags, i);
           // the low block (m < lowm_x, n < lowm_y) comes from the six-slice products instead
-          const bool ok = (m < S.nx) && (n < S.ny) && (s > 0.f) && !(m < S.lowm_x && n < S.lowm_y);
-          const f2 wv = df_mul(f2{val[i], vlo[i]}, spectral_weight_of(S.wnorm, s));
+          const bool ok = row_in && (f & 1u) && (s > 0.f) && !(row_low && (f & 2u));
+          const f2 wv = df_mul(f2{val[i], vlo[i]}, spectral_weight_of(wnorm, s));
           val[i] = ok ? wv.hi : 0.f;
           vlo[i] = ok ? wv.lo : 0.f;
         }
