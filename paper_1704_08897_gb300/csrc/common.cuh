@@ -414,6 +414,17 @@ struct CompDotDF {
     return d;
   }
 };
+// CompDotDF on two lanes at once (the same operations, in the same order, per lane).
+struct CompDotDF2 {
+  float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+  __device__ __forceinline__ void add(float2 ah, float2 al, float2 bh, float2 bl) {
+    const float2 p = __fmul2_rn(ah, bh);
+    const float2 pe = __ffma2_rn(ah, bh, make_float2(-p.x, -p.y));
+    float2 e;
+    two_sum2(s, p, s, e);
+    c = add2(c, add2(e, __ffma2_rn(ah, bl, __ffma2_rn(al, bh, pe))));
+  }
+};
 
 // ------------------------------------------------------------------------------------------
 // Ghost-node maps of one axis (Algorithm 1 padding; symmetric = half-sample reflection;

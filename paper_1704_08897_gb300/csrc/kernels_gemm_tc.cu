@@ -1011,7 +1011,8 @@ constexpr int kLowSmem = kLowNS * (LA_PLANE + LB_PLANE) + 1024 + 256;
 static_assert(kLowNS * LBN <= kLowTmemCols, "low-mode TMEM columns");
 static_assert(kLowK3 == LBK, "the inverse product's k fits one copy");
 static_assert(kLowThreads == 16 * 32 && 2 * BM * 33 * 4 + 2 * BM * kLowM * 4 <= kLowNS * (LA_PLANE + LB_PLANE),
-              "the G stage: sixteen warps (ky = warp, warp + 16) and its staging in the operand buffers");
+              "the G stage: sixteen warps (ky = 2 warp, 2 warp + 1) and its staging in the operand buffers");
+static_assert((2 * BM * 33) % 2 == 0 && kLowM % 2 == 0, "8-byte aligned Qy_low pairs in the G stage");
 
 struct LowCtl {
   uint64_t full, done;
@@ -1178,20 +1179,23 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
         ys[BM * kLowM + e] = S.low_qyd[static_cast<size_t>(S.nyp) * kLowM + a];
       }
       __syncthreads();
-      // thread: kx = lane, ky = warp and warp + 16
-      CompDotDF g0, g1;
+      // thread: kx = lane, ky = 2 warp and 2 warp + 1, the two dot products on packed FP32x2
+      // (one 8-byte broadcast load of each plane's Qy_low pair per row)
+      CompDotDF2 g;
+      const int ky0 = 2 * warp;
 #pragma unroll 4
       for (int rr = 0; rr < BM; ++rr) {
         const float bh = hs[rr * 33 + lane], bl = hs[BM * 33 + rr * 33 + lane];
-        g0.add(ys[rr * kLowM + warp], ys[BM * kLowM + rr * kLowM + warp], bh, bl);
-        g1.add(ys[rr * kLowM + warp + 16], ys[BM * kLowM + rr * kLowM + warp + 16], bh, bl);
+        const float2 ah = *reinterpret_cast<const float2*>(ys + rr * kLowM + ky0);
+        const float2 al = *reinterpret_cast<const float2*>(ys + BM * kLowM + rr * kLowM + ky0);
+        g.add(ah, al, make_float2(bh, bh), make_float2(bl, bl));
       }
       float* gp = S.low_gp + static_cast<size_t>(it.tile) * 2 * kLowM * kLowM;
-      const f2 a0 = df_norm(g0.s, g0.c), a1 = df_norm(g1.s, g1.c);
-      gp[warp * kLowM + lane] = a0.hi;
-      gp[kLowM * kLowM + warp * kLowM + lane] = a0.lo;
-      gp[(warp + 16) * kLowM + lane] = a1.hi;
-      gp[kLowM * kLowM + (warp + 16) * kLowM + lane] = a1.lo;
+      const f2 a0 = df_norm(g.s.x, g.c.x), a1 = df_norm(g.s.y, g.c.y);
+      gp[ky0 * kLowM + lane] = a0.hi;
+      gp[kLowM * kLowM + ky0 * kLowM + lane] = a0.lo;
+      gp[(ky0 + 1) * kLowM + lane] = a1.hi;
+      gp[kLowM * kLowM + (ky0 + 1) * kLowM + lane] = a1.lo;
       __syncthreads();  // the next item's tensor copies overwrite the staging
     }
   }
@@ -1299,8 +1303,9 @@ k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
       tc_fence_after();
       const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB + b * kLowNS * LB_PLANE);
       const uint32_t dset = tmem_base + b * 256;
+      // only the first kLowM of the copy's LBK k are modes; the rest is zero padding
 #pragma unroll
-      for (int jj = 0; jj < LBK / 16; ++jj) {
+      for (int jj = 0; jj < kLowM / 16; ++jj) {
 #pragma unroll
         for (int i = 0; i < kLowNS; ++i)
           umma(dset + i * LBN, sdesc(a0 + i * LA_PLANE) + 2 * jj, sdesc(b0) + 2 * jj,
@@ -1425,12 +1430,17 @@ __device__ __forceinline__ void slice_codes_df(float vh, float vl, float s, floa
 // product's items): G = the forward tiles' shares summed in tile order, G' = w o G, and the
 // block's rows of J^T, J^T[x][ky] = sum_kx G'[ky][kx] Qx[x][kx], by compensated dot products of
 // double-float operands (Ogita-Rump-Oishi), each row then cut into six slices with its block
-// exponent (the inverse product's A operand).  Qx's row is broadcast across the warp by shuffles.
+// exponent (the inverse product's A operand).  Lane ky reads its row of G' from shared memory;
+// the block's rows of Qx_low are staged there transposed, so that a warp takes the values of two
+// adjacent rows at one kx by one 8-byte broadcast load, and eight rows run as four packed
+// chains.
+constexpr int kQsStride = BM + 2;  // [kx][row] stride: even (8-byte pairs), 2-way staging conflicts
 template <bool BF16>
 __global__ void __launch_bounds__(256)
 k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
           const int* __restrict__ n_items, int mode) {
   __shared__ float gh[kLowM][kLowM + 1], gl[kLowM][kLowM + 1];
+  __shared__ __align__(16) float qs[2][kLowM][kQsStride];  // Qx_low rows of the block: hi, lo
   const int total = *n_items;
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   for (int w = blockIdx.x; w < total; w += gridDim.x) {
@@ -1439,6 +1449,13 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     if (!slot_runs(S.sc, mode) || S.lowm_x == 0) continue;
     const float* qx_h = S.low_qxd;
     const float* qx_l = S.low_qxd + static_cast<size_t>(S.nxp) * kLowM;
+    const int xb = it.tile * BM;
+    for (int e = t; e < BM * kLowM; e += 256) {
+      const int r = e / kLowM, kx = e - r * kLowM;
+      const size_t a = static_cast<size_t>(xb + r) * kLowM + kx;
+      qs[0][kx][r] = __ldg(qx_h + a);
+      qs[1][kx][r] = __ldg(qx_l + a);
+    }
     for (int e = t; e < kLowM * kLowM; e += 256) {
       f2 g{0.f, 0.f};
       for (int tt = 0; tt < S.n_l1_tiles; ++tt) {
@@ -1455,35 +1472,25 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     __syncthreads();
     uint16_t* jt = static_cast<uint16_t*>(S.low_jt);
     const size_t plane = static_cast<size_t>(S.nxp) * kLowK3;
-    float gr_h[kLowM], gr_l[kLowM];  // the lane's row ky of G'
-#pragma unroll
-    for (int kx = 0; kx < kLowM; ++kx) {
-      gr_h[kx] = gh[lane][kx];
-      gr_l[kx] = gl[lane][kx];
-    }
-    // the warp's 16 rows of the block, four at a time: four independent dot-product chains
-    constexpr int kRowsPerWarp = 4;
-    const int xw = it.tile * BM + warp * (BM / 8);
-    for (int x0 = xw; x0 < xw + BM / 8; x0 += kRowsPerWarp) {
-      float qh[kRowsPerWarp], ql[kRowsPerWarp];
-#pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r) {
-        const size_t a = static_cast<size_t>(x0 + r) * kLowM;
-        qh[r] = __ldg(qx_h + a + lane);
-        ql[r] = __ldg(qx_l + a + lane);
-      }
-      CompDotDF acc2[kRowsPerWarp];
-#pragma unroll
+    // the warp's 16 rows of the block, eight at a time: four packed pairs of independent chains
+    constexpr int kRowsPerGroup = 8;
+    for (int rb = warp * (BM / 8); rb < (warp + 1) * (BM / 8); rb += kRowsPerGroup) {
+      CompDotDF2 acc[kRowsPerGroup / 2];
+#pragma unroll 4
       for (int kx = 0; kx < kLowM; ++kx) {
+        const float ah = gh[lane][kx], al = gl[lane][kx];
 #pragma unroll
-        for (int r = 0; r < kRowsPerWarp; ++r)
-          acc2[r].add(gr_h[kx], gr_l[kx], __shfl_sync(0xffffffffu, qh[r], kx),
-                      __shfl_sync(0xffffffffu, ql[r], kx));
+        for (int q = 0; q < kRowsPerGroup / 2; ++q) {
+          const float2 bh = *reinterpret_cast<const float2*>(&qs[0][kx][rb + 2 * q]);
+          const float2 bl = *reinterpret_cast<const float2*>(&qs[1][kx][rb + 2 * q]);
+          acc[q].add(make_float2(ah, ah), make_float2(al, al), bh, bl);
+        }
       }
 #pragma unroll
-      for (int r = 0; r < kRowsPerWarp; ++r) {
-        const int x = x0 + r;
-        const f2 j = df_norm(acc2[r].s, acc2[r].c);
+      for (int r = 0; r < kRowsPerGroup; ++r) {
+        const int x = xb + rb + r;
+        const CompDotDF2& d = acc[r / 2];
+        const f2 j = (r & 1) ? df_norm(d.s.y, d.c.y) : df_norm(d.s.x, d.c.x);
         const int E = low_block_exp(warp_max(fabsf(j.hi)));
         uint16_t code[kLowNS];
         slice_codes_df<BF16>(j.hi, j.lo, pow2f(8 - E), pow2f(E - 8), code);
@@ -1495,7 +1502,7 @@ k_low_mid(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         if (lane == 0) S.low_jt_e[x] = static_cast<int8_t>(E);
       }
     }
-    __syncthreads();  // gh, gl are rewritten by the next item
+    __syncthreads();  // gh, gl and qs are rewritten by the next item
   }
 }
 
