@@ -481,6 +481,8 @@ def run_ours(args, rank, world):
            "config": dict(cfg, l2="flushed between steps (256 MiB write)",
                           parallelism="replicas" if world > 1 else "single",
                           low_modes=_options(cfg["prec"]).low_modes,
+                          # whether the profiled pass ran the low-mode kernels (None: not profiled)
+                          low_modes_active=None if kernels is None else "low_fwd" in kernels,
                           fold=_options(cfg["prec"]).fold),
            "iterations": iters if len(iters) <= 4 else
            {"min": min(iters), "median": statistics.median(iters), "max": max(iters)},

@@ -92,7 +92,11 @@ typedef struct {
                               tensor-core products of about 48 bits instead of the four-slice
                               stages: 20-28% fewer iterations at more cost per iteration;
                               0 = all modes from the four-slice stages; 2 = on for grids with a
-                              side of at least 2048 nodes, off otherwise (default)            */
+                              side of at least 2048 nodes and for every grid of an ext_solve /
+                              ext_solve_batch / ext_solve_multi call whose grids hold at least
+                              2048^2 nodes together, off otherwise (default; served requests
+                              take the per-grid rule).  With 2, a grid's iterates therefore
+                              depend on the call it is solved in; 0 or 1 fix them.            */
   int64_t wait_cycles;     /* bound, in SM clock cycles, of every wait of a kernel for its own
                               tensor copies and tensor-core pipeline; a wait that runs out makes
                               the kernel drain what it issued and return, and the call returns

@@ -499,7 +499,7 @@ static std::string shape_key(int count, const ext_problem* probs, bool host_io) 
 // descriptor, its tensor-core problems and their tensor maps.  With size_only, only s.bytes is
 // computed.
 static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotHost& s,
-                      char* arena = nullptr, bool size_only = false) {
+                      char* arena = nullptr, bool size_only = false, bool large_call = false) {
   std::lock_guard<std::recursive_mutex> plk(ctx->plan_mu);
   s.prob = prob;
   s.d = SlotDesc{};
@@ -572,10 +572,13 @@ static int build_slot(ext_ctx* ctx, const ext_problem& prob, bool host_io, SlotH
   };
   std::vector<TcLay> tl;
   const int NS = ctx->tc ? tc_planes(ctx->split) : 0;
-  // the low-mode correction: always (1), never (0), or for grids of side >= 2048 (2), where the
-  // four-slice stages dominate an iteration and the correction's iterations saved outweigh its cost
+  // the low-mode correction: always (1), never (0), or (2) for grids of side >= 2048 and for every
+  // grid of a call whose grids hold >= 2048^2 nodes together (large_call): there the correction's
+  // kernels run at throughput and the iterations they save outweigh their cost; on one smaller
+  // grid they are latency-bound and cost more than they save
   const bool low = ctx->tc && (ctx->opt.low_modes == 1 ||
-                               (ctx->opt.low_modes == 2 && std::max(nx, ny) >= kLowAutoSide));
+                               (ctx->opt.low_modes == 2 &&
+                                (std::max(nx, ny) >= kLowAutoSide || large_call)));
   // transform problems: in mixed modes always (the slot itself or its classes), on the CUDA
   // cores only for a folded slot (its classes; an unfolded slot runs on its own buffers)
   if (ctx->tc || d.mir) {
@@ -884,9 +887,11 @@ static int build_workspace(ext_ctx* ctx, int count, const ext_problem* probs, bo
   W->host_io = host_io;
   W->slots.resize(count);
   std::vector<WorkItem> st, vec, gm, l1, l3, fold, unfold, tcl, prep;
+  long long call_nodes = 0;
+  for (int i = 0; i < count; ++i) call_nodes += (long long)probs[i].nx * probs[i].ny;
   for (int i = 0; i < count; ++i) {
     SlotHost& s = W->slots[i];
-    int rc = build_slot(ctx, probs[i], host_io, s);
+    int rc = build_slot(ctx, probs[i], host_io, s, nullptr, false, call_nodes >= kLowAutoNodes);
     if (rc) {
       for (int j = 0; j < i; ++j) cudaFree(W->slots[j].arena);
       cudaFree(s.arena);

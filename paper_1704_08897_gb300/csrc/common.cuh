@@ -23,6 +23,7 @@ constexpr int kStWinY = kStTileY + 4;
 constexpr int kStMaps = 7;          // stencil tensor maps per slot
 constexpr int kLowM = 32;           // low modes per axis computed in high precision
 constexpr int kLowAutoSide = 2048;  // low_modes = 2: grids with a side of at least this many nodes
+constexpr long long kLowAutoNodes = 2048LL * 2048;  // low_modes = 2: or calls with this many nodes
 constexpr int kLowNS = 6;           // integer slices per operand of the low-mode products
 constexpr int kLowK3 = 64;          // k extent of the inverse low-mode product (32 modes, zero-padded)
 constexpr int kVecChunk = 4096;     // elements per work item of the vector kernels

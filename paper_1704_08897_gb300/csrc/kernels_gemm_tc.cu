@@ -1013,6 +1013,7 @@ static_assert(kLowK3 == LBK, "the inverse product's k fits one copy");
 static_assert(kLowThreads == 16 * 32 && 2 * BM * 33 * 4 + 2 * BM * kLowM * 4 <= kLowNS * (LA_PLANE + LB_PLANE),
               "the G stage: sixteen warps (ky = 2 warp, 2 warp + 1) and its staging in the operand buffers");
 static_assert((2 * BM * 33) % 2 == 0 && kLowM % 2 == 0, "8-byte aligned Qy_low pairs in the G stage");
+static_assert((BM * kLowM) % kLowThreads == 0, "the tile's Qy_low rows in equal shares per thread");
 
 struct LowCtl {
   uint64_t full, done;
@@ -1077,6 +1078,16 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
       tmap_acquire(mb);
     }
     const int m = m0 + row;
+    // the thread's share of the tile's Qy_low rows (the G stage's operand), loaded now so that
+    // their latency hides behind the k-blocks
+    constexpr int kYq = BM * kLowM / kLowThreads;
+    float yq[2 * kYq];
+#pragma unroll
+    for (int i = 0; i < kYq; ++i) {
+      const size_t a = static_cast<size_t>(m0) * kLowM + threadIdx.x + i * kLowThreads;
+      yq[i] = ld_early(S.low_qyd + a);
+      yq[kYq + i] = ld_early(S.low_qyd + static_cast<size_t>(S.nyp) * kLowM + a);
+    }
     // double-float result of the thread's row, one per column of its group
     float hi[kLowCols], lo[kLowCols];
 #pragma unroll
@@ -1173,10 +1184,10 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
         hs[row * 33 + cg * kLowCols + c] = hv.hi;
         hs[BM * 33 + row * 33 + cg * kLowCols + c] = hv.lo;
       }
-      for (int e = threadIdx.x; e < BM * kLowM; e += kLowThreads) {
-        const size_t a = static_cast<size_t>(m0) * kLowM + e;
-        ys[e] = S.low_qyd[a];
-        ys[BM * kLowM + e] = S.low_qyd[static_cast<size_t>(S.nyp) * kLowM + a];
+#pragma unroll
+      for (int i = 0; i < kYq; ++i) {
+        ys[threadIdx.x + i * kLowThreads] = yq[i];
+        ys[BM * kLowM + threadIdx.x + i * kLowThreads] = yq[kYq + i];
       }
       __syncthreads();
       // thread: kx = lane, ky = 2 warp and 2 warp + 1, the two dot products on packed FP32x2
@@ -1330,6 +1341,7 @@ k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
         ph_fa ^= 1;
         ok = issue_mma(0);
       }
+      if (ok && nt > 1) issue_b(1);
     }
     const int m = m0 + row;
     const float sa = pow2f(static_cast<int>(S.low_jt_e[min(m, S.nxp - 1)]) - 16);
@@ -1337,11 +1349,12 @@ k_low_inv(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items
     for (int j = 0; j < nt; ++j) {
       const int b = j & 1;
       if (threadIdx.x == 0 && !*abort_flag) {
-        if (j + 1 < nt) issue_b(j + 1);
+        // B(j + 1) was copied a step ago; once y-tile j's products are complete its B buffer
+        // takes the copy of y-tile j + 2, which lands while this step's sums are merged
         if (mbar_wait(&ctl->md[b], ph_md[b], abort_flag, wait_cycles)) {
           owe_md[b] = 0;
           ph_md[b] ^= 1;
-          if (j + 1 < nt) issue_mma(j + 1);
+          if (j + 1 < nt && issue_mma(j + 1) && j + 2 < nt) issue_b(j + 2);
         }
       }
       __syncthreads();

@@ -165,3 +165,34 @@ def test_low_mode_correction_cuts_iterations_and_keeps_parity(ext, fold):
             its[(p.name, low)] = res["iters"]
     for name in {k[0] for k in its}:
         assert its[(name, 1)] <= 0.9 * its[(name, 0)], its
+
+
+def test_automatic_low_modes_follow_the_call_size(ext):
+    """low_modes = 2 (the default) turns the correction on for every grid of a call whose grids
+    hold at least 2048^2 nodes together, and leaves it off for the same grids solved one by one
+    or with low_modes = 0 (seen in the per-kernel launch counts)."""
+    probs = [synth.wobbly(512, i) for i in range(17)]  # 17 x 512^2 = 4.46 M nodes >= 2048^2
+    assert sum(p.nx * p.ny for p in probs) >= 2048 * 2048 > 512 * 512
+
+    def low_launches(low_modes, batch):
+        kw = {} if low_modes is None else {"low_modes": low_modes}
+        c = ext.ext_create(ext.options("mixed_bf16", rtol=1e-2, profile=1, **kw))
+        try:
+            sel = probs if batch else probs[:2]
+            outs = [torch.empty(p.phi.shape, device="cuda") for p in sel]
+            if batch:
+                rc, res = ext.ext_solve_batch(c, [ext.problem_of(p) for p in sel],
+                                              [dev(p.phi) for p in sel], [dev(p.f) for p in sel], outs)
+                assert all(r["status"] == 0 for r in res), res
+            else:
+                for p, o in zip(sel, outs):
+                    assert ext.ext_solve(c, ext.problem_of(p), dev(p.phi), dev(p.f), o)["status"] == 0
+            prof = ext.ext_profile_read(c)
+        finally:
+            ext.ext_destroy(c)
+        return prof["low_fwd"][1], prof["low_inv"][1]
+
+    fwd, inv = low_launches(None, True)
+    assert fwd > 0 and inv == fwd
+    assert low_launches(None, False) == (0, 0)
+    assert low_launches(0, True) == (0, 0)
