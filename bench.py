@@ -152,8 +152,9 @@ def _fold_default():
     return bool(_OPTION_OVERRIDES.get("fold", 1))
 
 
-def algorithmic_cost(probs, kind):
-    """(amount, unit) per launch of one kernel kind over the workload's instances."""
+def algorithmic_cost(probs, kind, low=False):
+    """(amount, unit) per launch of one kernel kind over the workload's instances; low: the
+    low-mode correction ran (the residual is then cut into six slices instead of four)."""
     if kind in ("low_fwd", "low_inv"):
         # the lowest 32 modes of one axis against the whole grid: 2 * nx * ny * 32 flop
         return sum(2 * p.nx * p.ny * min(32, p.nx) for p in probs), "flop"
@@ -169,9 +170,10 @@ def algorithmic_cost(probs, kind):
         return sum(33 * p.nx * p.ny for p in probs), "byte"
     if kind == "update":    # read x, p, q, r; write x, r (8 bytes each)
         return sum(48 * p.nx * p.ny for p in probs), "byte"
-    if kind in ("split", "fold"):  # read r (8); write four 16-bit slices (8): unfolded / folded
+    if kind in ("split", "fold"):  # read r (8); write four (six) 16-bit slices: unfolded / folded
         f = kind == "fold"
-        return sum(16 * p.nx * p.ny for p in probs
+        per_node = 8 + 2 * (6 if low else 4)
+        return sum(per_node * p.nx * p.ny for p in probs
                    if (len(mirror_classes(p.nx, _fold_default())) > 1 or
                        len(mirror_classes(p.ny, _fold_default())) > 1) == f), "byte"
     if kind == "unfold":    # read the classes' g (8), r (8), mask (1); write z (8); q (8) is read
@@ -421,7 +423,7 @@ def run_ours(args, rank, world):
                    for k, (ms, n) in prof.items() if n}
         dom = max(prof, key=lambda k: prof[k][0])
         ms, n = prof[dom]
-        amount, unit = algorithmic_cost(probs, dom)
+        amount, unit = algorithmic_cost(probs, dom, low="low_fwd" in kernels)
         if amount is not None and n:
             per_launch_s = ms / n / 1e3
             if unit == "flop" and prec != "fp32":
@@ -458,7 +460,7 @@ def run_ours(args, rank, world):
                 hbm_peak = json.load(fh)["hbm_gbs"]
             hbm = {}
             for kd in ("stencil", "update", "split", "fold", "unfold"):
-                amt, un = algorithmic_cost(probs, kd)
+                amt, un = algorithmic_cost(probs, kd, low="low_fwd" in kernels)
                 if kd in prof and prof[kd][1] and un == "byte":
                     gbs = amt / (prof[kd][0] / prof[kd][1] / 1e3) / 1e9
                     hbm[kd] = {"achieved_gbs": round(gbs, 1), "frac": round(gbs / hbm_peak, 4),

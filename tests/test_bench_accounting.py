@@ -20,6 +20,7 @@ def test_algorithmic_cost_per_kernel_kind():
     assert bench.algorithmic_cost(probs, "update") == (48 * nodes, "byte")
     # 64 and 128 do not fold: all slicing is the unfolded kind
     assert bench.algorithmic_cost(probs, "split") == (16 * nodes, "byte")
+    assert bench.algorithmic_cost(probs, "split", low=True) == (20 * nodes, "byte")
     assert bench.algorithmic_cost(probs, "fold") == (0, "byte")
     big = [synth.wobbly(256, 1)]
     assert bench.algorithmic_cost(big, "fold") == (16 * 256 * 256, "byte")
