@@ -329,9 +329,8 @@ int ext_axis_slices(int32_t n, ext_bc bc, int32_t type, uint16_t* codes, int8_t*
  * that stream has finished its work.
  * Scratch: one fixed 2 MiB array per device (grids up to 1,048,576 nodes and 32,768 stencil
  * tiles of 64x32; larger grids return EXT_EINVAL, see ext_noalloc_last_error).  The first call on
- * a device looks up that array's device address (a lookup that allocates nothing); make that first
- * call before any stream capture.  The looked-up address is kept for the life of the process and
- * does not survive cudaDeviceReset.  All calls on a device share the array: calls whose GPU work
+ * a device looks up that array's device address (a lookup that allocates nothing).  The looked-up
+ * address is kept for the life of the process and does not survive cudaDeviceReset.  All calls on a device share the array: calls whose GPU work
  * overlaps race and must be serialised by the caller.  Nothing in it needs to start at zero. */
 int ext_apply_biharmonic_noalloc(const ext_problem* prob, const float* phi, const float* p,
                                  float* q, double* sum_pq, void* cuda_stream);

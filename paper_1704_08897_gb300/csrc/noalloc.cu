@@ -15,8 +15,8 @@
 // reads is written earlier in that same call, so nothing has to start at zero.  Calls whose work
 // overlaps on the GPU (different streams, or different host threads) race on the array and must
 // be serialised by the caller.  The array's device address is looked up once per device, by the
-// first call made with that device current; that first call should come before any stream
-// capture, and the cached address does not survive cudaDeviceReset (the module is loaded anew).
+// first call made with that device current; the cached address does not survive cudaDeviceReset
+// (the module is loaded anew).
 #include <cuda_runtime.h>
 
 #include <cstdint>
