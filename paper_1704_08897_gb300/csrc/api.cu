@@ -183,17 +183,6 @@ bool bx::is_device_ptr(const void* p) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-// Transform tiles in decreasing order of their k extent (a tile's cost is proportional to it), so
-// that the persistent CTAs of a launch end together; tiles of one slot keep their order.  Any
-// order gives the same results: tile partial sums are stored per tile and reduced in tile order.
-static void longest_first(std::vector<WorkItem>& gm, const std::vector<SlotHost>& slots) {
-  std::stable_sort(gm.begin(), gm.end(), [&](const WorkItem& a, const WorkItem& b) {
-    const SlotDesc& da = slots[a.slot].d;
-    const SlotDesc& db = slots[b.slot].d;
-    return std::max(da.nxp, da.nyp) > std::max(db.nxp, db.nyp);
-  });
-}
-
 // ---- tensor-core operands --------------------------------------------------------------------
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
@@ -864,7 +853,10 @@ static void tc_items(const SlotHost& s, int i, std::vector<WorkItem>& gm, std::v
   }
 }
 
-// Tensor-core work items in the order the persistent kernels take them (longest first).
+// Tensor-core work items in the order the persistent kernels take them: decreasing k extent of
+// their transform problem (a tile's cost is proportional to it), so that the persistent CTAs of a
+// launch end together; tiles of one problem keep their order.  Any order gives the same results:
+// tile partial sums are stored per tile and reduced in tile order.
 static void longest_first_tc(std::vector<WorkItem>& gm, const std::vector<SlotHost>& slots) {
   std::stable_sort(gm.begin(), gm.end(), [&](const WorkItem& a, const WorkItem& b) {
     const SlotDesc& da = slots[a.slot / kMirClasses].tcp[a.slot % kMirClasses];
