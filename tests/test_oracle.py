@@ -8,7 +8,6 @@ import os
 
 import numpy as np
 import pytest
-import scipy.sparse as sp
 
 from oracle import biharmonic as ob
 from paper_1704_08897_gb300 import synth
