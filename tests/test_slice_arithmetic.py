@@ -19,7 +19,7 @@ def magic_round(t):
         return (t + ROUND) - ROUND
 
 
-def test_magic_rounding_equals_rint_on_every_slice_value():
+def test_magic_rounding_equals_rint_over_the_slice_range():
     # FP32 values of the slices' range [-256, 256]: every exponent (subnormals included), each
     # with a dense sample of its mantissas (every 97th bit pattern)
     vals = []
