@@ -1235,10 +1235,11 @@ k_low_tc(const SlotDesc* __restrict__ slots, const WorkItem* __restrict__ items,
 }
 
 // Inverse low-mode product, zl[y][x] = sum_ky Qy[y][ky] J[ky][x], one item per (slot, 128-row
-// tile of x).  The tile's six J^T slice planes (its A operand, k = ky padded to 64) are copied
-// once; the B operand (Qy_low's slices for 32 values of y) is double-buffered, and the products of
-// consecutive y-tiles go to two TMEM sets, so that the MMAs of one y-tile run while the sixteen
-// warps merge and store the previous one.
+// tile of x).  The tile's six J^T slice planes (its A operand, k = ky padded to 64; the products
+// use the 32 real k) are copied once; the B operand (Qy_low's slices for 32 values of y) is
+// double-buffered, each copy issued two y-tiles ahead (as soon as the products that read its
+// buffer are complete), and the products of consecutive y-tiles go to two TMEM sets, so that the
+// MMAs of one y-tile run while the sixteen warps merge and store the previous one.
 struct LowInvCtl {
   uint64_t fa, fb[2], md[2];
   uint32_t tmem;
